@@ -1,0 +1,214 @@
+/*
+ * mhs.h -- C ABI of the GB300 kernelization library for Multiple Hitting Set.
+ *
+ * The library applies the paper's two demand-aware rules exhaustively, in
+ * rounds, on one GPU (arXiv 2109.06042, Section 4.1):
+ *
+ *   DP (demand pushing, Section 3.1): hyperedge e_i supersedes e_j if
+ *       f(e_i) - |e_i \ e_j| >= f(e_j); a superseded hyperedge is deleted.
+ *       Algorithm 1 computes this for all pairs from I^E = A A^T (Eq. (1)):
+ *       D_ij = [f_i - (I^E_ii - I^E_ij) >= f_j], and deletes e_j iff some
+ *       i has D_ij and (not D_ji or i < j).
+ *   MD (multiple domination, Section 3.1): vertex v_j is deleted if it has
+ *       at least max_{e in E(v_j)} f(e) dominators (v_i with E(v_j) within
+ *       E(v_i)).  Algorithm 2 computes this from I^V = A^T A (Eq. (2)):
+ *       D_ij = [I_ij = I_jj and (I_ij != I_ii or i < j)], C_j = sum_i D_ij,
+ *       delete v_j iff C_j >= max f over E(v_j) (0 if E(v_j) is empty).
+ *   Algorithm 3: repeat (Algorithm 1, then Algorithm 2 on its output) until
+ *       a round deletes nothing.
+ *
+ * Problem input (Problem 1.1, Section 1): hypergraph H = (V, E) with
+ * V = {0..n-1}, hyperedges e_0..e_{m-1} in CSR form, demands f(e) >= 1 and
+ * the budget k.  DP and MD never change f or k; k is passed through.
+ *
+ * Conventions
+ *  - Every function returns an mhs_status; mhs_last_error() gives a message
+ *    for the calling thread.
+ *  - The library never takes ownership of caller memory.  Input arrays are
+ *    read during the call (host arrays) or before the call's stream work
+ *    completes (device arrays); output buffers are written by the call.
+ *  - Lowest-index tie-breaking makes results deterministic: ids are the
+ *    input ids, and the result lists them in ascending order.
+ *  - Counts are exact: incidences are 0/1 values in FP8 E4M3 (exact) with
+ *    FP32 accumulation (exact below 2^24), or bit-packed with integer
+ *    popcounts; n and m must be < 2^24.
+ *  - All device work of an instance runs on the stream given at load time
+ *    (NULL: the library creates a non-blocking stream for the instance).
+ */
+#ifndef MHS_H
+#define MHS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MHS_OK = 0,
+    MHS_EINVAL = 1,    /* invalid argument or malformed instance */
+    MHS_ENOMEM = 2,    /* device or host allocation failed, or over budget */
+    MHS_ECUDA = 3,     /* CUDA error; see mhs_last_error() */
+    MHS_EAGAIN = 4,    /* result not ready yet (serving) */
+    MHS_ETIMEDOUT = 5, /* a bounded wait ran out */
+    MHS_EBUSY = 6,     /* request queue full (serving) */
+    MHS_EDEVICE = 7    /* a kernel reported an internal error status */
+} mhs_status;
+
+/* How the pair counts I^E_ij / I^V_ij are contracted. */
+typedef enum {
+    MHS_CONTRACT_AUTO = 0,     /* library choice by size */
+    MHS_CONTRACT_FP8 = 1,      /* tcgen05 tensor cores, E4M3 0/1, FP32 accumulate */
+    MHS_CONTRACT_POPCOUNT = 2  /* bit-packed AND + popcount on the integer units */
+} mhs_contraction;
+
+typedef struct {
+    int32_t contraction; /* mhs_contraction */
+    int32_t max_rounds;  /* mhs_kernelize stops after this many rounds; 0 = fixpoint */
+    int32_t use_graphs;  /* 1: replay one captured CUDA graph per round */
+    int32_t reserved[5]; /* must be zero */
+} mhs_options;
+
+typedef struct {
+    int32_t n_alive;    /* vertices left (over all instances for a batch) */
+    int32_t m_alive;    /* hyperedges left */
+    int32_t rounds;     /* rounds executed so far, incl. a final unchanged one (max over a batch) */
+    int32_t changed;    /* 1 if the last executed round deleted something */
+    int32_t dp_deleted; /* hyperedges deleted by the last round's DP pass */
+    int32_t md_deleted; /* vertices deleted by the last round's MD pass */
+} mhs_round_stats;
+
+typedef struct mhs_instance mhs_instance;
+
+/* Fill *opt with defaults (AUTO contraction, fixpoint, graphs on). */
+mhs_status mhs_default_options(mhs_options *opt);
+
+/*
+ * Load one instance from HOST arrays (the input encoding of Section 2.2:
+ * the library builds the incidence matrix A of Section 2.1 on the device).
+ *   n, m          number of vertices / hyperedges, 0 <= n, m < 2^24
+ *   edge_ptr      int32[m+1], edge_ptr[0] = 0, non-decreasing
+ *   edge_vtx      int32[edge_ptr[m]], vertex ids in [0, n), no id twice in
+ *                 one hyperedge (any order)
+ *   demand        int32[m], f(e) >= 1 (f(e) > |e| is allowed: the instance
+ *                 is then infeasible but the rules stay well defined)
+ *   k             the budget, returned unchanged
+ *   opt           options (NULL: defaults)
+ *   cuda_stream   cudaStream_t for all work of this instance, or NULL
+ *   out           receives the new instance handle
+ * Errors: MHS_EINVAL for malformed input (nothing allocated), MHS_ENOMEM,
+ * MHS_ECUDA.  The call returns after the input is on the device.
+ */
+mhs_status mhs_load(int32_t n, int32_t m, const int32_t *edge_ptr, const int32_t *edge_vtx,
+                    const int32_t *demand, int64_t k, const mhs_options *opt,
+                    void *cuda_stream, mhs_instance **out);
+
+/*
+ * Same as mhs_load with DEVICE arrays (same layout).  The instance keeps
+ * its own copy.  Structural checks run on the device; malformed input
+ * gives MHS_EINVAL (one stream synchronisation at load).  Repeated vertex
+ * ids inside one hyperedge count once.
+ */
+mhs_status mhs_load_device(int32_t n, int32_t m, const int32_t *edge_ptr,
+                           const int32_t *edge_vtx, const int32_t *demand, int64_t k,
+                           const mhs_options *opt, void *cuda_stream, mhs_instance **out);
+
+/*
+ * Load a batch of independent instances from HOST arrays, reduced together
+ * (each round contracts all unfinished instances in the same launches).
+ *   count                 number of instances, >= 1
+ *   n[b], m[b]            sizes of instance b
+ *   edge_ptr              int64[sum m + 1]: CSR over the concatenated
+ *                         hyperedges of all instances (instance b owns
+ *                         hyperedges [sum_{c<b} m[c], sum_{c<=b} m[c]))
+ *   edge_vtx              vertex ids local to each instance, in [0, n[b])
+ *   demand                int32[sum m]
+ *   k                     int64[count]
+ * Results are read per instance with mhs_result_at().
+ */
+mhs_status mhs_load_batch(int32_t count, const int32_t *n, const int32_t *m,
+                          const int64_t *edge_ptr, const int32_t *edge_vtx,
+                          const int32_t *demand, const int64_t *k, const mhs_options *opt,
+                          void *cuda_stream, mhs_instance **out);
+
+/* Number of instances held by the handle (1 unless loaded as a batch). */
+int32_t mhs_count(const mhs_instance *inst);
+
+/*
+ * One iteration of Algorithm 3 (one DP pass, then one MD pass on its
+ * output) for every unfinished instance.  An instance whose last round
+ * deleted nothing is finished and is not run again.  stats may be NULL.
+ * Synchronises the instance's stream once.
+ */
+mhs_status mhs_reduce_round(mhs_instance *inst, mhs_round_stats *stats);
+
+/* Algorithm 3 to the fixpoint (or opt.max_rounds rounds).  stats may be NULL. */
+mhs_status mhs_kernelize(mhs_instance *inst, mhs_round_stats *stats);
+
+/*
+ * Copy the current result of instance `index` to HOST buffers (any may be
+ * NULL to skip it; the counts are always returned when their pointer is
+ * non-NULL).
+ *   vtx_out[vtx_cap]      surviving vertex ids (input ids), ascending
+ *   edge_out[edge_cap]    surviving hyperedge ids (input ids), ascending
+ *   demand_out[edge_cap]  f of each surviving hyperedge (unchanged input)
+ *   n_out, m_out          number of surviving vertices / hyperedges
+ *   k_out                 k (unchanged)
+ *   rounds_out            rounds executed for this instance
+ * MHS_EINVAL if a capacity is too small (counts are still returned).
+ */
+mhs_status mhs_result_at(const mhs_instance *inst, int32_t index, int32_t *vtx_out,
+                         int32_t vtx_cap, int32_t *n_out, int32_t *edge_out,
+                         int32_t *demand_out, int32_t edge_cap, int32_t *m_out,
+                         int64_t *k_out, int32_t *rounds_out);
+
+/* mhs_result_at for index 0. */
+mhs_status mhs_result(const mhs_instance *inst, int32_t *vtx_out, int32_t vtx_cap,
+                      int32_t *n_out, int32_t *edge_out, int32_t *demand_out,
+                      int32_t edge_cap, int32_t *m_out, int64_t *k_out, int32_t *rounds_out);
+
+/*
+ * Device-side result of instance `index`: alive masks over the input ids,
+ * written on the instance's stream (no synchronisation).
+ *   alive_v   uint8[n] device buffer, 1 = vertex survives
+ *   alive_e   uint8[m] device buffer, 1 = hyperedge survives
+ */
+mhs_status mhs_result_device(const mhs_instance *inst, int32_t index, uint8_t *alive_v,
+                             uint8_t *alive_e);
+
+/*
+ * Export the current (reduced) instance `index` as a new CSR over the
+ * surviving items, renumbered 0..n'-1 / 0..m'-1 in input order, into HOST
+ * buffers.  Re-loading it with mhs_load and reducing further reaches the
+ * same fixpoint (the output of a round is itself an instance).
+ *   edge_ptr_out  int32[m'+1], edge_vtx_out int32[nnz'], demand_out int32[m']
+ *   *nnz_out      receives nnz'; MHS_EINVAL if nnz_cap or edge_cap is too small.
+ */
+mhs_status mhs_export(const mhs_instance *inst, int32_t index, int32_t *edge_ptr_out,
+                      int32_t edge_cap, int32_t *edge_vtx_out, int64_t nnz_cap,
+                      int32_t *demand_out, int32_t *n_out, int32_t *m_out, int64_t *nnz_out);
+
+/*
+ * Per-round device time split of the last mhs_kernelize / mhs_reduce_round
+ * call, in milliseconds (CUDA events on the instance's stream):
+ * ms[0] DP contraction, ms[1] MD contraction, ms[2] encode + compaction,
+ * ms[3] total.  Timing is recorded only if enabled with mhs_set_timing.
+ */
+mhs_status mhs_set_timing(mhs_instance *inst, int32_t enable);
+mhs_status mhs_last_timing(const mhs_instance *inst, float *ms4);
+
+/* Free all device and host memory of the instance (synchronises its stream). */
+void mhs_free(mhs_instance *inst);
+
+/* Thread-local message for the last failing call on this thread. */
+const char *mhs_last_error(void);
+
+/* Library version string. */
+const char *mhs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MHS_H */

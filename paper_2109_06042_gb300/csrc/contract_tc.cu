@@ -1,0 +1,524 @@
+// contract_tc.cu -- tcgen05 tensor-core contraction of the 0/1 incidence
+// operands with the fused DP / MD epilogue (sm_103a).
+//
+// For each tile of 128 rows i x 256 columns j of the upper triangle, the
+// kernel computes x_ij = sum_k X_ik X_jk, i.e. I^E_ij of Eq. (1) for
+// X = A (phase 0, DP) or I^V_ij of Eq. (2) for X = A^T (phase 1, MD), with
+// both operands taken from the same K-major FP8 E4M3 matrix (0x38 = 1.0,
+// 0x00 = 0).  Products are 0/1 and the FP32 accumulator holds integers
+// below 2^24, so x_ij is exact.  The counts stay in TMEM: the epilogue warps
+// read them with tcgen05.ld and apply Algorithm 1 (DP) or Algorithm 2 (MD)
+// directly; the matrix I is never written.
+//
+// Warp roles (192 threads, one CTA per SM, persistent over the tile list):
+//   warp 0      TMA producer: 128-byte-swizzled K slices of the i rows
+//               (128 x 128 B) and j rows (2 x 128 x 128 B) into a 4-stage
+//               shared-memory ring.
+//   warp 1      TMEM allocation (512 columns = two 128 x 256 FP32
+//               accumulators) and the single-thread tcgen05.mma issuer.
+//   warps 2-5   epilogue; warp w reads TMEM lanes 32*(w%4) .. +31.
+// Every mbarrier wait is bounded: on timeout the kernel records
+// kErrTimeout, stops issuing work, frees its TMEM and returns.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <cstring>
+
+#include "kernels.h"
+#include "mhs_internal.h"
+
+namespace mhs {
+
+namespace {
+
+constexpr int kStages = 4;
+constexpr int kABytes = kTcM * kTcK;            // 16 KB
+constexpr int kBBytes = kTcN * kTcK;            // 32 KB
+constexpr int kStageBytes = kABytes + kBBytes;  // 48 KB
+constexpr int kAccCols = kTcN;                  // FP32 columns per accumulator
+constexpr int kTmemCols = 2 * kAccCols;         // 512
+constexpr int kThreads = 192;
+constexpr int kEpiThreads = 128;
+constexpr int kGroupRows = 8;                   // row blocks per L2 group
+constexpr uint64_t kWaitNs = 4000000000ull;     // 4 s bound on any wait
+
+// ------------------------------------------------------------- PTX glue --
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait; returns false (and raises *abort) once the limit passes or
+// another warp has aborted.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort) {
+    if (mbar_try(bar, parity)) return true;
+    uint64_t t0 = globaltimer();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try(bar, parity)) return true;
+        if ((it & 255u) == 0) {
+            if (*abort) return false;
+            if (globaltimer() - t0 > kWaitNs) { *abort = 1; return false; }
+        }
+    }
+}
+// Bounded wait used only while draining after an abort.
+__device__ __forceinline__ bool mbar_wait_ns(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
+    uint64_t t0 = globaltimer();
+    for (;;) {
+        if (mbar_try(bar, parity)) return true;
+        if (globaltimer() - t0 > limit_ns) return false;
+    }
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const void *tmap, int32_t x, int32_t y,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"(tmap), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms
+// of 1024 bytes (stride byte offset), version 1 (bits 46-48).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;            // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset
+    d |= (uint64_t)1 << 46;            // descriptor version
+    d |= (uint64_t)2 << 61;            // SWIZZLE_128B
+    return d;
+}
+// Instruction descriptor, kind::f8f6f4: D = F32, A = B = E4M3, both K-major,
+// N = 256, M = 128.
+constexpr uint32_t kIdesc = (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(kTcN >> 3) << 17) |
+                            ((uint32_t)(kTcM >> 4) << 24);
+
+__device__ __forceinline__ void mma_f8(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                       uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int c = 0; c < 32; ++c) v[c] = __uint_as_float(r[c]);
+}
+__device__ __forceinline__ void epi_bar() {  // named barrier among the 4 epilogue warps
+    asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory");
+}
+// Named barrier among the epilogue warps that also ANDs a flag, so that all
+// four take the same branch after a wait.
+__device__ __forceinline__ bool epi_bar_and(bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n"
+        " bar.red.and.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(r)
+        : "r"((uint32_t)v), "n"(kEpiThreads)
+        : "memory");
+    return r != 0;
+}
+
+// ------------------------------------------------------ tile scheduling --
+
+// Tiles of one instance: row block bi (128 rows) x column block bj (256
+// columns), kept iff it holds a pair i < j, i.e. bj >= floor(bi / 2).
+// prefix(bi) = number of tiles in row blocks < bi.
+__device__ __forceinline__ int64_t tc_prefix(int64_t bi, int64_t cb) {
+    return bi * cb - (bi / 2) * ((bi - 1) / 2 > 0 ? (bi - 1) / 2 : 0);
+}
+
+// Order: groups of kGroupRows row blocks; inside a group, column block by
+// column block, and inside a column block the group's row blocks.  About
+// 152 concurrent tiles then share ~8 row blocks and ~19 column blocks,
+// which keeps their K slices in L2.
+__device__ void tc_tile_coords(int64_t t, int32_t R, int32_t *bi_out, int32_t *bj_out) {
+    const int32_t rb = tc_row_blocks(R), cb = tc_col_blocks(R);
+    const int32_t ng = (rb + kGroupRows - 1) / kGroupRows;
+    int32_t lo = 0, hi = ng;  // find group g: prefix(g*G) <= t < prefix((g+1)*G)
+    while (hi - lo > 1) {
+        int32_t mid = (lo + hi) >> 1;
+        if (tc_prefix((int64_t)mid * kGroupRows, cb) <= t) lo = mid; else hi = mid;
+    }
+    const int32_t g = lo;
+    const int32_t r0 = g * kGroupRows;
+    const int32_t gsz = min(kGroupRows, rb - r0);
+    int64_t p = t - tc_prefix(r0, cb);
+    int32_t bj = r0 / 2;  // first column block of the group
+    for (;;) {
+        // row blocks bi in [r0, r0+gsz) with floor(bi/2) <= bj
+        int32_t c = 2 * bj + 2 - r0;
+        c = c < 0 ? 0 : (c > gsz ? gsz : c);
+        if (c == gsz) {
+            *bj_out = bj + (int32_t)(p / gsz);
+            *bi_out = r0 + (int32_t)(p % gsz);
+            return;
+        }
+        if (p < c) { *bj_out = bj; *bi_out = r0 + (int32_t)p; return; }
+        p -= c;
+        ++bj;
+    }
+}
+
+struct TileInfo {
+    int b;
+    int32_t bi, bj, R, nk;
+};
+
+__device__ __forceinline__ bool next_tile(const InstState *st, const Plan *plan, int phase,
+                                          int64_t t, TileInfo *ti) {
+    if (t >= plan->total_tiles) return false;
+    int lo = 0, hi = plan->count;
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (plan->tile_off[mid] <= t) lo = mid; else hi = mid;
+    }
+    const InstState &s = st[lo];
+    ti->b = lo;
+    ti->R = phase == 0 ? s.m : s.n;
+    const int32_t K = phase == 0 ? s.n : s.m_dp;
+    ti->nk = ((K > 0 ? K : 1) + kTcK - 1) / kTcK;
+    tc_tile_coords(t - plan->tile_off[lo], ti->R, &ti->bi, &ti->bj);
+    return true;
+}
+
+struct __align__(8) SharedCtl {
+    uint64_t full[kStages];
+    uint64_t empty[kStages];
+    uint64_t tmem_full[2];
+    uint64_t tmem_empty[2];
+    uint64_t drain;
+    uint32_t tmem_base;
+    int abort;
+    float colA[kTcN];  // DP: f_j        MD: d_j
+    float colB[kTcN];  // DP: f_j - s_j  MD: unused
+    int32_t ccnt[kTcN];
+};
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_tc_contract(InstState *st, const Plan *plan, int phase, int32_t *kerr) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    // 1024-byte alignment for the swizzle atoms
+    uint8_t *smem = reinterpret_cast<uint8_t *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    SharedCtl *ctl = reinterpret_cast<SharedCtl *>(smem + kStages * kStageBytes);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    volatile int *abort = &ctl->abort;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(smem_u32(&ctl->full[s]), 1);
+            mbar_init(smem_u32(&ctl->empty[s]), 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(smem_u32(&ctl->tmem_full[a]), 1);
+            mbar_init(smem_u32(&ctl->tmem_empty[a]), kEpiThreads);
+        }
+        mbar_init(smem_u32(&ctl->drain), 1);
+        ctl->abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (threadIdx.x >= 64) {
+        for (int c = threadIdx.x - 64; c < kTcN; c += kEpiThreads) ctl->ccnt[c] = 0;
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&ctl->tmem_base)),
+                     "n"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = ctl->tmem_base;
+
+    if (warp == 0) {
+        // ------------------------------------------------ TMA producer --
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase_bit = 0;
+            int64_t issued = 0;
+            bool aborted = false;
+            const void *fenced = nullptr;
+            TileInfo ti;
+            for (int64_t t = blockIdx.x; !aborted && next_tile(st, plan, phase, t, &ti);
+                 t += gridDim.x) {
+                const InstState &s = st[ti.b];
+                const void *tmap = phase == 0 ? s.tmap_A : s.tmap_At;
+                if (tmap != fenced) {  // the maps were written to global memory by a copy
+                    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmap)
+                                 : "memory");
+                    fenced = tmap;
+                }
+                const int32_t yi = ti.bi * kTcM, yj = ti.bj * kTcN;
+                for (int32_t kb = 0; kb < ti.nk; ++kb) {
+                    if (!mbar_wait(smem_u32(&ctl->empty[stage]), phase_bit ^ 1, abort)) {
+                        aborted = true;
+                        break;
+                    }
+                    const uint32_t full = smem_u32(&ctl->full[stage]);
+                    mbar_expect_tx(full, kStageBytes);
+                    const uint32_t sa = smem_u32(smem + stage * kStageBytes);
+                    const uint32_t sb = sa + kABytes;
+                    tma_load_2d(sa, tmap, kb * kTcK, yi, full);
+                    tma_load_2d(sb, tmap, kb * kTcK, yj, full);
+                    tma_load_2d(sb + kABytes, tmap, kb * kTcK, yj + kTcM, full);
+                    ++issued;
+                    if (++stage == kStages) { stage = 0; phase_bit ^= 1; }
+                }
+            }
+            if (aborted) {  // let the loads still in flight land before exiting
+                for (int64_t k = issued > kStages ? issued - kStages : 0; k < issued; ++k)
+                    mbar_wait_ns(smem_u32(&ctl->full[k % kStages]), (uint32_t)((k / kStages) & 1),
+                                 100000000ull);
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------------------------------------------- MMA issuer --
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase_bit = 0;
+            int it = 0;
+            bool aborted = false;
+            TileInfo ti;
+            for (int64_t t = blockIdx.x; !aborted && next_tile(st, plan, phase, t, &ti);
+                 t += gridDim.x, ++it) {
+                const int acc = it & 1;
+                const uint32_t acc_phase = (it >> 1) & 1;
+                if (!mbar_wait(smem_u32(&ctl->tmem_empty[acc]), acc_phase ^ 1, abort)) {
+                    aborted = true;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = tmem + acc * kAccCols;
+                for (int32_t kb = 0; kb < ti.nk; ++kb) {
+                    if (!mbar_wait(smem_u32(&ctl->full[stage]), phase_bit, abort)) {
+                        aborted = true;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sa = smem_u32(smem + stage * kStageBytes);
+                    const uint32_t sb = sa + kABytes;
+#pragma unroll
+                    for (int k = 0; k < kTcK / 32; ++k)
+                        mma_f8(d, smem_desc(sa + 32 * k), smem_desc(sb + 32 * k),
+                               (kb > 0 || k > 0) ? 1u : 0u);
+                    mma_commit(smem_u32(&ctl->empty[stage]));
+                    if (++stage == kStages) { stage = 0; phase_bit ^= 1; }
+                }
+                if (!aborted) mma_commit(smem_u32(&ctl->tmem_full[acc]));
+            }
+            if (aborted) {  // wait for the MMAs already issued before freeing TMEM
+                mma_commit(smem_u32(&ctl->drain));
+                mbar_wait_ns(smem_u32(&ctl->drain), 0, 100000000ull);
+            }
+        }
+    } else {
+        // ------------------------------------------------------ epilogue --
+        const int q = warp & 3;  // TMEM lane quarter
+        const int et = threadIdx.x - 64;
+        int it = 0;
+        TileInfo ti;
+        for (int64_t t = blockIdx.x; next_tile(st, plan, phase, t, &ti); t += gridDim.x, ++it) {
+            InstState &s = st[ti.b];
+            const int acc = it & 1;
+            const uint32_t acc_phase = (it >> 1) & 1;
+            const int32_t R = ti.R;
+            const int32_t j0 = ti.bj * kTcN;
+            const int32_t i = ti.bi * kTcM + 32 * q + lane;
+            // stage the column data of this tile
+            epi_bar();
+            for (int c = et; c < kTcN; c += kEpiThreads) {
+                const int32_t j = j0 + c;
+                float a = 0.f, bb = 0.f;
+                if (j < R) {
+                    if (phase == 0) { a = (float)s.e_f[j]; bb = (float)(s.e_f[j] - s.e_s[j]); }
+                    else a = (float)s.v_deg[j];
+                }
+                ctl->colA[c] = a;
+                ctl->colB[c] = bb;
+            }
+            float ri_f = 0.f, ri_a = 0.f;  // DP: f_i, f_i - s_i ; MD: d_i
+            if (i < R) {
+                if (phase == 0) { ri_f = (float)s.e_f[i]; ri_a = (float)(s.e_f[i] - s.e_s[i]); }
+                else ri_f = (float)s.v_deg[i];
+            }
+            epi_bar();
+            const bool ok = epi_bar_and(mbar_wait(smem_u32(&ctl->tmem_full[acc]), acc_phase, abort));
+            if (!ok) { *abort = 1; break; }
+            tc_fence_after();
+            bool rowflag = false;
+            int32_t rowcnt = 0;
+            {
+                const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + acc * kAccCols;
+#pragma unroll 1
+                for (int ch = 0; ch < kTcN / 32; ++ch) {
+                    float v[32];
+                    tmem_ld32(taddr + ch * 32, v);
+                    uint32_t colmask = 0;
+#pragma unroll
+                    for (int c = 0; c < 32; ++c) {
+                        const int cc = ch * 32 + c;
+                        const int32_t j = j0 + cc;
+                        const bool valid = (i < j) && (j < R);
+                        const float x = v[c];
+                        if (phase == 0) {
+                            // Algorithm 1: D_ij = [f_i - (s_i - x) >= f_j]
+                            const bool dij = x + ri_a >= ctl->colA[cc];
+                            const bool dji = x + ctl->colB[cc] >= ri_f;
+                            colmask |= (uint32_t)(valid && dij) << c;
+                            rowflag |= valid && dji && !dij;
+                        } else {
+                            // Algorithm 2: D_ij = [x = d_j] and D_ji = [x = d_i, x != d_j] for i < j
+                            const bool dij = x == ctl->colA[cc];
+                            const bool dji = (x == ri_f) && !dij;
+                            colmask |= (uint32_t)(valid && dij) << c;
+                            rowcnt += (int32_t)(valid && dji);
+                        }
+                    }
+                    const uint32_t any = __reduce_or_sync(0xffffffffu, colmask);
+                    if (any) {
+                        if (phase == 0) {
+                            if ((any >> lane) & 1u) s.e_del[j0 + ch * 32 + lane] = 1;
+                        } else {
+                            uint32_t m = any;
+                            while (m) {
+                                const int c = __ffs(m) - 1;
+                                m &= m - 1;
+                                const int n1 = __popc(__ballot_sync(0xffffffffu, (colmask >> c) & 1u));
+                                if (lane == 0) atomicAdd(&ctl->ccnt[ch * 32 + c], n1);
+                            }
+                        }
+                    }
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(smem_u32(&ctl->tmem_empty[acc]));
+            if (phase == 0) {
+                if (rowflag) s.e_del[i] = 1;
+            } else {
+                if (rowcnt) atomicAdd(&s.v_cnt[i], rowcnt);
+                epi_bar();
+                for (int c = et; c < kTcN; c += kEpiThreads) {
+                    const int32_t cnt = ctl->ccnt[c];
+                    if (cnt) { atomicAdd(&s.v_cnt[j0 + c], cnt); ctl->ccnt[c] = 0; }
+                }
+            }
+        }
+    }
+    __syncwarp();
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x == 0 && *abort) atomicOr(kerr, kErrTimeout);
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "n"(kTmemCols)
+                     : "memory");
+    }
+}
+
+constexpr size_t kSmemBytes = 1024 + kStages * kStageBytes + sizeof(SharedCtl);
+
+}  // namespace
+
+// Host side ----------------------------------------------------------------
+
+static PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void *p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// 2D uint8 tensor map over a rows x pitch byte matrix, box 128 x 128 bytes,
+// 128-byte swizzle; out-of-range rows read as zero.
+bool make_operand_tmap(void *out128, const void *base, int64_t pitch, int64_t rows) {
+    PFN_cuTensorMapEncodeTiled_v12000 fn = get_encode_fn();
+    if (!fn) return false;
+    CUtensorMap m;
+    std::memset(&m, 0, sizeof(m));
+    cuuint64_t dims[2] = {(cuuint64_t)pitch, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)pitch};
+    cuuint32_t box[2] = {(cuuint32_t)kTcK, (cuuint32_t)kTcM};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(&m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void *>(base), dims, strides,
+                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return false;
+    std::memcpy(out128, &m, sizeof(m));
+    return true;
+}
+
+size_t tmap_bytes() { return sizeof(CUtensorMap); }
+
+cudaError_t prepare_tc_contract() {
+    return cudaFuncSetAttribute(k_tc_contract, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kSmemBytes);
+}
+
+cudaError_t launch_tc_contract(InstState *st, Plan *plan, int phase, int sms, int32_t *kerr,
+                               cudaStream_t s) {
+    k_tc_contract<<<sms, kThreads, kSmemBytes, s>>>(st, plan, phase, kerr);
+    return cudaGetLastError();
+}
+
+}  // namespace mhs

@@ -1,0 +1,43 @@
+// kernels.h -- launchers shared by the host driver (mhs_api.cpp) and the
+// CUDA translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "mhs_internal.h"
+
+namespace mhs {
+
+// Batch-wide totals of the last round, accumulated on the device and read
+// back once per round (the round's only device-to-host transfer).
+struct BatchCounters {
+    int32_t active;           // instances still short of their fixpoint
+    int32_t n_alive, m_alive; // summed over the batch
+    int32_t dp_deleted, md_deleted;
+    int32_t max_rounds_seen;
+    int32_t changed_any;
+    int32_t status_any;
+};
+
+cudaError_t launch_validate(InstState *st, cudaStream_t s);
+cudaError_t launch_build(InstState *st, int count, int32_t max_rounds, int64_t max_nnz,
+                         int64_t max_m, int64_t max_n, cudaStream_t s);
+// One phase of a round: phase 0 = DP (Algorithm 1), phase 1 = MD (Algorithm 2).
+cudaError_t launch_round_phase(InstState *st, Plan *plan, BatchCounters *ctr, int count,
+                               int phase, int contraction, int sms, int32_t *kerr,
+                               cudaStream_t s, cudaEvent_t ev_contract_begin,
+                               cudaEvent_t ev_contract_end);
+cudaError_t launch_alive_masks(const InstState *st, uint8_t *alive_v, uint8_t *alive_e,
+                               cudaStream_t s);
+
+// tcgen05 contraction (contract_tc.cu)
+cudaError_t launch_tc_contract(InstState *st, Plan *plan, int phase, int sms, int32_t *kerr,
+                               cudaStream_t s);
+cudaError_t prepare_tc_contract();  // once per process, before any capture
+bool make_operand_tmap(void *out128, const void *base, int64_t pitch, int64_t rows);
+size_t tmap_bytes();
+
+}  // namespace mhs

@@ -1,0 +1,781 @@
+// mhs_api.cpp -- the C ABI of include/mhs.h: validation, device memory,
+// the round driver of Algorithm 3 and result extraction.
+#include "mhs.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "mhs_internal.h"
+
+using namespace mhs;
+
+namespace {
+
+thread_local std::string g_err;
+
+mhs_status fail(mhs_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    std::vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+#define CUDA_TRY(expr)                                                                   \
+    do {                                                                                 \
+        cudaError_t e_ = (expr);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return fail(e_ == cudaErrorMemoryAllocation ? MHS_ENOMEM : MHS_ECUDA,        \
+                        "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+inline int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+inline int64_t kpad_bytes(int64_t K) { return round_up(std::max<int64_t>(K, 1), kTcK); }
+inline int64_t kpad_words(int64_t K) {
+    return round_up(std::max<int64_t>((K + 31) / 32, 1), 4);
+}
+
+// Library-owned stream-ordered memory pool (keeps freed blocks for reuse).
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[64] = {};
+
+cudaError_t pool_for(int dev, cudaMemPool_t *out) {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!g_pool[dev]) {
+        cudaMemPoolProps p;
+        std::memset(&p, 0, sizeof(p));
+        p.allocType = cudaMemAllocationTypePinned;
+        p.handleTypes = cudaMemHandleTypeNone;
+        p.location.type = cudaMemLocationTypeDevice;
+        p.location.id = dev;
+        cudaError_t e = cudaMemPoolCreate(&g_pool[dev], &p);
+        if (e != cudaSuccess) return e;
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(g_pool[dev], cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    *out = g_pool[dev];
+    return cudaSuccess;
+}
+
+// Sub-allocation plan of one arena.
+struct Arena {
+    int64_t bytes = 0;
+    int64_t take(int64_t nbytes) {
+        int64_t off = bytes;
+        bytes += round_up(std::max<int64_t>(nbytes, 1), 256);
+        return off;
+    }
+};
+
+struct HostInst {  // per-instance host bookkeeping
+    int32_t n0, m0;
+    int64_t nnz0;
+    int64_t k;
+};
+
+}  // namespace
+
+struct mhs_instance {
+    int device = 0;
+    int sms = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    mhs_options opt{};
+    int contraction = kFp8;
+    int32_t count = 0;
+    std::vector<HostInst> hinst;
+    std::vector<InstState> hstate;  // host mirror: pointers and static fields
+    uint8_t *arena = nullptr;       // all device memory of the instance
+    InstState *dstate = nullptr;
+    Plan *dplan = nullptr;
+    BatchCounters *dctr = nullptr;
+    int32_t *dkerr = nullptr;
+    BatchCounters *hctr = nullptr;  // pinned
+    int32_t *hkerr = nullptr;       // pinned
+    int64_t max_nnz = 0, max_m = 0, max_n = 0;
+    // arena offsets of the batch-wide input arrays
+    int64_t in_eptr = 0, in_evtx = 0, in_f = 0;
+    int64_t sum_m1 = 0, sum_nnz = 0, sum_m = 0;
+    // round graph
+    cudaGraphExec_t graph = nullptr;
+    // timing
+    bool timing = false;
+    cudaEvent_t ev[6] = {};
+    float last_ms[4] = {0, 0, 0, 0};
+    int32_t rounds_done = 0;
+};
+
+namespace {
+
+void destroy(mhs_instance *h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    for (auto &e : h->ev)
+        if (e) cudaEventDestroy(e);
+    if (h->arena) cudaFreeAsync(h->arena, h->stream);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->hctr) cudaFreeHost(h->hctr);
+    if (h->hkerr) cudaFreeHost(h->hkerr);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+mhs_status check_options(const mhs_options *opt, mhs_options *out) {
+    mhs_default_options(out);
+    if (!opt) return MHS_OK;
+    *out = *opt;
+    if (out->contraction < 0 || out->contraction > 2)
+        return fail(MHS_EINVAL, "options.contraction must be 0 (auto), 1 (fp8) or 2 (popcount)");
+    if (out->max_rounds < 0) return fail(MHS_EINVAL, "options.max_rounds must be >= 0");
+    for (int i = 0; i < 5; ++i)
+        if (out->reserved[i] != 0) return fail(MHS_EINVAL, "options.reserved must be zero");
+    return MHS_OK;
+}
+
+// Host-side structural validation of one instance's CSR.
+mhs_status validate_host(int32_t n, int32_t m, const int64_t *eptr64, const int32_t *eptr32,
+                         const int32_t *evtx, const int32_t *demand, std::vector<int32_t> &mark,
+                         int32_t tag_base, const char *what) {
+    if (n < 0 || m < 0) return fail(MHS_EINVAL, "%s: n and m must be >= 0", what);
+    if (n >= (1 << 24) || m >= (1 << 24))
+        return fail(MHS_EINVAL, "%s: n and m must be < 2^24 (exact FP32 counts)", what);
+    auto ptr = [&](int64_t i) -> int64_t { return eptr64 ? eptr64[i] : eptr32[i]; };
+    if ((size_t)n > mark.size()) mark.assign((size_t)n, -1);
+    for (int32_t e = 0; e < m; ++e) {
+        int64_t a = ptr(e), b = ptr(e + 1);
+        if (b < a) return fail(MHS_EINVAL, "%s: edge_ptr decreases at hyperedge %d", what, e);
+        if (b - a > (1ll << 24)) return fail(MHS_EINVAL, "%s: hyperedge %d too large", what, e);
+        if (demand[e] < 1) return fail(MHS_EINVAL, "%s: demand of hyperedge %d is < 1", what, e);
+        for (int64_t p = a; p < b; ++p) {
+            int32_t v = evtx[p];
+            if (v < 0 || v >= n)
+                return fail(MHS_EINVAL, "%s: hyperedge %d has vertex id %d outside [0,%d)", what,
+                            e, v, n);
+            if (mark[v] == tag_base + e)
+                return fail(MHS_EINVAL, "%s: hyperedge %d lists vertex %d twice", what, e, v);
+            mark[v] = tag_base + e;
+        }
+    }
+    return MHS_OK;
+}
+
+struct Layout {  // byte offsets inside the arena for one instance
+    int64_t eptr, evtx, f, vptr, vedg;
+    int64_t v_o2c, v_c2o, e_o2c, e_c2o, e_f, e_s, v_deg, v_maxf, v_cnt, e_del, v_del;
+    int64_t A, At, Ab, Atb;
+};
+
+mhs_status create(int32_t count, const int32_t *n, const int32_t *m, const int64_t *nnz,
+                  const int64_t *k, const mhs_options *opt_in, void *cuda_stream,
+                  mhs_instance **out, std::vector<Layout> &lay, int64_t &glob_off) {
+    mhs_options opt;
+    mhs_status st = check_options(opt_in, &opt);
+    if (st) return st;
+    auto *h = new mhs_instance();
+    h->opt = opt;
+    h->contraction = opt.contraction == kPopcount ? kPopcount : kFp8;
+    h->count = count;
+    if (cudaGetDevice(&h->device) != cudaSuccess) {
+        destroy(h);
+        return fail(MHS_ECUDA, "no CUDA device");
+    }
+    cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (cuda_stream) {
+        h->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            destroy(h);
+            return fail(MHS_ECUDA, "cudaStreamCreate failed");
+        }
+        h->own_stream = true;
+    }
+    const bool dense = h->contraction == kFp8;
+    Arena ar;
+    lay.resize(count);
+    h->hinst.resize(count);
+    // inputs are laid out array by array over the batch, so that a batch is
+    // uploaded with one copy per array
+    int64_t sum_m1 = 0, sum_z = 0, sum_m = 0;
+    for (int b = 0; b < count; ++b) { sum_m1 += m[b] + 1; sum_z += nnz[b]; sum_m += m[b]; }
+    const int64_t off_eptr = ar.take(4 * sum_m1);
+    const int64_t off_evtx = ar.take(4 * sum_z);
+    const int64_t off_f = ar.take(4 * sum_m);
+    h->in_eptr = off_eptr;
+    h->in_evtx = off_evtx;
+    h->in_f = off_f;
+    h->sum_m1 = sum_m1;
+    h->sum_nnz = sum_z;
+    h->sum_m = sum_m;
+    int64_t c_m1 = 0, c_z = 0, c_m = 0;
+    for (int b = 0; b < count; ++b) {
+        Layout &L = lay[b];
+        const int64_t n0 = n[b], m0 = m[b], z = nnz[b];
+        h->hinst[b] = {n[b], m[b], z, k[b]};
+        h->max_nnz = std::max(h->max_nnz, z);
+        h->max_m = std::max(h->max_m, m0);
+        h->max_n = std::max(h->max_n, n0);
+        L.eptr = off_eptr + 4 * c_m1;
+        L.evtx = off_evtx + 4 * c_z;
+        L.f = off_f + 4 * c_m;
+        c_m1 += m0 + 1;
+        c_z += z;
+        c_m += m0;
+        L.vptr = ar.take(4 * (n0 + 1));
+        L.vedg = ar.take(4 * z);
+        L.v_o2c = ar.take(4 * n0);
+        L.v_c2o = ar.take(4 * n0);
+        L.e_o2c = ar.take(4 * m0);
+        L.e_c2o = ar.take(4 * m0);
+        L.e_f = ar.take(4 * m0);
+        L.e_s = ar.take(4 * m0);
+        L.v_deg = ar.take(4 * n0);
+        L.v_maxf = ar.take(4 * n0);
+        L.v_cnt = ar.take(4 * n0);
+        L.e_del = ar.take(m0);
+        L.v_del = ar.take(n0);
+        const int64_t arows = round_up(std::max<int64_t>(m0, 1), kRowAlign);
+        const int64_t atrows = round_up(std::max<int64_t>(n0, 1), kRowAlign);
+        if (dense) {
+            L.A = ar.take(arows * kpad_bytes(n0));
+            L.At = ar.take(atrows * kpad_bytes(m0));
+            L.Ab = L.Atb = -1;
+        } else {
+            L.Ab = ar.take(arows * kpad_words(n0) * 4);
+            L.Atb = ar.take(atrows * kpad_words(m0) * 4);
+            L.A = L.At = -1;
+        }
+    }
+    // batch-level objects
+    const int64_t off_state = ar.take((int64_t)sizeof(InstState) * count);
+    const int64_t off_plan = ar.take(sizeof(Plan));
+    const int64_t off_rowoff = ar.take(4 * (int64_t)(count + 1));
+    const int64_t off_tileoff = ar.take(8 * (int64_t)(count + 1));
+    const int64_t off_ctr = ar.take(sizeof(BatchCounters));
+    const int64_t off_kerr = ar.take(4);
+    const int64_t off_tmaps = ar.take(dense ? (int64_t)tmap_bytes() * 2 * count : 0);
+    glob_off = off_tmaps;
+
+    cudaMemPool_t pool;
+    cudaError_t ce = pool_for(h->device, &pool);
+    if (ce == cudaSuccess)
+        ce = cudaMallocFromPoolAsync(reinterpret_cast<void **>(&h->arena), (size_t)ar.bytes, pool,
+                                     h->stream);
+    if (ce != cudaSuccess) {
+        destroy(h);
+        return fail(ce == cudaErrorMemoryAllocation ? MHS_ENOMEM : MHS_ECUDA,
+                    "device allocation of %lld bytes failed: %s", (long long)ar.bytes,
+                    cudaGetErrorString(ce));
+    }
+    uint8_t *base = h->arena;
+    h->dstate = reinterpret_cast<InstState *>(base + off_state);
+    h->dplan = reinterpret_cast<Plan *>(base + off_plan);
+    h->dctr = reinterpret_cast<BatchCounters *>(base + off_ctr);
+    h->dkerr = reinterpret_cast<int32_t *>(base + off_kerr);
+    if (cudaMallocHost(&h->hctr, sizeof(BatchCounters)) != cudaSuccess ||
+        cudaMallocHost(&h->hkerr, sizeof(int32_t)) != cudaSuccess) {
+        destroy(h);
+        return fail(MHS_ENOMEM, "pinned host allocation failed");
+    }
+    h->hstate.resize(count);
+    for (int b = 0; b < count; ++b) {
+        const Layout &L = lay[b];
+        InstState s;
+        std::memset(&s, 0, sizeof(s));
+        s.n0 = n[b];
+        s.m0 = m[b];
+        s.nnz0 = nnz[b];
+        s.k = k[b];
+        s.eptr = reinterpret_cast<int32_t *>(base + L.eptr);
+        s.evtx = reinterpret_cast<int32_t *>(base + L.evtx);
+        s.f = reinterpret_cast<int32_t *>(base + L.f);
+        s.vptr = reinterpret_cast<int32_t *>(base + L.vptr);
+        s.vedg = reinterpret_cast<int32_t *>(base + L.vedg);
+        s.v_o2c = reinterpret_cast<int32_t *>(base + L.v_o2c);
+        s.v_c2o = reinterpret_cast<int32_t *>(base + L.v_c2o);
+        s.e_o2c = reinterpret_cast<int32_t *>(base + L.e_o2c);
+        s.e_c2o = reinterpret_cast<int32_t *>(base + L.e_c2o);
+        s.e_f = reinterpret_cast<int32_t *>(base + L.e_f);
+        s.e_s = reinterpret_cast<int32_t *>(base + L.e_s);
+        s.v_deg = reinterpret_cast<int32_t *>(base + L.v_deg);
+        s.v_maxf = reinterpret_cast<int32_t *>(base + L.v_maxf);
+        s.v_cnt = reinterpret_cast<int32_t *>(base + L.v_cnt);
+        s.e_del = base + L.e_del;
+        s.v_del = base + L.v_del;
+        const int64_t arows = round_up(std::max<int64_t>(m[b], 1), kRowAlign);
+        const int64_t atrows = round_up(std::max<int64_t>(n[b], 1), kRowAlign);
+        s.A_rows = (int32_t)arows;
+        s.At_rows = (int32_t)atrows;
+        if (dense) {
+            s.A = base + L.A;
+            s.At = base + L.At;
+            s.A_pitch = kpad_bytes(n[b]);
+            s.At_pitch = kpad_bytes(m[b]);
+            uint8_t *tm = base + off_tmaps + (int64_t)tmap_bytes() * 2 * b;
+            s.tmap_A = tm;
+            s.tmap_At = tm + tmap_bytes();
+        } else {
+            s.Ab = reinterpret_cast<uint32_t *>(base + L.Ab);
+            s.Atb = reinterpret_cast<uint32_t *>(base + L.Atb);
+            s.Ab_pitch = (int32_t)kpad_words(n[b]);
+            s.Atb_pitch = (int32_t)kpad_words(m[b]);
+        }
+        h->hstate[b] = s;
+    }
+    // device plan header
+    Plan p;
+    std::memset(&p, 0, sizeof(p));
+    p.count = count;
+    p.row_off = reinterpret_cast<int32_t *>(base + off_rowoff);
+    p.tile_off = reinterpret_cast<int64_t *>(base + off_tileoff);
+    ce = cudaMemcpyAsync(h->dplan, &p, sizeof(p), cudaMemcpyHostToDevice, h->stream);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(h->dkerr, 0, 4, h->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);  // p is a stack object
+    if (ce != cudaSuccess) {
+        destroy(h);
+        return fail(MHS_ECUDA, "setup copy failed: %s", cudaGetErrorString(ce));
+    }
+    *out = h;
+    return MHS_OK;
+}
+
+// Tensor maps (host encode, one copy to the device), state upload, and the
+// device-side build of the vertex -> hyperedge lists and id maps.
+mhs_status finish_load(mhs_instance *h, int64_t tmap_off) {
+    const bool dense = h->contraction == kFp8;
+    if (dense) {
+        CUDA_TRY(prepare_tc_contract());
+        std::vector<uint8_t> maps(tmap_bytes() * 2 * h->count);
+        for (int b = 0; b < h->count; ++b) {
+            const InstState &s = h->hstate[b];
+            if (!make_operand_tmap(maps.data() + tmap_bytes() * 2 * b, s.A, s.A_pitch, s.A_rows) ||
+                !make_operand_tmap(maps.data() + tmap_bytes() * (2 * b + 1), s.At, s.At_pitch,
+                                   s.At_rows))
+                return fail(MHS_ECUDA, "cuTensorMapEncodeTiled failed for instance %d", b);
+        }
+        CUDA_TRY(cudaMemcpyAsync(h->arena + tmap_off, maps.data(), maps.size(),
+                                 cudaMemcpyHostToDevice, h->stream));
+        CUDA_TRY(cudaStreamSynchronize(h->stream));  // `maps` is pageable and local
+    }
+    CUDA_TRY(cudaMemcpyAsync(h->dstate, h->hstate.data(), sizeof(InstState) * h->count,
+                             cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(launch_build(h->dstate, h->count, h->opt.max_rounds, h->max_nnz, h->max_m,
+                          h->max_n, h->stream));
+    return MHS_OK;
+}
+
+mhs_status check_device_status(mhs_instance *h) {
+    if (*h->hkerr) return fail(MHS_EDEVICE, "kernel reported error status 0x%x", *h->hkerr);
+    if (h->hctr->status_any)
+        return fail(MHS_EDEVICE, "instance reported error status 0x%x", h->hctr->status_any);
+    return MHS_OK;
+}
+
+// Enqueue one round (DP phase, MD phase, counters to pinned host memory).
+cudaError_t enqueue_round(mhs_instance *h, bool with_events) {
+    cudaError_t e = launch_round_phase(h->dstate, h->dplan, h->dctr, h->count, 0, h->contraction,
+                                       h->sms, h->dkerr, h->stream,
+                                       with_events ? h->ev[0] : nullptr,
+                                       with_events ? h->ev[1] : nullptr);
+    if (e != cudaSuccess) return e;
+    e = launch_round_phase(h->dstate, h->dplan, h->dctr, h->count, 1, h->contraction, h->sms,
+                           h->dkerr, h->stream, with_events ? h->ev[2] : nullptr,
+                           with_events ? h->ev[3] : nullptr);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(h->hctr, h->dctr, sizeof(BatchCounters), cudaMemcpyDeviceToHost,
+                        h->stream);
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyAsync(h->hkerr, h->dkerr, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                           h->stream);
+}
+
+mhs_status run_rounds(mhs_instance *h, int32_t limit, mhs_round_stats *stats) {
+    if (h->timing) {
+        for (auto &e : h->ev)
+            if (!e) CUDA_TRY(cudaEventCreate(&e));
+        for (float &x : h->last_ms) x = 0.f;
+    }
+    if (h->opt.use_graphs && !h->timing && !h->graph) {
+        cudaGraph_t g;
+        CUDA_TRY(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = enqueue_round(h, false);
+        cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
+        if (e != cudaSuccess || e2 != cudaSuccess)
+            return fail(MHS_ECUDA, "graph capture failed: %s",
+                        cudaGetErrorString(e != cudaSuccess ? e : e2));
+        e = cudaGraphInstantiate(&h->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return fail(MHS_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    }
+    int32_t done = 0;
+    bool any = false;
+    while (limit <= 0 || done < limit) {
+        if (h->timing) {
+            CUDA_TRY(cudaEventRecord(h->ev[4], h->stream));
+            CUDA_TRY(enqueue_round(h, true));
+            CUDA_TRY(cudaEventRecord(h->ev[5], h->stream));
+        } else if (h->graph) {
+            CUDA_TRY(cudaGraphLaunch(h->graph, h->stream));
+        } else {
+            CUDA_TRY(enqueue_round(h, false));
+        }
+        CUDA_TRY(cudaStreamSynchronize(h->stream));
+        any = true;
+        ++done;
+        if (h->timing) {
+            float a = 0, b = 0, t = 0;
+            cudaEventElapsedTime(&a, h->ev[0], h->ev[1]);
+            cudaEventElapsedTime(&b, h->ev[2], h->ev[3]);
+            cudaEventElapsedTime(&t, h->ev[4], h->ev[5]);
+            h->last_ms[0] += a;
+            h->last_ms[1] += b;
+            h->last_ms[3] += t;
+            h->last_ms[2] += t - a - b;
+        }
+        mhs_status st = check_device_status(h);
+        if (st) return st;
+        if (h->hctr->active == 0) break;
+    }
+    if (stats) {
+        if (any) {
+            stats->n_alive = h->hctr->n_alive;
+            stats->m_alive = h->hctr->m_alive;
+            stats->rounds = h->hctr->max_rounds_seen;
+            stats->changed = h->hctr->changed_any;
+            stats->dp_deleted = h->hctr->dp_deleted;
+            stats->md_deleted = h->hctr->md_deleted;
+        } else {
+            std::memset(stats, 0, sizeof(*stats));
+        }
+    }
+    return MHS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mhs_status mhs_default_options(mhs_options *opt) {
+    if (!opt) return fail(MHS_EINVAL, "opt is NULL");
+    std::memset(opt, 0, sizeof(*opt));
+    opt->contraction = MHS_CONTRACT_AUTO;
+    opt->max_rounds = 0;
+    opt->use_graphs = 1;
+    return MHS_OK;
+}
+
+mhs_status mhs_load(int32_t n, int32_t m, const int32_t *edge_ptr, const int32_t *edge_vtx,
+                    const int32_t *demand, int64_t k, const mhs_options *opt, void *cuda_stream,
+                    mhs_instance **out) {
+    if (!out) return fail(MHS_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!edge_ptr || (m > 0 && !demand)) return fail(MHS_EINVAL, "NULL input array");
+    if (m >= 0 && edge_ptr[0] != 0) return fail(MHS_EINVAL, "edge_ptr[0] must be 0");
+    std::vector<int32_t> mark;
+    if (m > 0 && edge_ptr[m] > 0 && !edge_vtx) return fail(MHS_EINVAL, "edge_vtx is NULL");
+    mhs_status st = validate_host(n, m, nullptr, edge_ptr, edge_vtx, demand, mark, 0, "instance");
+    if (st) return st;
+    int64_t nnz = edge_ptr[m];
+    std::vector<Layout> lay;
+    int64_t tmoff = 0;
+    mhs_instance *h = nullptr;
+    st = create(1, &n, &m, &nnz, &k, opt, cuda_stream, &h, lay, tmoff);
+    if (st) return st;
+    const InstState &s = h->hstate[0];
+    cudaError_t e = cudaMemcpyAsync(const_cast<int32_t *>(s.eptr), edge_ptr, 4 * ((size_t)m + 1),
+                                    cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess && nnz > 0)
+        e = cudaMemcpyAsync(const_cast<int32_t *>(s.evtx), edge_vtx, 4 * (size_t)nnz,
+                            cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess && m > 0)
+        e = cudaMemcpyAsync(const_cast<int32_t *>(s.f), demand, 4 * (size_t)m,
+                            cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) {
+        destroy(h);
+        return fail(MHS_ECUDA, "input copy failed: %s", cudaGetErrorString(e));
+    }
+    st = finish_load(h, tmoff);
+    if (st == MHS_OK && cudaStreamSynchronize(h->stream) != cudaSuccess)
+        st = fail(MHS_ECUDA, "load failed: %s", cudaGetErrorString(cudaGetLastError()));
+    if (st) {
+        destroy(h);
+        return st;
+    }
+    *out = h;
+    return MHS_OK;
+}
+
+mhs_status mhs_load_device(int32_t n, int32_t m, const int32_t *edge_ptr, const int32_t *edge_vtx,
+                           const int32_t *demand, int64_t k, const mhs_options *opt,
+                           void *cuda_stream, mhs_instance **out) {
+    if (!out) return fail(MHS_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n < 0 || m < 0) return fail(MHS_EINVAL, "n and m must be >= 0");
+    if (n >= (1 << 24) || m >= (1 << 24)) return fail(MHS_EINVAL, "n and m must be < 2^24");
+    if (!edge_ptr || (m > 0 && !demand)) return fail(MHS_EINVAL, "NULL input array");
+    cudaStream_t cs = static_cast<cudaStream_t>(cuda_stream);
+    int32_t nnz32 = 0;
+    CUDA_TRY(cudaMemcpyAsync(&nnz32, edge_ptr + m, 4, cudaMemcpyDeviceToHost, cs));
+    CUDA_TRY(cudaStreamSynchronize(cs));
+    if (nnz32 < 0) return fail(MHS_EINVAL, "edge_ptr[m] < 0");
+    if (nnz32 > 0 && !edge_vtx) return fail(MHS_EINVAL, "edge_vtx is NULL");
+    int64_t nnz = nnz32;
+    std::vector<Layout> lay;
+    int64_t tmoff = 0;
+    mhs_instance *h = nullptr;
+    mhs_status st = create(1, &n, &m, &nnz, &k, opt, cuda_stream, &h, lay, tmoff);
+    if (st) return st;
+    InstState &s = h->hstate[0];
+    cudaError_t e = cudaMemcpyAsync(const_cast<int32_t *>(s.eptr), edge_ptr, 4 * ((size_t)m + 1),
+                                    cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess && nnz > 0)
+        e = cudaMemcpyAsync(const_cast<int32_t *>(s.evtx), edge_vtx, 4 * (size_t)nnz,
+                            cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess && m > 0)
+        e = cudaMemcpyAsync(const_cast<int32_t *>(s.f), demand, 4 * (size_t)m,
+                            cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->dstate, h->hstate.data(), sizeof(InstState), cudaMemcpyHostToDevice,
+                            h->stream);
+    if (e == cudaSuccess) e = launch_validate(h->dstate, h->stream);
+    int32_t status = 0;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&status, &h->dstate->status, 4, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        destroy(h);
+        return fail(MHS_ECUDA, "device load failed: %s", cudaGetErrorString(e));
+    }
+    if (status) {
+        destroy(h);
+        return fail(MHS_EINVAL, "malformed device instance (status 0x%x: %s)", status,
+                    (status & kErrBadVertex) ? "vertex id out of range" : "bad edge_ptr");
+    }
+    st = finish_load(h, tmoff);
+    if (st == MHS_OK && cudaStreamSynchronize(h->stream) != cudaSuccess)
+        st = fail(MHS_ECUDA, "load failed");
+    if (st) {
+        destroy(h);
+        return st;
+    }
+    *out = h;
+    return MHS_OK;
+}
+
+mhs_status mhs_load_batch(int32_t count, const int32_t *n, const int32_t *m,
+                          const int64_t *edge_ptr, const int32_t *edge_vtx, const int32_t *demand,
+                          const int64_t *k, const mhs_options *opt, void *cuda_stream,
+                          mhs_instance **out) {
+    if (!out) return fail(MHS_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (count < 1 || count > (1 << 20)) return fail(MHS_EINVAL, "count must be in [1, 2^20]");
+    if (!n || !m || !edge_ptr || !k) return fail(MHS_EINVAL, "NULL input array");
+    std::vector<int64_t> eoff(count + 1, 0), nnz(count);
+    for (int b = 0; b < count; ++b) {
+        if (m[b] < 0) return fail(MHS_EINVAL, "instance %d: m < 0", b);
+        eoff[b + 1] = eoff[b] + m[b];
+    }
+    if (edge_ptr[0] != 0) return fail(MHS_EINVAL, "edge_ptr[0] must be 0");
+    if (eoff[count] > 0 && !demand) return fail(MHS_EINVAL, "demand is NULL");
+    std::vector<int32_t> mark;
+    int32_t tag = 0;
+    for (int b = 0; b < count; ++b) {
+        const int64_t e0 = eoff[b];
+        nnz[b] = edge_ptr[e0 + m[b]] - edge_ptr[e0];
+        if (nnz[b] > 0 && !edge_vtx) return fail(MHS_EINVAL, "edge_vtx is NULL");
+        char what[64];
+        std::snprintf(what, sizeof(what), "instance %d", b);
+        // validate against the global pointer array, vertex ids local
+        if (n[b] < 0) return fail(MHS_EINVAL, "%s: n < 0", what);
+        if ((size_t)n[b] > mark.size()) mark.resize((size_t)n[b], -1);
+        std::fill(mark.begin(), mark.begin() + n[b], -1);
+        mhs_status st = validate_host(n[b], m[b], edge_ptr + e0, nullptr, edge_vtx, demand + e0,
+                                      mark, tag, what);
+        if (st) return st;
+        if (nnz[b] >= (1ll << 31)) return fail(MHS_EINVAL, "%s: too many incidences", what);
+    }
+    std::vector<Layout> lay;
+    int64_t tmoff = 0;
+    mhs_instance *h = nullptr;
+    mhs_status st = create(count, n, m, nnz.data(), k, opt, cuda_stream, &h, lay, tmoff);
+    if (st) return st;
+    // one copy per input array: local int32 offsets, vertex ids, demands
+    std::vector<int32_t> local_ptr((size_t)h->sum_m1);
+    {
+        size_t w = 0;
+        for (int b = 0; b < count; ++b) {
+            const int64_t e0 = eoff[b];
+            for (int32_t i = 0; i <= m[b]; ++i)
+                local_ptr[w++] = (int32_t)(edge_ptr[e0 + i] - edge_ptr[e0]);
+        }
+    }
+    cudaError_t e = cudaMemcpyAsync(h->arena + h->in_eptr, local_ptr.data(), 4 * local_ptr.size(),
+                                    cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess && h->sum_nnz > 0)
+        e = cudaMemcpyAsync(h->arena + h->in_evtx, edge_vtx, 4 * (size_t)h->sum_nnz,
+                            cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess && h->sum_m > 0)
+        e = cudaMemcpyAsync(h->arena + h->in_f, demand, 4 * (size_t)h->sum_m,
+                            cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);  // local_ptr is pageable
+    if (e != cudaSuccess) {
+        destroy(h);
+        return fail(MHS_ECUDA, "input copy failed: %s", cudaGetErrorString(e));
+    }
+    st = finish_load(h, tmoff);
+    if (st == MHS_OK && cudaStreamSynchronize(h->stream) != cudaSuccess)
+        st = fail(MHS_ECUDA, "load failed");
+    if (st) {
+        destroy(h);
+        return st;
+    }
+    *out = h;
+    return MHS_OK;
+}
+
+int32_t mhs_count(const mhs_instance *inst) { return inst ? inst->count : 0; }
+
+mhs_status mhs_reduce_round(mhs_instance *inst, mhs_round_stats *stats) {
+    if (!inst) return fail(MHS_EINVAL, "instance is NULL");
+    return run_rounds(inst, 1, stats);
+}
+
+mhs_status mhs_kernelize(mhs_instance *inst, mhs_round_stats *stats) {
+    if (!inst) return fail(MHS_EINVAL, "instance is NULL");
+    return run_rounds(inst, 0, stats);
+}
+
+mhs_status mhs_result_at(const mhs_instance *inst, int32_t index, int32_t *vtx_out,
+                         int32_t vtx_cap, int32_t *n_out, int32_t *edge_out, int32_t *demand_out,
+                         int32_t edge_cap, int32_t *m_out, int64_t *k_out, int32_t *rounds_out) {
+    if (!inst) return fail(MHS_EINVAL, "instance is NULL");
+    if (index < 0 || index >= inst->count) return fail(MHS_EINVAL, "index out of range");
+    InstState s;
+    cudaStream_t cs = inst->stream;
+    CUDA_TRY(cudaMemcpyAsync(&s, inst->dstate + index, sizeof(s), cudaMemcpyDeviceToHost, cs));
+    CUDA_TRY(cudaStreamSynchronize(cs));
+    if (n_out) *n_out = s.n;
+    if (m_out) *m_out = s.m;
+    if (k_out) *k_out = s.k;
+    if (rounds_out) *rounds_out = s.rounds;
+    if (s.status) return fail(MHS_EDEVICE, "instance %d error status 0x%x", index, s.status);
+    if ((vtx_out && vtx_cap < s.n) || ((edge_out || demand_out) && edge_cap < s.m))
+        return fail(MHS_EINVAL, "output capacity too small (need %d vertices, %d edges)", s.n,
+                    s.m);
+    if (vtx_out && s.n > 0)
+        CUDA_TRY(cudaMemcpyAsync(vtx_out, s.v_c2o, 4 * (size_t)s.n, cudaMemcpyDeviceToHost, cs));
+    std::vector<int32_t> eids;
+    int32_t *eo = edge_out;
+    if (!eo && demand_out) {
+        eids.resize(std::max(s.m, 1));
+        eo = eids.data();
+    }
+    if (eo && s.m > 0)
+        CUDA_TRY(cudaMemcpyAsync(eo, s.e_c2o, 4 * (size_t)s.m, cudaMemcpyDeviceToHost, cs));
+    std::vector<int32_t> f;
+    if (demand_out && s.m > 0) {
+        f.resize(s.m0);
+        CUDA_TRY(cudaMemcpyAsync(f.data(), s.f, 4 * (size_t)s.m0, cudaMemcpyDeviceToHost, cs));
+    }
+    CUDA_TRY(cudaStreamSynchronize(cs));
+    if (demand_out)
+        for (int32_t i = 0; i < s.m; ++i) demand_out[i] = f[eo[i]];
+    return MHS_OK;
+}
+
+mhs_status mhs_result(const mhs_instance *inst, int32_t *vtx_out, int32_t vtx_cap, int32_t *n_out,
+                      int32_t *edge_out, int32_t *demand_out, int32_t edge_cap, int32_t *m_out,
+                      int64_t *k_out, int32_t *rounds_out) {
+    return mhs_result_at(inst, 0, vtx_out, vtx_cap, n_out, edge_out, demand_out, edge_cap, m_out,
+                         k_out, rounds_out);
+}
+
+mhs_status mhs_result_device(const mhs_instance *inst, int32_t index, uint8_t *alive_v,
+                             uint8_t *alive_e) {
+    if (!inst) return fail(MHS_EINVAL, "instance is NULL");
+    if (index < 0 || index >= inst->count) return fail(MHS_EINVAL, "index out of range");
+    if (!alive_v || !alive_e) return fail(MHS_EINVAL, "NULL output");
+    CUDA_TRY(launch_alive_masks(inst->dstate + index, alive_v, alive_e, inst->stream));
+    return MHS_OK;
+}
+
+mhs_status mhs_export(const mhs_instance *inst, int32_t index, int32_t *edge_ptr_out,
+                      int32_t edge_cap, int32_t *edge_vtx_out, int64_t nnz_cap,
+                      int32_t *demand_out, int32_t *n_out, int32_t *m_out, int64_t *nnz_out) {
+    if (!inst) return fail(MHS_EINVAL, "instance is NULL");
+    if (index < 0 || index >= inst->count) return fail(MHS_EINVAL, "index out of range");
+    InstState s;
+    cudaStream_t cs = inst->stream;
+    CUDA_TRY(cudaMemcpyAsync(&s, inst->dstate + index, sizeof(s), cudaMemcpyDeviceToHost, cs));
+    CUDA_TRY(cudaStreamSynchronize(cs));
+    std::vector<int32_t> eptr(s.m0 + 1), evtx(std::max<int64_t>(s.nnz0, 1)), f(std::max(s.m0, 1)),
+        vmap(std::max(s.n0, 1)), ec2o(std::max(s.m, 1));
+    CUDA_TRY(cudaMemcpyAsync(eptr.data(), s.eptr, 4 * ((size_t)s.m0 + 1), cudaMemcpyDeviceToHost, cs));
+    if (s.nnz0 > 0)
+        CUDA_TRY(cudaMemcpyAsync(evtx.data(), s.evtx, 4 * (size_t)s.nnz0, cudaMemcpyDeviceToHost, cs));
+    if (s.m0 > 0)
+        CUDA_TRY(cudaMemcpyAsync(f.data(), s.f, 4 * (size_t)s.m0, cudaMemcpyDeviceToHost, cs));
+    if (s.n0 > 0)
+        CUDA_TRY(cudaMemcpyAsync(vmap.data(), s.v_o2c, 4 * (size_t)s.n0, cudaMemcpyDeviceToHost, cs));
+    if (s.m > 0)
+        CUDA_TRY(cudaMemcpyAsync(ec2o.data(), s.e_c2o, 4 * (size_t)s.m, cudaMemcpyDeviceToHost, cs));
+    CUDA_TRY(cudaStreamSynchronize(cs));
+    int64_t nnz = 0;
+    for (int32_t i = 0; i < s.m; ++i) {
+        const int32_t e = ec2o[i];
+        for (int32_t p = eptr[e]; p < eptr[e + 1]; ++p) nnz += vmap[evtx[p]] >= 0;
+    }
+    if (n_out) *n_out = s.n;
+    if (m_out) *m_out = s.m;
+    if (nnz_out) *nnz_out = nnz;
+    if (!edge_ptr_out && !edge_vtx_out && !demand_out) return MHS_OK;
+    if (edge_cap < s.m || nnz_cap < nnz)
+        return fail(MHS_EINVAL, "export capacity too small (need %d edges, %lld incidences)", s.m,
+                    (long long)nnz);
+    int64_t w = 0;
+    if (edge_ptr_out) edge_ptr_out[0] = 0;
+    for (int32_t i = 0; i < s.m; ++i) {
+        const int32_t e = ec2o[i];
+        for (int32_t p = eptr[e]; p < eptr[e + 1]; ++p) {
+            const int32_t c = vmap[evtx[p]];
+            if (c >= 0) {
+                if (edge_vtx_out) edge_vtx_out[w] = c;
+                ++w;
+            }
+        }
+        if (edge_ptr_out) edge_ptr_out[i + 1] = (int32_t)w;
+        if (demand_out) demand_out[i] = f[e];
+    }
+    return MHS_OK;
+}
+
+mhs_status mhs_set_timing(mhs_instance *inst, int32_t enable) {
+    if (!inst) return fail(MHS_EINVAL, "instance is NULL");
+    inst->timing = enable != 0;
+    return MHS_OK;
+}
+
+mhs_status mhs_last_timing(const mhs_instance *inst, float *ms4) {
+    if (!inst || !ms4) return fail(MHS_EINVAL, "NULL argument");
+    std::memcpy(ms4, inst->last_ms, sizeof(inst->last_ms));
+    return MHS_OK;
+}
+
+void mhs_free(mhs_instance *inst) { destroy(inst); }
+
+const char *mhs_last_error(void) { return g_err.c_str(); }
+
+const char *mhs_version(void) { return "mhs-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

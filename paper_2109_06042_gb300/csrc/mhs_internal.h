@@ -1,0 +1,113 @@
+// mhs_internal.h -- device-resident state shared by the kernels and the host driver.
+//
+// One InstState per instance lives in device memory.  Every kernel reads the
+// current sizes from it, so the host never needs them to size a launch: all
+// launches use fixed persistent grids and a round can be captured as one
+// CUDA graph for any batch.
+//
+// Ids.  "Original" ids are the input ids.  "Current" ids number the items
+// still alive, in input order (compaction is order-preserving), so comparing
+// current ids is the lowest-index tie-break of Algorithms 1 and 2.
+#pragma once
+
+#include <cstdint>
+
+namespace mhs {
+
+// Tile shapes.
+constexpr int kPopTile = 64;     // popcount contraction: 64 x 64 pair tiles
+constexpr int kTcM = 128;        // tcgen05 contraction: 128 rows (i) ...
+constexpr int kTcN = 256;        // ... x 256 columns (j) per tile
+constexpr int kTcK = 128;        // K bytes per pipeline stage (FP8)
+constexpr int kRowAlign = 256;   // row capacity rounded to this
+
+enum Contraction : int32_t { kAuto = 0, kFp8 = 1, kPopcount = 2 };
+
+// Status bits written by kernels (OR-ed into InstState::status).
+enum : int32_t {
+    kErrBadVertex = 1,     // vertex id out of range in the input
+    kErrBadPtr = 2,        // edge_ptr not monotone / inconsistent
+    kErrTimeout = 4,       // a bounded wait gave up
+    kErrCapacity = 8,      // an index exceeded an allocated capacity
+};
+
+struct InstState {
+    // ---- input (original ids), device copies owned by the instance ----
+    int32_t n0, m0;
+    int64_t nnz0;
+    const int32_t *eptr;   // [m0+1] (int32 offsets into evtx)
+    const int32_t *evtx;   // [nnz0] vertex ids
+    const int32_t *f;      // [m0] demands
+    const int32_t *vptr;   // [n0+1] vertex -> hyperedge lists (built on device)
+    const int32_t *vedg;   // [nnz0]
+    int64_t k;
+
+    // ---- round state ----
+    int32_t n, m;          // current alive vertices / hyperedges
+    int32_t m_dp;          // hyperedges alive after this round's DP pass
+    int32_t n_next;        // vertices alive after this round's MD pass
+    int32_t rounds;        // executed rounds
+    int32_t active;        // 1 while the instance has not reached its fixpoint
+    int32_t max_rounds;    // 0 = unbounded
+    int32_t changed;       // last round deleted something
+    int32_t dp_deleted, md_deleted;
+    int32_t status;        // kErr* bits
+    int32_t pad_;
+
+    // id maps (capacity n0 / m0)
+    int32_t *v_o2c, *v_c2o;
+    int32_t *e_o2c, *e_c2o;
+
+    // epilogue inputs, indexed by current id
+    int32_t *e_f;          // f of current hyperedge
+    int32_t *e_s;          // alive size |e| of current hyperedge (= I^E_ii)
+    int32_t *v_deg;        // degree over alive hyperedges (= I^V_jj)
+    int32_t *v_maxf;       // max demand over alive hyperedges (0 if none)
+    int32_t *v_cnt;        // C_j of Algorithm 2
+    uint8_t *e_del;        // DP deletion flags
+    uint8_t *v_del;        // MD deletion flags
+
+    // dense FP8 operands: rows x pitch bytes (0x38 = 1.0 in E4M3)
+    uint8_t *A;            // rows = current hyperedges, K = current vertices
+    uint8_t *At;           // rows = current vertices, K = current hyperedges
+    int64_t A_pitch, At_pitch;
+    int32_t A_rows, At_rows;
+    // bit-packed operands: rows x pitch 32-bit words
+    uint32_t *Ab, *Atb;
+    int32_t Ab_pitch, Atb_pitch;
+    // tcgen05 tensor maps (CUtensorMap, 128 bytes each) for A and At, in device memory
+    const void *tmap_A;
+    const void *tmap_At;
+};
+
+// Per-phase work plan over a batch, rebuilt on the device before each phase.
+struct Plan {
+    int32_t count;          // instances
+    int32_t total_rows;     // rows to encode this phase
+    int64_t total_tiles;    // contraction tiles this phase
+    int32_t any_active;
+    int32_t pad_;
+    int32_t *row_off;       // [count+1] prefix of rows
+    int64_t *tile_off;      // [count+1] prefix of tiles
+};
+
+// Number of pair tiles of an R x R upper triangle.
+__host__ __device__ inline int64_t pop_tiles(int32_t R) {
+    int64_t t = (R + kPopTile - 1) / kPopTile;
+    return R > 1 ? t * (t + 1) / 2 : 0;
+}
+
+// tcgen05 tiles: row blocks of kTcM, column blocks of kTcN; a tile is needed
+// if it holds some pair i < j (j < R).
+__host__ __device__ inline int32_t tc_col_blocks(int32_t R) { return (R + kTcN - 1) / kTcN; }
+__host__ __device__ inline int32_t tc_row_blocks(int32_t R) { return (R + kTcM - 1) / kTcM; }
+// first column block holding a j > i for some i in row block bi
+__host__ __device__ inline int32_t tc_first_cb(int32_t bi) { return (bi * kTcM + 1) / kTcN; }
+__host__ __device__ inline int64_t tc_tiles(int32_t R) {
+    if (R <= 1) return 0;
+    // sum over row blocks bi of (cb - floor(bi/2))
+    const int64_t rb = tc_row_blocks(R), cb = tc_col_blocks(R);
+    return rb * cb - (rb / 2) * ((rb - 1) / 2 > 0 ? (rb - 1) / 2 : 0);
+}
+
+}  // namespace mhs

@@ -1,0 +1,276 @@
+"""Python binding of the C ABI in ``include/mhs.h`` (ctypes; marshalling only).
+
+Every step of the reduction runs in ``libmhs.so``; this module only converts
+arguments.  If the library has not been built, importing works but every
+call raises ``MhsError`` -- there is no fallback implementation.
+
+Example::
+
+    from paper_2109_06042_gb300 import mhs, instances
+    inst = instances.config_uniform(seed=0)
+    res = mhs.kernelize(inst)            # dict of surviving ids, demands, k, rounds
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libmhs.so")
+
+CONTRACTIONS = {"auto": 0, "fp8": 1, "popcount": 2}
+
+MHS_OK, MHS_EINVAL, MHS_ENOMEM, MHS_ECUDA, MHS_EAGAIN, MHS_ETIMEDOUT, MHS_EBUSY, MHS_EDEVICE = range(8)
+STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "EAGAIN", "ETIMEDOUT", "EBUSY", "EDEVICE"]
+
+
+class MhsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        self.status = status
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("contraction", ctypes.c_int32), ("max_rounds", ctypes.c_int32),
+                ("use_graphs", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+
+
+class RoundStats(ctypes.Structure):
+    _fields_ = [("n_alive", ctypes.c_int32), ("m_alive", ctypes.c_int32),
+                ("rounds", ctypes.c_int32), ("changed", ctypes.c_int32),
+                ("dp_deleted", ctypes.c_int32), ("md_deleted", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
+
+
+_lib = None
+
+_i32, _i64, _vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
+_P32 = ctypes.POINTER(ctypes.c_int32)
+_P64 = ctypes.POINTER(ctypes.c_int64)
+_PU8 = ctypes.POINTER(ctypes.c_uint8)
+
+_SIGS = {
+    "mhs_default_options": (_i32, [ctypes.POINTER(Options)]),
+    "mhs_load": (_i32, [_i32, _i32, _P32, _P32, _P32, _i64, ctypes.POINTER(Options), _vp,
+                        ctypes.POINTER(_vp)]),
+    "mhs_load_device": (_i32, [_i32, _i32, _vp, _vp, _vp, _i64, ctypes.POINTER(Options), _vp,
+                               ctypes.POINTER(_vp)]),
+    "mhs_load_batch": (_i32, [_i32, _P32, _P32, _P64, _P32, _P32, _P64, ctypes.POINTER(Options),
+                              _vp, ctypes.POINTER(_vp)]),
+    "mhs_count": (_i32, [_vp]),
+    "mhs_reduce_round": (_i32, [_vp, ctypes.POINTER(RoundStats)]),
+    "mhs_kernelize": (_i32, [_vp, ctypes.POINTER(RoundStats)]),
+    "mhs_result_at": (_i32, [_vp, _i32, _P32, _i32, _P32, _P32, _P32, _i32, _P32, _P64, _P32]),
+    "mhs_result": (_i32, [_vp, _P32, _i32, _P32, _P32, _P32, _i32, _P32, _P64, _P32]),
+    "mhs_result_device": (_i32, [_vp, _i32, _vp, _vp]),
+    "mhs_export": (_i32, [_vp, _i32, _P32, _i32, _P32, _i64, _P32, _P32, _P32, _P64]),
+    "mhs_set_timing": (_i32, [_vp, _i32]),
+    "mhs_last_timing": (_i32, [_vp, ctypes.POINTER(ctypes.c_float)]),
+    "mhs_free": (None, [_vp]),
+    "mhs_last_error": (ctypes.c_char_p, []),
+    "mhs_version": (ctypes.c_char_p, []),
+}
+
+
+def exported_names():
+    return sorted(_SIGS)
+
+
+def lib():
+    """Load ``libmhs.so`` (raises MhsError if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise MhsError(MHS_ECUDA, f"{LIB_PATH} is missing: build it with "
+                           "`python -m paper_2109_06042_gb300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != MHS_OK:
+        raise MhsError(status, lib().mhs_last_error().decode(errors="replace"))
+
+
+def _p32(a):
+    return a.ctypes.data_as(_P32)
+
+
+def make_options(contraction="auto", max_rounds=0, use_graphs=True) -> Options:
+    o = Options()
+    _check(lib().mhs_default_options(ctypes.byref(o)))
+    o.contraction = CONTRACTIONS[contraction] if isinstance(contraction, str) else int(contraction)
+    o.max_rounds = int(max_rounds)
+    o.use_graphs = int(bool(use_graphs))
+    return o
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+class Instance:
+    """Handle of one instance (or a batch) loaded on the GPU."""
+
+    def __init__(self, handle, keepalive=None):
+        self._h = handle
+        self._keep = keepalive
+
+    # ---- loading ----
+    @classmethod
+    def load(cls, inst, contraction="auto", max_rounds=0, use_graphs=True, stream=None):
+        """mhs_load from host arrays of an ``instances.Instance``-like object."""
+        ptr = np.ascontiguousarray(inst.edge_ptr, dtype=np.int32)
+        vtx = np.ascontiguousarray(inst.edge_vtx, dtype=np.int32)
+        dem = np.ascontiguousarray(inst.demand, dtype=np.int32)
+        if vtx.size == 0:
+            vtx = np.zeros(1, np.int32)
+        if dem.size == 0:
+            dem = np.zeros(1, np.int32)
+        opt = make_options(contraction, max_rounds, use_graphs)
+        h = ctypes.c_void_p()
+        _check(lib().mhs_load(int(inst.n), int(inst.m), _p32(ptr), _p32(vtx), _p32(dem),
+                              int(inst.k), ctypes.byref(opt), _stream_ptr(stream),
+                              ctypes.byref(h)))
+        return cls(h)
+
+    @classmethod
+    def load_device(cls, n, m, edge_ptr, edge_vtx, demand, k, contraction="auto", max_rounds=0,
+                    use_graphs=True, stream=None):
+        """mhs_load_device from CUDA tensors (int32, contiguous)."""
+        opt = make_options(contraction, max_rounds, use_graphs)
+        h = ctypes.c_void_p()
+        _check(lib().mhs_load_device(int(n), int(m), ctypes.c_void_p(edge_ptr.data_ptr()),
+                                     ctypes.c_void_p(edge_vtx.data_ptr()),
+                                     ctypes.c_void_p(demand.data_ptr()), int(k),
+                                     ctypes.byref(opt), _stream_ptr(stream), ctypes.byref(h)))
+        return cls(h)
+
+    @classmethod
+    def load_batch(cls, insts, contraction="auto", max_rounds=0, use_graphs=True, stream=None):
+        """mhs_load_batch from a list of host instances."""
+        count = len(insts)
+        n = np.array([i.n for i in insts], dtype=np.int32)
+        m = np.array([i.m for i in insts], dtype=np.int32)
+        k = np.array([i.k for i in insts], dtype=np.int64)
+        nnz = np.array([i.nnz for i in insts], dtype=np.int64)
+        ptr = np.zeros(int(m.sum()) + 1, dtype=np.int64)
+        base = np.concatenate([[0], np.cumsum(nnz)])
+        e0 = 0
+        for b, i in enumerate(insts):
+            ptr[e0:e0 + i.m + 1] = np.asarray(i.edge_ptr, dtype=np.int64) + base[b]
+            e0 += i.m
+        vtx = np.concatenate([np.asarray(i.edge_vtx, np.int32) for i in insts] + [np.zeros(1, np.int32)])
+        dem = np.concatenate([np.asarray(i.demand, np.int32) for i in insts] + [np.zeros(1, np.int32)])
+        return cls.load_batch_arrays(count, n, m, ptr, vtx, dem, k, contraction, max_rounds,
+                                     use_graphs, stream)
+
+    @classmethod
+    def load_batch_arrays(cls, count, n, m, ptr, vtx, dem, k, contraction="auto", max_rounds=0,
+                          use_graphs=True, stream=None):
+        opt = make_options(contraction, max_rounds, use_graphs)
+        h = ctypes.c_void_p()
+        _check(lib().mhs_load_batch(int(count), _p32(n), _p32(m), ptr.ctypes.data_as(_P64),
+                                    _p32(vtx), _p32(dem), k.ctypes.data_as(_P64),
+                                    ctypes.byref(opt), _stream_ptr(stream), ctypes.byref(h)))
+        return cls(h)
+
+    # ---- running ----
+    def reduce_round(self) -> dict:
+        st = RoundStats()
+        _check(lib().mhs_reduce_round(self._h, ctypes.byref(st)))
+        return st.as_dict()
+
+    def kernelize(self) -> dict:
+        st = RoundStats()
+        _check(lib().mhs_kernelize(self._h, ctypes.byref(st)))
+        return st.as_dict()
+
+    def set_timing(self, enable=True):
+        _check(lib().mhs_set_timing(self._h, int(bool(enable))))
+
+    def last_timing(self):
+        a = (ctypes.c_float * 4)()
+        _check(lib().mhs_last_timing(self._h, a))
+        return {"dp_ms": a[0], "md_ms": a[1], "other_ms": a[2], "total_ms": a[3]}
+
+    @property
+    def count(self) -> int:
+        return int(lib().mhs_count(self._h))
+
+    # ---- results ----
+    def result(self, index: int = 0) -> dict:
+        n = ctypes.c_int32()
+        m = ctypes.c_int32()
+        k = ctypes.c_int64()
+        r = ctypes.c_int32()
+        _check(lib().mhs_result_at(self._h, int(index), None, 0, ctypes.byref(n), None, None, 0,
+                                   ctypes.byref(m), ctypes.byref(k), ctypes.byref(r)))
+        vtx = np.zeros(max(n.value, 1), np.int32)
+        edg = np.zeros(max(m.value, 1), np.int32)
+        dem = np.zeros(max(m.value, 1), np.int32)
+        _check(lib().mhs_result_at(self._h, int(index), _p32(vtx), vtx.size, ctypes.byref(n),
+                                   _p32(edg), _p32(dem), edg.size, ctypes.byref(m),
+                                   ctypes.byref(k), ctypes.byref(r)))
+        return {"vertices": vtx[:n.value], "edges": edg[:m.value], "demands": dem[:m.value],
+                "k": int(k.value), "rounds": int(r.value)}
+
+    def result_device(self, alive_v, alive_e, index: int = 0):
+        """Write uint8 alive masks (CUDA tensors) over the input ids."""
+        _check(lib().mhs_result_device(self._h, int(index), ctypes.c_void_p(alive_v.data_ptr()),
+                                       ctypes.c_void_p(alive_e.data_ptr())))
+
+    def export(self, index: int = 0):
+        """The current reduced instance as (n, edge_ptr, edge_vtx, demand), renumbered."""
+        n = ctypes.c_int32()
+        m = ctypes.c_int32()
+        nnz = ctypes.c_int64()
+        _check(lib().mhs_export(self._h, int(index), None, 0, None, 0, None, ctypes.byref(n),
+                                ctypes.byref(m), ctypes.byref(nnz)))
+        ptr = np.zeros(m.value + 1, np.int32)
+        vtx = np.zeros(max(nnz.value, 1), np.int32)
+        dem = np.zeros(max(m.value, 1), np.int32)
+        _check(lib().mhs_export(self._h, int(index), _p32(ptr), m.value, _p32(vtx), vtx.size,
+                                _p32(dem), ctypes.byref(n), ctypes.byref(m), ctypes.byref(nnz)))
+        return int(n.value), ptr, vtx[:nnz.value], dem[:m.value]
+
+    def free(self):
+        if self._h:
+            lib().mhs_free(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.free()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def kernelize(inst, contraction="auto", max_rounds=0, use_graphs=True) -> dict:
+    """Load, reduce to the fixpoint and return the result of one host instance."""
+    with Instance.load(inst, contraction, max_rounds, use_graphs) as h:
+        h.kernelize()
+        return h.result()
+
+
+def version() -> str:
+    return lib().mhs_version().decode()

@@ -1,0 +1,222 @@
+"""Bit-exact parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Results are integer sets, so the bar is exact equality of the surviving
+vertex ids, hyperedge ids, demands, k and the round count.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2109_06042_gb300 import instances as I
+
+pytestmark = pytest.mark.gpu
+
+MODES = ("fp8", "popcount")
+
+
+@pytest.fixture(scope="module")
+def mhs():
+    from paper_2109_06042_gb300 import build
+    build.build()
+    from paper_2109_06042_gb300 import mhs as M
+    return M
+
+
+def _same(gpu, ref, ctx=""):
+    assert gpu["vertices"].tolist() == ref["vertices"].tolist(), f"vertices differ {ctx}"
+    assert gpu["edges"].tolist() == ref["edges"].tolist(), f"edges differ {ctx}"
+    assert gpu["demands"].tolist() == ref["demands"].tolist(), f"demands differ {ctx}"
+    assert gpu["k"] == ref["k"], ctx
+    assert gpu["rounds"] == ref["rounds"], f"rounds {gpu['rounds']} != {ref['rounds']} {ctx}"
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_uniform_workload_100_seeds(mhs, mode):
+    """The plain 200 x 400 workload, seeds 0..99."""
+    for seed in range(100):
+        inst = I.config_uniform(seed)
+        _same(mhs.kernelize(inst, contraction=mode), O.reduce(inst), f"seed {seed}")
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_tiny_and_degenerate(mhs, mode):
+    """Tiny instances with duplicate hyperedges, twin vertices and infeasible demands."""
+    for seed in range(300):
+        inst = I.tiny_random(seed, nmax=24, mmax=30)
+        _same(mhs.kernelize(inst, contraction=mode), O.reduce(inst), f"seed {seed}")
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_edge_cases(mhs, mode):
+    cases = [
+        I.from_edges(0, [], []),
+        I.from_edges(5, [], []),                      # no hyperedges: all vertices go
+        I.from_edges(3, [[], [0]], [1, 1]),           # an empty (infeasible) hyperedge
+        I.from_edges(1, [[0]], [1]),
+        I.from_edges(300, [[i] for i in range(300)], [1] * 300),   # irreducible family
+        I.from_edges(5, [[0, 1], [1, 2, 3], [1, 2, 4]], [2, 2, 2], k=3),  # Appendix A
+        I.from_edges(4, [[0, 1, 2, 3]] * 5, [1, 2, 2, 1, 2]),    # equal hyperedges
+        I.from_edges(6, [[0, 1, 2, 3, 4, 5]], [6]),    # a full hyperedge
+    ]
+    for c, inst in enumerate(cases):
+        _same(mhs.kernelize(inst, contraction=mode), O.reduce(inst), f"case {c}")
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("n,m", [(127, 129), (128, 256), (129, 257), (255, 383), (257, 640),
+                                 (513, 1100), (700, 1500)])
+def test_ragged_tile_boundaries(mhs, mode, n, m):
+    """Sizes around the 64 / 128 / 256 tile edges, several tiles per side."""
+    for seed in range(3):
+        inst = I.uniform_random(n, m, 1, 12, 3, n // 10, 50_000 + 97 * n + seed)
+        _same(mhs.kernelize(inst, contraction=mode), O.reduce(inst), f"seed {seed}")
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_round_by_round(mhs, mode):
+    """mhs_reduce_round after each round equals the oracle's state after as many rounds."""
+    for seed in range(5):
+        inst = I.uniform_random(400, 900, 1, 10, 3, 0, 70_000 + seed)
+        with mhs.Instance.load(inst, contraction=mode) as h:
+            r = 0
+            while True:
+                st = h.reduce_round()
+                r += 1
+                got = h.result()
+                ref = O.reduce(inst, max_rounds=r)
+                _same(got, ref, f"seed {seed} round {r}")
+                if not ref["changed"]:
+                    assert st["changed"] == 0
+                    break
+                assert st["changed"] == 1
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_powerlaw_full_size(mhs, mode):
+    """n=20,000, m=40,000, power-law sizes, Zipf(1.1) vertices, bit-exact."""
+    inst = I.config_powerlaw(0)
+    _same(mhs.kernelize(inst, contraction=mode), O.reduce(inst))
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_interval_full_size(mhs, mode):
+    """n=50,000, m=100,000 interval hyperedges with noise, bit-exact."""
+    inst = I.config_interval(0)
+    _same(mhs.kernelize(inst, contraction=mode), O.reduce(inst))
+
+
+def test_fp8_and_popcount_agree_on_medium(mhs):
+    for seed in range(4):
+        inst = I.config_powerlaw(seed, n=3000, m=6000)
+        a = mhs.kernelize(inst, contraction="fp8")
+        b = mhs.kernelize(inst, contraction="popcount")
+        for key in ("vertices", "edges", "rounds"):
+            assert np.array_equal(a[key], b[key])
+
+
+def test_large_counts_exact(mhs):
+    """Counts up to 2^20 stay exact with E4M3 0/1 operands and FP32 accumulation.
+
+    Hyperedges {0, 1, a, b} over all pairs a < b of the other vertices, f = 1.
+    Closed form under Algorithms 1-3: no DP deletion in round 1 (distinct
+    hyperedges of equal size); MD deletes v1 (same hyperedges as v0, higher
+    index) and every v_a (strictly dominated by v0 and v1) -- this needs the
+    pair count I_01 = m to equal deg(v1) = m exactly; round 2 keeps the first
+    of the now identical hyperedges {0}; round 3 changes nothing.
+    """
+    nb = 1450
+    pairs = np.array([(a, b) for a in range(2, nb + 2) for b in range(a + 1, nb + 2)],
+                     dtype=np.int32)[: (1 << 20) + 5]
+    m = pairs.shape[0]
+    vtx = np.empty((m, 4), np.int32)
+    vtx[:, 0] = 0
+    vtx[:, 1] = 1
+    vtx[:, 2:] = pairs
+    inst = I.Instance(n=nb + 2, m=m, edge_ptr=np.arange(0, 4 * m + 1, 4, dtype=np.int32),
+                      edge_vtx=vtx.reshape(-1), demand=np.ones(m, np.int32), k=1)
+    for mode in MODES:
+        r = mhs.kernelize(inst, contraction=mode)
+        assert r["vertices"].tolist() == [0], mode
+        assert r["edges"].tolist() == [0], mode
+        assert r["rounds"] == 3, mode
+
+
+def test_batch_matches_single(mhs):
+    """A batch of uneven instances reduced together equals each reduced alone
+    and the oracle."""
+    insts = [I.config_batch_one(4000 + i) for i in range(24)]
+    insts += [I.from_edges(0, [], []), I.from_edges(3, [], []), I.tiny_random(5)]
+    for mode in MODES:
+        with mhs.Instance.load_batch(insts, contraction=mode) as h:
+            assert h.count == len(insts)
+            h.kernelize()
+            for b, inst in enumerate(insts):
+                _same(h.result(b), O.reduce(inst), f"{mode} instance {b}")
+
+
+def test_load_device_and_masks(mhs):
+    import torch
+    inst = I.config_uniform(3)
+    dev = torch.device("cuda:0")
+    ptr = torch.from_numpy(inst.edge_ptr).to(dev)
+    vtx = torch.from_numpy(inst.edge_vtx).to(dev)
+    dem = torch.from_numpy(inst.demand).to(dev)
+    ref = O.reduce(inst)
+    for mode in MODES:
+        with mhs.Instance.load_device(inst.n, inst.m, ptr, vtx, dem, inst.k, contraction=mode) as h:
+            h.kernelize()
+            _same(h.result(), ref, mode)
+            av = torch.zeros(inst.n, dtype=torch.uint8, device=dev)
+            ae = torch.zeros(inst.m, dtype=torch.uint8, device=dev)
+            h.result_device(av, ae)
+            torch.cuda.synchronize()
+            assert np.nonzero(av.cpu().numpy())[0].tolist() == ref["vertices"].tolist()
+            assert np.nonzero(ae.cpu().numpy())[0].tolist() == ref["edges"].tolist()
+
+
+def test_export_and_resume(mhs):
+    """A post-round state re-loaded through mhs_export reaches the same fixpoint."""
+    inst = I.config_uniform(7, n=300, m=700)
+    full = O.reduce(inst)
+    with mhs.Instance.load(inst) as h:
+        h.reduce_round()
+        n, ptr, vtx, dem = h.export()
+        part = h.result()
+    sub = I.Instance(n=n, m=len(dem), edge_ptr=ptr, edge_vtx=vtx, demand=dem, k=inst.k)
+    res = mhs.kernelize(sub)
+    # map renumbered ids back
+    assert part["vertices"][res["vertices"]].tolist() == full["vertices"].tolist()
+    assert part["edges"][res["edges"]].tolist() == full["edges"].tolist()
+    assert res["rounds"] + 1 == full["rounds"] or (res["rounds"] == 1 and full["rounds"] == 1)
+
+
+def test_invalid_inputs_rejected(mhs):
+    import torch
+    bad = [
+        I.Instance(n=3, m=1, edge_ptr=np.array([0, 2], np.int32),
+                   edge_vtx=np.array([0, 3], np.int32), demand=np.array([1], np.int32), k=0),
+        I.Instance(n=3, m=1, edge_ptr=np.array([0, 2], np.int32),
+                   edge_vtx=np.array([1, 1], np.int32), demand=np.array([1], np.int32), k=0),
+        I.Instance(n=3, m=1, edge_ptr=np.array([0, 2], np.int32),
+                   edge_vtx=np.array([0, 1], np.int32), demand=np.array([0], np.int32), k=0),
+    ]
+    for inst in bad:
+        with pytest.raises(mhs.MhsError) as ei:
+            mhs.Instance.load(inst)
+        assert ei.value.status == mhs.MHS_EINVAL
+    dev = torch.device("cuda:0")
+    inst = bad[0]
+    with pytest.raises(mhs.MhsError) as ei:
+        mhs.Instance.load_device(3, 1, torch.from_numpy(inst.edge_ptr).to(dev),
+                                 torch.from_numpy(inst.edge_vtx).to(dev),
+                                 torch.from_numpy(inst.demand).to(dev), 0)
+    assert ei.value.status == mhs.MHS_EINVAL
+
+
+def test_deterministic_repeats(mhs):
+    inst = I.config_powerlaw(1, n=4000, m=8000)
+    first = mhs.kernelize(inst)
+    for _ in range(5):
+        again = mhs.kernelize(inst)
+        for key in ("vertices", "edges", "rounds"):
+            assert np.array_equal(first[key], again[key])
