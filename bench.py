@@ -231,11 +231,13 @@ def run_ours(args, rank, world, dist):
 
     peaks, kind = load_peaks()
     if args.contraction == "fp8":
-        peak = 2.0 * peaks["bf16_tflops_sustained"]  # FP8 dense = 2x BF16 (4.5 / 2.25 PF nominal)
+        # FP8 dense = 2 x BF16 (4.5 / 2.25 PF nominal); the burst figure, since the
+        # contraction is timed in short steps (tens of ms) at full clock
+        peak = 2.0 * peaks["bf16_tflops"]
         achieved = flops / (contract_ms / args.steps / 1e3) / 1e12
         roof = {"bound": "tensor", "achieved": round(achieved, 2), "peak": round(peak, 1),
                 "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
-                "kernel": "k_tc_contract", "peak_source": f"{kind}: 2 x bf16_tflops_sustained",
+                "kernel": "k_tc_contract", "peak_source": f"{kind}: 2 x bf16_tflops (burst)",
                 "launches_per_step": 2 * rounds}
     else:
         sm_mhz = peaks.get("sm_max_mhz", 2070.0)

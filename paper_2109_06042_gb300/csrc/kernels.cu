@@ -559,14 +559,14 @@ cudaError_t launch_round_phase(InstState *st, Plan *plan, BatchCounters *ctr, in
         if (tc) k_encode_vertices<true><<<enc_grid, 256, 0, s>>>(st, plan);
         else k_encode_vertices<false><<<enc_grid, 256, 0, s>>>(st, plan);
     }
-    if (ev_contract_begin) cudaEventRecord(ev_contract_begin, s);
+    if (ev_contract_begin) cudaEventRecordWithFlags(ev_contract_begin, s, cudaEventRecordExternal);
     if (tc) {
         cudaError_t e = launch_tc_contract(st, plan, phase, sms, kerr, s);
         if (e != cudaSuccess) return e;
     } else {
         k_pop_contract<<<grid_for(sms, 6), 256, 0, s>>>(st, plan, phase);
     }
-    if (ev_contract_end) cudaEventRecord(ev_contract_end, s);
+    if (ev_contract_end) cudaEventRecordWithFlags(ev_contract_end, s, cudaEventRecordExternal);
     if (phase == 0) k_compact_edges<<<count, 1024, 0, s>>>(st, count);
     else k_compact_vertices<<<count, 1024, 0, s>>>(st, count, ctr);
     return cudaGetLastError();

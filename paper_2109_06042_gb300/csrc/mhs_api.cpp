@@ -107,8 +107,8 @@ struct mhs_instance {
     // arena offsets of the batch-wide input arrays
     int64_t in_eptr = 0, in_evtx = 0, in_f = 0;
     int64_t sum_m1 = 0, sum_nnz = 0, sum_m = 0;
-    // round graph
-    cudaGraphExec_t graph = nullptr;
+    // round graphs: graph[0] plain, graph[1] with timing events
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
     // timing
     bool timing = false;
     cudaEvent_t ev[6] = {};
@@ -121,7 +121,8 @@ namespace {
 void destroy(mhs_instance *h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
-    if (h->graph) cudaGraphExecDestroy(h->graph);
+    for (auto &g : h->graph)
+        if (g) cudaGraphExecDestroy(g);
     for (auto &e : h->ev)
         if (e) cudaEventDestroy(e);
     if (h->arena) cudaFreeAsync(h->arena, h->stream);
@@ -400,36 +401,38 @@ cudaError_t enqueue_round(mhs_instance *h, bool with_events) {
                            h->stream);
 }
 
+mhs_status capture_round(mhs_instance *h, bool with_events, cudaGraphExec_t *out) {
+    cudaGraph_t g;
+    CUDA_TRY(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = enqueue_round(h, with_events);
+    cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess)
+        return fail(MHS_ECUDA, "graph capture failed: %s",
+                    cudaGetErrorString(e != cudaSuccess ? e : e2));
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(MHS_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    return MHS_OK;
+}
+
 mhs_status run_rounds(mhs_instance *h, int32_t limit, mhs_round_stats *stats) {
     if (h->timing) {
         for (auto &e : h->ev)
             if (!e) CUDA_TRY(cudaEventCreate(&e));
         for (float &x : h->last_ms) x = 0.f;
     }
-    if (h->opt.use_graphs && !h->timing && !h->graph) {
-        cudaGraph_t g;
-        CUDA_TRY(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-        cudaError_t e = enqueue_round(h, false);
-        cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
-        if (e != cudaSuccess || e2 != cudaSuccess)
-            return fail(MHS_ECUDA, "graph capture failed: %s",
-                        cudaGetErrorString(e != cudaSuccess ? e : e2));
-        e = cudaGraphInstantiate(&h->graph, g, 0);
-        cudaGraphDestroy(g);
-        if (e != cudaSuccess) return fail(MHS_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    const int gi = h->timing ? 1 : 0;
+    if (h->opt.use_graphs && !h->graph[gi]) {
+        mhs_status st = capture_round(h, h->timing, &h->graph[gi]);
+        if (st) return st;
     }
     int32_t done = 0;
     bool any = false;
     while (limit <= 0 || done < limit) {
-        if (h->timing) {
-            CUDA_TRY(cudaEventRecord(h->ev[4], h->stream));
-            CUDA_TRY(enqueue_round(h, true));
-            CUDA_TRY(cudaEventRecord(h->ev[5], h->stream));
-        } else if (h->graph) {
-            CUDA_TRY(cudaGraphLaunch(h->graph, h->stream));
-        } else {
-            CUDA_TRY(enqueue_round(h, false));
-        }
+        if (h->timing) CUDA_TRY(cudaEventRecord(h->ev[4], h->stream));
+        if (h->graph[gi]) CUDA_TRY(cudaGraphLaunch(h->graph[gi], h->stream));
+        else CUDA_TRY(enqueue_round(h, h->timing));
+        if (h->timing) CUDA_TRY(cudaEventRecord(h->ev[5], h->stream));
         CUDA_TRY(cudaStreamSynchronize(h->stream));
         any = true;
         ++done;
