@@ -198,6 +198,38 @@ mhs_status mhs_export(const mhs_instance *inst, int32_t index, int32_t *edge_ptr
 mhs_status mhs_set_timing(mhs_instance *inst, int32_t enable);
 mhs_status mhs_last_timing(const mhs_instance *inst, float *ms4);
 
+/*
+ * Kernelize one small instance without allocating any memory.  The paper has
+ * no counterpart: this entry point exists for callers that must not
+ * allocate device memory while they run -- for example code running under a
+ * fixed-budget or external allocator, real-time loops where cudaMalloc /
+ * cudaFree (which may synchronise the device) are not allowed, or plug-ins
+ * whose host owns all device memory.
+ *
+ * Inputs are DEVICE arrays in the layout of mhs_load (edge_ptr[m+1] with
+ * edge_ptr[m] == nnz, edge_vtx[nnz], demand[m]); they are read in place and
+ * must stay valid until the call returns.  Outputs: alive_v (uint8[n]) and
+ * alive_e (uint8[m]) DEVICE buffers receive 1 for surviving vertices /
+ * hyperedges (input ids); *rounds_out (host, may be NULL) the round count.
+ * Same rules and result as mhs_kernelize (bit-packed popcount contraction).
+ *
+ * All working memory is one file-scope device array of 6 MiB that every GPU
+ * loading the library keeps until the process exits.  Limits: n <= 4096,
+ * m <= 4096, nnz <= 65536; larger instances give MHS_EINVAL.  Every call
+ * reuses the same array (the call clears what must start at zero), so calls
+ * whose GPU work overlaps race and must be serialised by the caller.  The
+ * first call on each device looks up the array's address
+ * (cudaGetSymbolAddress) and should come before any stream capture.  The
+ * call runs on cuda_stream (NULL: the default stream) and returns after the
+ * work is done.  Errors are reported through the return value and, if
+ * err_buf is non-NULL, a message in err_buf[err_cap] (mhs_last_error is not
+ * used, so that no host string is allocated either).
+ */
+mhs_status mhs_kernelize_noalloc(int32_t n, int32_t m, const int32_t *edge_ptr,
+                                 const int32_t *edge_vtx, const int32_t *demand, int32_t nnz,
+                                 uint8_t *alive_v, uint8_t *alive_e, int32_t *rounds_out,
+                                 void *cuda_stream, char *err_buf, size_t err_cap);
+
 /* Free all device and host memory of the instance (synchronises its stream). */
 void mhs_free(mhs_instance *inst);
 

@@ -70,6 +70,8 @@ _SIGS = {
     "mhs_export": (_i32, [_vp, _i32, _P32, _i32, _P32, _i64, _P32, _P32, _P32, _P64]),
     "mhs_set_timing": (_i32, [_vp, _i32]),
     "mhs_last_timing": (_i32, [_vp, ctypes.POINTER(ctypes.c_float)]),
+    "mhs_kernelize_noalloc": (_i32, [_i32, _i32, _vp, _vp, _vp, _i32, _vp, _vp, _P32, _vp,
+                                     ctypes.c_char_p, ctypes.c_size_t]),
     "mhs_free": (None, [_vp]),
     "mhs_last_error": (ctypes.c_char_p, []),
     "mhs_version": (ctypes.c_char_p, []),
@@ -270,6 +272,23 @@ def kernelize(inst, contraction="auto", max_rounds=0, use_graphs=True) -> dict:
     with Instance.load(inst, contraction, max_rounds, use_graphs) as h:
         h.kernelize()
         return h.result()
+
+
+def kernelize_noalloc(n, m, edge_ptr, edge_vtx, demand, nnz, alive_v, alive_e, stream=None):
+    """mhs_kernelize_noalloc on CUDA tensors: no memory is allocated by the
+    call; alive_v / alive_e (uint8 CUDA tensors) receive the surviving masks.
+    Returns the round count."""
+    rounds = ctypes.c_int32(0)
+    buf = ctypes.create_string_buffer(256)
+    st = lib().mhs_kernelize_noalloc(int(n), int(m), ctypes.c_void_p(edge_ptr.data_ptr()),
+                                     ctypes.c_void_p(edge_vtx.data_ptr()),
+                                     ctypes.c_void_p(demand.data_ptr()), int(nnz),
+                                     ctypes.c_void_p(alive_v.data_ptr()),
+                                     ctypes.c_void_p(alive_e.data_ptr()), ctypes.byref(rounds),
+                                     _stream_ptr(stream), buf, 256)
+    if st != MHS_OK:
+        raise MhsError(st, buf.value.decode(errors="replace"))
+    return int(rounds.value)
 
 
 def version() -> str:
