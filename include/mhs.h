@@ -132,6 +132,17 @@ mhs_status mhs_load_batch(int32_t count, const int32_t *n, const int32_t *m,
                           const int32_t *demand, const int64_t *k, const mhs_options *opt,
                           void *cuda_stream, mhs_instance **out);
 
+/*
+ * mhs_load_batch with the CSR arrays in DEVICE memory (edge_ptr int64,
+ * edge_vtx and demand int32, same layout); n, m and k stay host arrays.
+ * Structural checks run on the device; a malformed instance gives
+ * MHS_EINVAL naming its index.
+ */
+mhs_status mhs_load_batch_device(int32_t count, const int32_t *n, const int32_t *m,
+                                 const int64_t *edge_ptr, const int32_t *edge_vtx,
+                                 const int32_t *demand, const int64_t *k,
+                                 const mhs_options *opt, void *cuda_stream, mhs_instance **out);
+
 /* Number of instances held by the handle (1 unless loaded as a batch). */
 int32_t mhs_count(const mhs_instance *inst);
 
@@ -176,6 +187,24 @@ mhs_status mhs_result(const mhs_instance *inst, int32_t *vtx_out, int32_t vtx_ca
  */
 mhs_status mhs_result_device(const mhs_instance *inst, int32_t index, uint8_t *alive_v,
                              uint8_t *alive_e);
+
+/*
+ * Alive masks of every instance of a batch in one launch, over the
+ * concatenated input ids: alive_v (uint8[sum n]) and alive_e (uint8[sum m])
+ * DEVICE buffers; instance b's vertices start at sum_{c<b} n[c], its
+ * hyperedges at sum_{c<b} m[c].  Written on the instance's stream.
+ */
+mhs_status mhs_result_batch_device(const mhs_instance *inst, uint8_t *alive_v,
+                                   uint8_t *alive_e);
+
+/*
+ * Per-round sizes recorded by instance `index` (HOST output): for each
+ * executed round r < min(cap_rounds, 32), rows_out[3r..3r+2] = hyperedges
+ * entering DP, vertices entering DP, hyperedges left after DP (the sizes
+ * the two contractions of that round work on).  *rounds_out = rounds run.
+ */
+mhs_status mhs_trace_at(const mhs_instance *inst, int32_t index, int32_t *rows_out,
+                        int32_t cap_rounds, int32_t *rounds_out);
 
 /*
  * Export the current (reduced) instance `index` as a new CSR over the

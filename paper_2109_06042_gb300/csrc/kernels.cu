@@ -84,66 +84,74 @@ __device__ __forceinline__ int32_t kpad_words(int32_t K) {
 
 // ---------------------------------------------------------------- setup --
 
-__global__ void k_validate(InstState *st) {
-    InstState &s = *st;
+// Structural checks of device-resident inputs (blockIdx.y = instance):
+// edge_ptr starts at 0, is non-decreasing and ends at nnz; vertex ids lie in
+// [0, n); demands are >= 1.
+__global__ void k_validate(InstState *st, int count) {
+    const int b = blockIdx.y;
+    if (b >= count) return;
+    InstState &s = st[b];
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     if (tid == 0) {
         if (s.eptr[0] != 0 || (int64_t)s.eptr[s.m0] != s.nnz0) atomicOr(&s.status, kErrBadPtr);
     }
-    for (int64_t e = tid; e < s.m0; e += stride)
+    for (int64_t e = tid; e < s.m0; e += stride) {
         if (s.eptr[e + 1] < s.eptr[e]) atomicOr(&s.status, kErrBadPtr);
+        if (s.f[e] < 1) atomicOr(&s.status, kErrBadDemand);
+    }
     for (int64_t p = tid; p < s.nnz0; p += stride) {
         int32_t v = s.evtx[p];
         if (v < 0 || v >= s.n0) atomicOr(&s.status, kErrBadVertex);
     }
 }
 
-// Zero the list heads and the per-vertex cursors (v_cnt) of every instance.
-__global__ void k_csc_zero(InstState *st, int count) {
+// Batch inputs from device arrays: convert the global int64 CSR offsets of
+// instance b (hyperedges [e0[b], e0[b] + m0)) to its local int32 offsets.
+__global__ void k_localize_ptr(InstState *st, int count, const int64_t *gptr, const int64_t *e0) {
     const int b = blockIdx.y;
     if (b >= count) return;
     InstState &s = st[b];
-    int32_t *vptr = const_cast<int32_t *>(s.vptr);
-    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v <= s.n0;
-         v += (int64_t)gridDim.x * blockDim.x) {
-        vptr[v] = 0;
-        if (v < s.n0) s.v_cnt[v] = 0;
+    int32_t *eptr = const_cast<int32_t *>(s.eptr);
+    const int64_t base = gptr[e0[b]];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= s.m0;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t x = gptr[e0[b] + i] - base;
+        eptr[i] = (x >= 0 && x <= s.nnz0) ? (int32_t)x : -1;
     }
 }
 
-// Degree count for the vertex -> hyperedge lists (blockIdx.y = instance).
-__global__ void k_csc_count(InstState *st, int count, int32_t *vcount_base_unused) {
-    (void)vcount_base_unused;
+// Gather gptr[e0[b]] for b in [0, count] (instance boundaries of a batch).
+__global__ void k_gather_bounds(const int64_t *gptr, const int64_t *e0, int64_t *out, int count) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b <= count; b += gridDim.x * blockDim.x)
+        out[b] = gptr[e0[b]];
+}
+
+// Incidence -> hyperedge id (blockIdx.y = instance).
+__global__ void k_inc_build(InstState *st, int count) {
     const int b = blockIdx.y;
     if (b >= count) return;
     InstState &s = st[b];
     if (s.status) return;
-    int32_t *vptr = const_cast<int32_t *>(s.vptr);
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < s.nnz0;
-         p += (int64_t)gridDim.x * blockDim.x)
-        atomicAdd(&vptr[s.evtx[p] + 1], 1);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < s.m0;
+         e += (int64_t)gridDim.x * blockDim.x)
+        for (int32_t p = s.eptr[e]; p < s.eptr[e + 1]; ++p) s.inc_e[p] = (int32_t)e;
 }
 
-// Exclusive scan of vptr (one block per instance); also initialises the
-// round state and the identity id maps.
-__global__ void k_csc_scan_init(InstState *st, int count, int32_t max_rounds) {
-    __shared__ int32_t sh[33];
+// Round state, identity id maps and the hyperedge rows of round 1 (one
+// block per instance).
+__global__ void k_init(InstState *st, int count, int32_t max_rounds) {
     const int b = blockIdx.x;
     if (b >= count) return;
     InstState &s = st[b];
-    int32_t *vptr = const_cast<int32_t *>(s.vptr);
-    int32_t carry = 0;
-    for (int32_t base = 0; base < s.n0 + 1; base += blockDim.x) {
-        int32_t i = base + threadIdx.x;
-        int32_t x = i < s.n0 + 1 ? vptr[i] : 0;
-        int32_t tot;
-        int32_t ex = block_exclusive_scan<int32_t>(x, &tot, sh);
-        if (i < s.n0 + 1) vptr[i] = carry + ex + x;  // inclusive of the shifted counts
-        carry += tot;
-    }
     for (int32_t v = threadIdx.x; v < s.n0; v += blockDim.x) { s.v_o2c[v] = v; s.v_c2o[v] = v; }
-    for (int32_t e = threadIdx.x; e < s.m0; e += blockDim.x) { s.e_o2c[e] = e; s.e_c2o[e] = e; }
+    for (int32_t e = threadIdx.x; e < s.m0; e += blockDim.x) {
+        s.e_o2c[e] = e;
+        s.e_c2o[e] = e;
+        s.e_f[e] = s.f[e];
+        s.e_s[e] = 0;
+        s.e_del[e] = 0;
+    }
     if (threadIdx.x == 0) {
         s.n = s.n0; s.m = s.m0; s.m_dp = s.m0; s.n_next = s.n0;
         s.rounds = 0; s.active = s.status == 0; s.max_rounds = max_rounds; s.changed = 0;
@@ -151,48 +159,32 @@ __global__ void k_csc_scan_init(InstState *st, int count, int32_t max_rounds) {
     }
 }
 
-// Fill the lists.  v_cnt (zeroed by the caller, unused until the first MD
-// pass) serves as the per-vertex cursor.
-__global__ void k_csc_fill(InstState *st, int count) {
-    const int b = blockIdx.y;
-    if (b >= count) return;
-    InstState &s = st[b];
-    if (s.status) return;
-    int32_t *vedg = const_cast<int32_t *>(s.vedg);
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < s.m0;
-         e += (int64_t)gridDim.x * blockDim.x)
-        for (int32_t p = s.eptr[e]; p < s.eptr[e + 1]; ++p) {
-            const int32_t v = s.evtx[p];
-            vedg[s.vptr[v] + atomicAdd(&s.v_cnt[v], 1)] = (int32_t)e;
-        }
-}
-
 // ------------------------------------------------------------- planning --
 
 // phase 0: rows = current hyperedges (DP); phase 1: rows = current vertices (MD).
 __global__ void k_plan(InstState *st, Plan *plan, int phase, int tc, BatchCounters *ctr) {
-    __shared__ int32_t sh[33];
     __shared__ int64_t sh64[33];
     const int count = plan->count;
-    int32_t rcarry = 0;
+    int64_t icarry = 0;
     int64_t tcarry = 0;
     int32_t act_any = 0;
     for (int base = 0; base < count; base += blockDim.x) {
         int b = base + threadIdx.x;
-        int32_t rows = 0;
+        int64_t inc = 0;
         int64_t tiles = 0;
         if (b < count) {
             const InstState &s = st[b];
             if (s.active && s.status == 0) {
-                rows = phase == 0 ? s.m : s.n;
+                const int32_t rows = phase == 0 ? s.m : s.n;
+                inc = s.nnz0;
                 tiles = tc ? tc_tiles(rows) : pop_tiles(rows);
                 act_any = 1;
             }
         }
-        int32_t tot;
-        int32_t ex = block_exclusive_scan<int32_t>(rows, &tot, sh);
-        if (b < count) plan->row_off[b] = rcarry + ex;
-        rcarry += tot;
+        int64_t itot;
+        int64_t iex = block_exclusive_scan<int64_t>(inc, &itot, sh64);
+        if (b < count) plan->inc_off[b] = icarry + iex;
+        icarry += itot;
         int64_t ttot;
         int64_t tex = block_exclusive_scan<int64_t>(tiles, &ttot, sh64);
         if (b < count) plan->tile_off[b] = tcarry + tex;
@@ -200,9 +192,9 @@ __global__ void k_plan(InstState *st, Plan *plan, int phase, int tc, BatchCounte
     }
     act_any = __syncthreads_or(act_any);
     if (threadIdx.x == 0) {
-        plan->row_off[count] = rcarry;
+        plan->inc_off[count] = icarry;
         plan->tile_off[count] = tcarry;
-        plan->total_rows = rcarry;
+        plan->total_inc = icarry;
         plan->total_tiles = tcarry;
         plan->any_active = act_any;
         if (phase == 0 && ctr) {
@@ -215,96 +207,60 @@ __global__ void k_plan(InstState *st, Plan *plan, int phase, int tc, BatchCounte
 
 // --------------------------------------------------------------- encode --
 
-// One warp per row: zero the row of the dense / bit operand over the
-// current K range, then set the incidences of the row's alive partners.
-// Returns the number of distinct incidences set by this lane.
-template <bool kDense>
-__device__ __forceinline__ int32_t write_row(uint8_t *drow, uint32_t *brow, int64_t kbytes,
-                                             int32_t kwords, const int32_t *part, int32_t np,
-                                             const int32_t *o2c, const int32_t *fval,
-                                             int32_t *maxf, int32_t limit, int32_t *err) {
-    const int lane = threadIdx.x & 31;
-    if (kDense) {
-        uint4 z = make_uint4(0, 0, 0, 0);
-        for (int64_t c = lane; c < kbytes / 16; c += 32) reinterpret_cast<uint4 *>(drow)[c] = z;
-    } else {
-        for (int32_t c = lane; c < kwords / 4; c += 32)
-            reinterpret_cast<uint4 *>(brow)[c] = make_uint4(0, 0, 0, 0);
-    }
-    __syncwarp();
-    int32_t cnt = 0, mx = 0;
-    for (int32_t p = lane; p < np; p += 32) {
-        int32_t item = part[p];
-        int32_t c = o2c[item];
-        if (c < 0) continue;
-        if (c >= limit) { atomicOr(err, kErrCapacity); continue; }
-        if (fval) mx = max(mx, fval[item]);
-        if (kDense) {
-            uint32_t *w = reinterpret_cast<uint32_t *>(drow + (c & ~3));
-            uint32_t sh = 8u * (c & 3);
-            uint32_t old = atomicOr(w, (uint32_t)kFp8One << sh);
-            cnt += ((old >> sh) & 0xffu) == 0;
-        } else {
-            uint32_t bit = 1u << (c & 31);
-            uint32_t old = atomicOr(&brow[c >> 5], bit);
-            cnt += (old & bit) == 0;
-        }
-    }
-    if (maxf) *maxf = mx;
-    return cnt;
-}
-
-// Phase 0 rows: current hyperedges; partners: vertices (K = current n).
-template <bool kDense>
-__global__ void k_encode_edges(InstState *st, const Plan *plan) {
-    const int lane = threadIdx.x & 31;
-    const int32_t gw0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int32_t nw = (gridDim.x * blockDim.x) >> 5;
-    const int32_t total = plan->total_rows;
-    for (int32_t g = gw0; g < total; g += nw) {
-        const int b = find_owner(plan->row_off, plan->count, g);
+// One thread per incidence (e, v) of the original instance.  Phase 0 sets
+// A[e'][v'] (rows = current hyperedges, K = current vertices) and counts
+// |e| (= I^E_ii); phase 1 sets At[v'][e''] (rows = current vertices, K =
+// hyperedges alive after DP) and counts deg(v) (= I^V_jj) and the maximum
+// demand.  The operands are all-zero between phases: kClear writes zeros at
+// exactly the positions kSet wrote, with the same id maps, after the
+// contraction has read them.  A set counts only incidences that were not
+// already set, so a repeated id inside one hyperedge counts once.
+template <int kPhase, bool kSet, bool kDense>
+__global__ void k_scatter(InstState *st, const Plan *plan) {
+    const int64_t total = plan->total_inc;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const int b = find_owner(plan->inc_off, plan->count, g);
         InstState &s = st[b];
-        const int32_t r = g - plan->row_off[b];
-        const int32_t e = s.e_c2o[r];
-        const int32_t p0 = s.eptr[e], np = s.eptr[e + 1] - p0;
-        int32_t cnt;
+        const int64_t p = g - plan->inc_off[b];
+        const int32_t e = s.inc_e[p];
+        const int32_t v = s.evtx[p];
+        const int32_t ce = s.e_o2c[e], cv = s.v_o2c[v];
+        if (ce < 0 || cv < 0) continue;
+        const int32_t r = kPhase == 0 ? ce : cv;
+        const int32_t c = kPhase == 0 ? cv : ce;
+        const int32_t R = kPhase == 0 ? s.m : s.n;
+        const int32_t K = kPhase == 0 ? s.n : s.m_dp;
+        if (r >= R || c >= K) { atomicOr(&s.status, kErrCapacity); continue; }
+        bool fresh = false;
         if (kDense) {
-            cnt = write_row<true>(s.A + (int64_t)r * s.A_pitch, nullptr, kpad_bytes(s.n), 0,
-                                  s.evtx + p0, np, s.v_o2c, nullptr, nullptr, s.n, &s.status);
+            uint8_t *row = (kPhase == 0 ? s.A : s.At) + (int64_t)r * (kPhase == 0 ? s.A_pitch : s.At_pitch);
+            if (kSet) {
+                uint32_t *w = reinterpret_cast<uint32_t *>(row + (c & ~3));
+                const uint32_t sh = 8u * (c & 3);
+                const uint32_t old = atomicOr(w, (uint32_t)kFp8One << sh);
+                fresh = ((old >> sh) & 0xffu) == 0;
+            } else {
+                row[c] = 0;
+            }
         } else {
-            cnt = write_row<false>(nullptr, s.Ab + (int64_t)r * s.Ab_pitch, 0, kpad_words(s.n),
-                                   s.evtx + p0, np, s.v_o2c, nullptr, nullptr, s.n, &s.status);
+            uint32_t *row = (kPhase == 0 ? s.Ab : s.Atb) +
+                            (int64_t)r * (kPhase == 0 ? s.Ab_pitch : s.Atb_pitch);
+            if (kSet) {
+                const uint32_t bit = 1u << (c & 31);
+                fresh = (atomicOr(&row[c >> 5], bit) & bit) == 0;
+            } else {
+                row[c >> 5] = 0;  // every set bit of this word is cleared by some thread
+            }
         }
-        cnt = warp_sum(cnt);
-        if (lane == 0) { s.e_s[r] = cnt; s.e_f[r] = s.f[e]; s.e_del[r] = 0; }
-    }
-}
-
-// Phase 1 rows: current vertices; partners: hyperedges alive after DP (K = m_dp).
-template <bool kDense>
-__global__ void k_encode_vertices(InstState *st, const Plan *plan) {
-    const int lane = threadIdx.x & 31;
-    const int32_t gw0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int32_t nw = (gridDim.x * blockDim.x) >> 5;
-    const int32_t total = plan->total_rows;
-    for (int32_t g = gw0; g < total; g += nw) {
-        const int b = find_owner(plan->row_off, plan->count, g);
-        InstState &s = st[b];
-        const int32_t r = g - plan->row_off[b];
-        const int32_t v = s.v_c2o[r];
-        const int32_t q0 = s.vptr[v], nq = s.vptr[v + 1] - q0;
-        int32_t cnt, mx = 0;
-        if (kDense) {
-            cnt = write_row<true>(s.At + (int64_t)r * s.At_pitch, nullptr, kpad_bytes(s.m_dp), 0,
-                                  s.vedg + q0, nq, s.e_o2c, s.f, &mx, s.m_dp, &s.status);
-        } else {
-            cnt = write_row<false>(nullptr, s.Atb + (int64_t)r * s.Atb_pitch, 0,
-                                   kpad_words(s.m_dp), s.vedg + q0, nq, s.e_o2c, s.f, &mx,
-                                   s.m_dp, &s.status);
+        if (kSet && fresh) {
+            if (kPhase == 0) {
+                atomicAdd(&s.e_s[r], 1);
+            } else {
+                atomicAdd(&s.v_deg[r], 1);
+                atomicMax(&s.v_maxf[r], s.f[e]);
+            }
         }
-        cnt = warp_sum(cnt);
-        mx = warp_max(mx);
-        if (lane == 0) { s.v_deg[r] = cnt; s.v_maxf[r] = mx; s.v_cnt[r] = 0; s.v_del[r] = 0; }
     }
 }
 
@@ -334,7 +290,22 @@ __global__ void k_compact_edges(InstState *st, int count) {
         carry += tot;
         __syncthreads();
     }
-    if (threadIdx.x == 0) { s.m_dp = carry; s.dp_deleted = m - carry; }
+    if (threadIdx.x == 0) {
+        s.m_dp = carry;
+        s.dp_deleted = m - carry;
+        if (s.rounds < kTraceRounds) {
+            s.trace[s.rounds][0] = m;
+            s.trace[s.rounds][1] = s.n;
+            s.trace[s.rounds][2] = carry;
+        }
+    }
+    // vertex rows of this round's MD pass
+    for (int32_t r = threadIdx.x; r < s.n; r += blockDim.x) {
+        s.v_deg[r] = 0;
+        s.v_maxf[r] = 0;
+        s.v_cnt[r] = 0;
+        s.v_del[r] = 0;
+    }
 }
 
 // MD decision (Algorithm 2: delete v_j iff C_j >= max f over E(v_j)),
@@ -369,6 +340,14 @@ __global__ void k_compact_vertices(InstState *st, int count, BatchCounters *ctr)
             s.rounds += 1;
             if (!s.changed || (s.max_rounds > 0 && s.rounds >= s.max_rounds)) s.active = 0;
         }
+        __syncthreads();
+        // hyperedge rows of the next round's DP pass
+        if (s.active)
+            for (int32_t r = threadIdx.x; r < s.m; r += blockDim.x) {
+                s.e_f[r] = s.f[s.e_c2o[r]];
+                s.e_s[r] = 0;
+                s.e_del[r] = 0;
+            }
     }
     if (threadIdx.x == 0 && ctr) {
         atomicAdd(&ctr->active, s.active);
@@ -510,8 +489,18 @@ __global__ void __launch_bounds__(256) k_pop_contract(InstState *st, const Plan 
 
 // --------------------------------------------------------------- results --
 
-__global__ void k_alive_masks(const InstState *st, uint8_t *alive_v, uint8_t *alive_e) {
-    const InstState &s = *st;
+// Alive masks over the input ids; blockIdx.y = instance.  With `batch`
+// set, instance b writes at its offsets v_base / e_base of the
+// concatenated masks; otherwise at 0.
+__global__ void k_alive_masks(const InstState *st, int count, bool batch, uint8_t *alive_v,
+                              uint8_t *alive_e) {
+    const int b = blockIdx.y;
+    if (b >= count) return;
+    const InstState &s = st[b];
+    if (batch) {
+        alive_v += s.v_base;
+        alive_e += s.e_base;
+    }
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)s.n0 + s.m0;
          i += (int64_t)gridDim.x * blockDim.x) {
         if (i < s.n0) alive_v[i] = s.v_o2c[i] >= 0;
@@ -525,24 +514,45 @@ __global__ void k_alive_masks(const InstState *st, uint8_t *alive_v, uint8_t *al
 
 static int grid_for(int sms, int per_sm) { return sms * per_sm; }
 
-cudaError_t launch_validate(InstState *st, cudaStream_t s) {
-    k_validate<<<256, 256, 0, s>>>(st);
+cudaError_t launch_validate(InstState *st, int count, cudaStream_t s) {
+    k_validate<<<dim3(count > 1 ? 16 : 256, count), 256, 0, s>>>(st, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_localize_ptr(InstState *st, int count, const int64_t *gptr, const int64_t *e0,
+                                cudaStream_t s) {
+    k_localize_ptr<<<dim3(16, count), 256, 0, s>>>(st, count, gptr, e0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_bounds(const int64_t *gptr, const int64_t *e0, int64_t *out, int count,
+                                 cudaStream_t s) {
+    k_gather_bounds<<<(count + 256) / 256, 256, 0, s>>>(gptr, e0, out, count);
     return cudaGetLastError();
 }
 
 cudaError_t launch_build(InstState *st, int count, int32_t max_rounds, int64_t max_nnz,
                          int64_t max_m, int64_t max_n, cudaStream_t s) {
-    int64_t work = max_nnz > max_m ? max_nnz : max_m;
-    if (max_n + 1 > work) work = max_n + 1;
-    int gx = (int)((work + 255) / 256);
+    (void)max_nnz;
+    (void)max_n;
+    int gx = (int)((max_m + 255) / 256);
     if (gx > 1024) gx = 1024;
     if (gx < 1) gx = 1;
-    dim3 g1(gx, count);
-    k_csc_zero<<<g1, 256, 0, s>>>(st, count);
-    k_csc_count<<<g1, 256, 0, s>>>(st, count, nullptr);
-    k_csc_scan_init<<<count, 1024, 0, s>>>(st, count, max_rounds);
-    k_csc_fill<<<g1, 256, 0, s>>>(st, count);
+    k_inc_build<<<dim3(gx, count), 256, 0, s>>>(st, count);
+    k_init<<<count, 1024, 0, s>>>(st, count, max_rounds);
     return cudaGetLastError();
+}
+
+template <int kPhase>
+static void launch_scatter(InstState *st, const Plan *plan, bool set, bool dense, int grid,
+                           cudaStream_t s) {
+    if (set) {
+        if (dense) k_scatter<kPhase, true, true><<<grid, 256, 0, s>>>(st, plan);
+        else k_scatter<kPhase, true, false><<<grid, 256, 0, s>>>(st, plan);
+    } else {
+        if (dense) k_scatter<kPhase, false, true><<<grid, 256, 0, s>>>(st, plan);
+        else k_scatter<kPhase, false, false><<<grid, 256, 0, s>>>(st, plan);
+    }
 }
 
 cudaError_t launch_round_phase(InstState *st, Plan *plan, BatchCounters *ctr, int count,
@@ -551,14 +561,9 @@ cudaError_t launch_round_phase(InstState *st, Plan *plan, BatchCounters *ctr, in
                                cudaEvent_t ev_contract_end) {
     const bool tc = contraction == kFp8;
     k_plan<<<1, 1024, 0, s>>>(st, plan, phase, tc ? 1 : 0, ctr);
-    const int enc_grid = grid_for(sms, 8);
-    if (phase == 0) {
-        if (tc) k_encode_edges<true><<<enc_grid, 256, 0, s>>>(st, plan);
-        else k_encode_edges<false><<<enc_grid, 256, 0, s>>>(st, plan);
-    } else {
-        if (tc) k_encode_vertices<true><<<enc_grid, 256, 0, s>>>(st, plan);
-        else k_encode_vertices<false><<<enc_grid, 256, 0, s>>>(st, plan);
-    }
+    const int grid = grid_for(sms, 8);
+    if (phase == 0) launch_scatter<0>(st, plan, true, tc, grid, s);
+    else launch_scatter<1>(st, plan, true, tc, grid, s);
     if (ev_contract_begin) cudaEventRecordWithFlags(ev_contract_begin, s, cudaEventRecordExternal);
     if (tc) {
         cudaError_t e = launch_tc_contract(st, plan, phase, sms, kerr, s);
@@ -567,6 +572,8 @@ cudaError_t launch_round_phase(InstState *st, Plan *plan, BatchCounters *ctr, in
         k_pop_contract<<<grid_for(sms, 6), 256, 0, s>>>(st, plan, phase);
     }
     if (ev_contract_end) cudaEventRecordWithFlags(ev_contract_end, s, cudaEventRecordExternal);
+    if (phase == 0) launch_scatter<0>(st, plan, false, tc, grid, s);
+    else launch_scatter<1>(st, plan, false, tc, grid, s);
     if (phase == 0) k_compact_edges<<<count, 1024, 0, s>>>(st, count);
     else k_compact_vertices<<<count, 1024, 0, s>>>(st, count, ctr);
     return cudaGetLastError();
@@ -574,7 +581,13 @@ cudaError_t launch_round_phase(InstState *st, Plan *plan, BatchCounters *ctr, in
 
 cudaError_t launch_alive_masks(const InstState *st, uint8_t *alive_v, uint8_t *alive_e,
                                cudaStream_t s) {
-    k_alive_masks<<<152, 256, 0, s>>>(st, alive_v, alive_e);
+    k_alive_masks<<<dim3(152, 1), 256, 0, s>>>(st, 1, false, alive_v, alive_e);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_alive_masks_batch(const InstState *st, int count, uint8_t *alive_v,
+                                     uint8_t *alive_e, cudaStream_t s) {
+    k_alive_masks<<<dim3(4, count), 256, 0, s>>>(st, count, true, alive_v, alive_e);
     return cudaGetLastError();
 }
 

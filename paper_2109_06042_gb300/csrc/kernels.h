@@ -22,7 +22,11 @@ struct BatchCounters {
     int32_t status_any;
 };
 
-cudaError_t launch_validate(InstState *st, cudaStream_t s);
+cudaError_t launch_validate(InstState *st, int count, cudaStream_t s);
+cudaError_t launch_localize_ptr(InstState *st, int count, const int64_t *gptr, const int64_t *e0,
+                                cudaStream_t s);
+cudaError_t launch_gather_bounds(const int64_t *gptr, const int64_t *e0, int64_t *out, int count,
+                                 cudaStream_t s);
 cudaError_t launch_build(InstState *st, int count, int32_t max_rounds, int64_t max_nnz,
                          int64_t max_m, int64_t max_n, cudaStream_t s);
 // One phase of a round: phase 0 = DP (Algorithm 1), phase 1 = MD (Algorithm 2).
@@ -32,6 +36,8 @@ cudaError_t launch_round_phase(InstState *st, Plan *plan, BatchCounters *ctr, in
                                cudaEvent_t ev_contract_end);
 cudaError_t launch_alive_masks(const InstState *st, uint8_t *alive_v, uint8_t *alive_e,
                                cudaStream_t s);
+cudaError_t launch_alive_masks_batch(const InstState *st, int count, uint8_t *alive_v,
+                                     uint8_t *alive_e, cudaStream_t s);
 
 // tcgen05 contraction (contract_tc.cu)
 cudaError_t launch_tc_contract(InstState *st, Plan *plan, int phase, int sms, int32_t *kerr,

@@ -107,6 +107,7 @@ struct mhs_instance {
     // arena offsets of the batch-wide input arrays
     int64_t in_eptr = 0, in_evtx = 0, in_f = 0;
     int64_t sum_m1 = 0, sum_nnz = 0, sum_m = 0;
+    int64_t dense_off = 0, dense_bytes = 0;
     // round graphs: graph[0] plain, graph[1] with timing events
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     // timing
@@ -173,7 +174,7 @@ mhs_status validate_host(int32_t n, int32_t m, const int64_t *eptr64, const int3
 }
 
 struct Layout {  // byte offsets inside the arena for one instance
-    int64_t eptr, evtx, f, vptr, vedg;
+    int64_t eptr, evtx, f, inc_e;
     int64_t v_o2c, v_c2o, e_o2c, e_c2o, e_f, e_s, v_deg, v_maxf, v_cnt, e_del, v_del;
     int64_t A, At, Ab, Atb;
 };
@@ -233,8 +234,7 @@ mhs_status create(int32_t count, const int32_t *n, const int32_t *m, const int64
         c_m1 += m0 + 1;
         c_z += z;
         c_m += m0;
-        L.vptr = ar.take(4 * (n0 + 1));
-        L.vedg = ar.take(4 * z);
+        L.inc_e = ar.take(4 * z);
         L.v_o2c = ar.take(4 * n0);
         L.v_c2o = ar.take(4 * n0);
         L.e_o2c = ar.take(4 * m0);
@@ -246,6 +246,13 @@ mhs_status create(int32_t count, const int32_t *n, const int32_t *m, const int64
         L.v_cnt = ar.take(4 * n0);
         L.e_del = ar.take(m0);
         L.v_del = ar.take(n0);
+    }
+    // the operands of all instances, contiguous, zeroed once at load: the
+    // scatter/clear passes leave them all-zero between phases
+    const int64_t off_dense0 = ar.bytes;
+    for (int b = 0; b < count; ++b) {
+        Layout &L = lay[b];
+        const int64_t n0 = n[b], m0 = m[b];
         const int64_t arows = round_up(std::max<int64_t>(m0, 1), kRowAlign);
         const int64_t atrows = round_up(std::max<int64_t>(n0, 1), kRowAlign);
         if (dense) {
@@ -258,10 +265,12 @@ mhs_status create(int32_t count, const int32_t *n, const int32_t *m, const int64
             L.A = L.At = -1;
         }
     }
+    h->dense_off = off_dense0;
+    h->dense_bytes = ar.bytes - off_dense0;
     // batch-level objects
     const int64_t off_state = ar.take((int64_t)sizeof(InstState) * count);
     const int64_t off_plan = ar.take(sizeof(Plan));
-    const int64_t off_rowoff = ar.take(4 * (int64_t)(count + 1));
+    const int64_t off_incoff = ar.take(8 * (int64_t)(count + 1));
     const int64_t off_tileoff = ar.take(8 * (int64_t)(count + 1));
     const int64_t off_ctr = ar.take(sizeof(BatchCounters));
     const int64_t off_kerr = ar.take(4);
@@ -290,10 +299,15 @@ mhs_status create(int32_t count, const int32_t *n, const int32_t *m, const int64
         return fail(MHS_ENOMEM, "pinned host allocation failed");
     }
     h->hstate.resize(count);
+    int64_t vbase = 0, ebase = 0;
     for (int b = 0; b < count; ++b) {
         const Layout &L = lay[b];
         InstState s;
         std::memset(&s, 0, sizeof(s));
+        s.v_base = vbase;
+        s.e_base = ebase;
+        vbase += n[b];
+        ebase += m[b];
         s.n0 = n[b];
         s.m0 = m[b];
         s.nnz0 = nnz[b];
@@ -301,8 +315,7 @@ mhs_status create(int32_t count, const int32_t *n, const int32_t *m, const int64
         s.eptr = reinterpret_cast<int32_t *>(base + L.eptr);
         s.evtx = reinterpret_cast<int32_t *>(base + L.evtx);
         s.f = reinterpret_cast<int32_t *>(base + L.f);
-        s.vptr = reinterpret_cast<int32_t *>(base + L.vptr);
-        s.vedg = reinterpret_cast<int32_t *>(base + L.vedg);
+        s.inc_e = reinterpret_cast<int32_t *>(base + L.inc_e);
         s.v_o2c = reinterpret_cast<int32_t *>(base + L.v_o2c);
         s.v_c2o = reinterpret_cast<int32_t *>(base + L.v_c2o);
         s.e_o2c = reinterpret_cast<int32_t *>(base + L.e_o2c);
@@ -338,7 +351,7 @@ mhs_status create(int32_t count, const int32_t *n, const int32_t *m, const int64
     Plan p;
     std::memset(&p, 0, sizeof(p));
     p.count = count;
-    p.row_off = reinterpret_cast<int32_t *>(base + off_rowoff);
+    p.inc_off = reinterpret_cast<int64_t *>(base + off_incoff);
     p.tile_off = reinterpret_cast<int64_t *>(base + off_tileoff);
     ce = cudaMemcpyAsync(h->dplan, &p, sizeof(p), cudaMemcpyHostToDevice, h->stream);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(h->dkerr, 0, 4, h->stream);
@@ -371,9 +384,19 @@ mhs_status finish_load(mhs_instance *h, int64_t tmap_off) {
     }
     CUDA_TRY(cudaMemcpyAsync(h->dstate, h->hstate.data(), sizeof(InstState) * h->count,
                              cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(cudaMemsetAsync(h->arena + h->dense_off, 0, (size_t)h->dense_bytes, h->stream));
     CUDA_TRY(launch_build(h->dstate, h->count, h->opt.max_rounds, h->max_nnz, h->max_m,
                           h->max_n, h->stream));
     return MHS_OK;
+}
+
+const char *status_text(int32_t st) {
+    if (st & kErrBadVertex) return "vertex id out of range";
+    if (st & kErrBadPtr) return "bad edge_ptr";
+    if (st & kErrBadDemand) return "demand < 1";
+    if (st & kErrCapacity) return "index beyond capacity";
+    if (st & kErrTimeout) return "bounded wait timed out";
+    return "unknown";
 }
 
 mhs_status check_device_status(mhs_instance *h) {
@@ -551,7 +574,7 @@ mhs_status mhs_load_device(int32_t n, int32_t m, const int32_t *edge_ptr, const 
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h->dstate, h->hstate.data(), sizeof(InstState), cudaMemcpyHostToDevice,
                             h->stream);
-    if (e == cudaSuccess) e = launch_validate(h->dstate, h->stream);
+    if (e == cudaSuccess) e = launch_validate(h->dstate, 1, h->stream);
     int32_t status = 0;
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(&status, &h->dstate->status, 4, cudaMemcpyDeviceToHost, h->stream);
@@ -563,7 +586,7 @@ mhs_status mhs_load_device(int32_t n, int32_t m, const int32_t *edge_ptr, const 
     if (status) {
         destroy(h);
         return fail(MHS_EINVAL, "malformed device instance (status 0x%x: %s)", status,
-                    (status & kErrBadVertex) ? "vertex id out of range" : "bad edge_ptr");
+                    status_text(status));
     }
     st = finish_load(h, tmoff);
     if (st == MHS_OK && cudaStreamSynchronize(h->stream) != cudaSuccess)
@@ -647,6 +670,109 @@ mhs_status mhs_load_batch(int32_t count, const int32_t *n, const int32_t *m,
     return MHS_OK;
 }
 
+mhs_status mhs_load_batch_device(int32_t count, const int32_t *n, const int32_t *m,
+                                 const int64_t *edge_ptr, const int32_t *edge_vtx,
+                                 const int32_t *demand, const int64_t *k,
+                                 const mhs_options *opt, void *cuda_stream, mhs_instance **out) {
+    if (!out) return fail(MHS_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (count < 1 || count > (1 << 20)) return fail(MHS_EINVAL, "count must be in [1, 2^20]");
+    if (!n || !m || !edge_ptr || !k) return fail(MHS_EINVAL, "NULL input array");
+    std::vector<int64_t> eoff(count + 1, 0);
+    for (int b = 0; b < count; ++b) {
+        if (n[b] < 0 || m[b] < 0) return fail(MHS_EINVAL, "instance %d: n or m < 0", b);
+        if (n[b] >= (1 << 24) || m[b] >= (1 << 24))
+            return fail(MHS_EINVAL, "instance %d: n and m must be < 2^24", b);
+        eoff[b + 1] = eoff[b] + m[b];
+    }
+    if (eoff[count] > 0 && !demand) return fail(MHS_EINVAL, "demand is NULL");
+    cudaStream_t cs = static_cast<cudaStream_t>(cuda_stream);
+    // instance boundaries in the device CSR: gather edge_ptr[eoff[b]]
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    cudaMemPool_t pool;
+    CUDA_TRY(pool_for(dev, &pool));
+    int64_t *tmp = nullptr;
+    CUDA_TRY(cudaMallocFromPoolAsync(reinterpret_cast<void **>(&tmp),
+                                     sizeof(int64_t) * 2 * ((size_t)count + 1), pool, cs));
+    std::vector<int64_t> bounds(count + 1);
+    cudaError_t e = cudaMemcpyAsync(tmp, eoff.data(), sizeof(int64_t) * (count + 1),
+                                    cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = launch_gather_bounds(edge_ptr, tmp, tmp + count + 1, count, cs);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(bounds.data(), tmp + count + 1, sizeof(int64_t) * (count + 1),
+                            cudaMemcpyDeviceToHost, cs);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(tmp, cs);
+        return fail(MHS_ECUDA, "batch bounds: %s", cudaGetErrorString(e));
+    }
+    std::vector<int64_t> nnz(count);
+    for (int b = 0; b < count; ++b) {
+        nnz[b] = bounds[b + 1] - bounds[b];
+        if (nnz[b] < 0 || nnz[b] >= (1ll << 31)) {
+            cudaFreeAsync(tmp, cs);
+            return fail(MHS_EINVAL, "instance %d: bad edge_ptr range", b);
+        }
+    }
+    if (bounds[0] != 0) {
+        cudaFreeAsync(tmp, cs);
+        return fail(MHS_EINVAL, "edge_ptr[0] must be 0");
+    }
+    const int64_t total_nnz = bounds[count];
+    if (total_nnz > 0 && !edge_vtx) {
+        cudaFreeAsync(tmp, cs);
+        return fail(MHS_EINVAL, "edge_vtx is NULL");
+    }
+    std::vector<Layout> lay;
+    int64_t tmoff = 0;
+    mhs_instance *h = nullptr;
+    mhs_status st = create(count, n, m, nnz.data(), k, opt, cuda_stream, &h, lay, tmoff);
+    if (st) {
+        cudaFreeAsync(tmp, cs);
+        return st;
+    }
+    // device-to-device: vertex ids and demands in one copy each, local offsets by a kernel
+    e = cudaSuccess;
+    if (h->sum_nnz > 0)
+        e = cudaMemcpyAsync(h->arena + h->in_evtx, edge_vtx, 4 * (size_t)h->sum_nnz,
+                            cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess && h->sum_m > 0)
+        e = cudaMemcpyAsync(h->arena + h->in_f, demand, 4 * (size_t)h->sum_m,
+                            cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->dstate, h->hstate.data(), sizeof(InstState) * count,
+                            cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = launch_localize_ptr(h->dstate, count, edge_ptr, tmp, h->stream);
+    if (e == cudaSuccess) e = launch_validate(h->dstate, count, h->stream);
+    std::vector<InstState> chk(count);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(chk.data(), h->dstate, sizeof(InstState) * count,
+                            cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFreeAsync(tmp, h->stream);
+    if (e != cudaSuccess) {
+        destroy(h);
+        return fail(MHS_ECUDA, "batch device load: %s", cudaGetErrorString(e));
+    }
+    for (int b = 0; b < count; ++b)
+        if (chk[b].status) {
+            const int32_t sv = chk[b].status;
+            destroy(h);
+            return fail(MHS_EINVAL, "instance %d malformed (status 0x%x: %s)", b, sv,
+                        status_text(sv));
+        }
+    st = finish_load(h, tmoff);
+    if (st == MHS_OK && cudaStreamSynchronize(h->stream) != cudaSuccess)
+        st = fail(MHS_ECUDA, "load failed");
+    if (st) {
+        destroy(h);
+        return st;
+    }
+    *out = h;
+    return MHS_OK;
+}
+
 int32_t mhs_count(const mhs_instance *inst) { return inst ? inst->count : 0; }
 
 mhs_status mhs_reduce_round(mhs_instance *inst, mhs_round_stats *stats) {
@@ -710,6 +836,30 @@ mhs_status mhs_result_device(const mhs_instance *inst, int32_t index, uint8_t *a
     if (index < 0 || index >= inst->count) return fail(MHS_EINVAL, "index out of range");
     if (!alive_v || !alive_e) return fail(MHS_EINVAL, "NULL output");
     CUDA_TRY(launch_alive_masks(inst->dstate + index, alive_v, alive_e, inst->stream));
+    return MHS_OK;
+}
+
+mhs_status mhs_result_batch_device(const mhs_instance *inst, uint8_t *alive_v,
+                                   uint8_t *alive_e) {
+    if (!inst) return fail(MHS_EINVAL, "instance is NULL");
+    if (!alive_v || !alive_e) return fail(MHS_EINVAL, "NULL output");
+    CUDA_TRY(launch_alive_masks_batch(inst->dstate, inst->count, alive_v, alive_e, inst->stream));
+    return MHS_OK;
+}
+
+mhs_status mhs_trace_at(const mhs_instance *inst, int32_t index, int32_t *rows_out,
+                        int32_t cap_rounds, int32_t *rounds_out) {
+    if (!inst) return fail(MHS_EINVAL, "instance is NULL");
+    if (index < 0 || index >= inst->count) return fail(MHS_EINVAL, "index out of range");
+    InstState s;
+    CUDA_TRY(cudaMemcpyAsync(&s, inst->dstate + index, sizeof(s), cudaMemcpyDeviceToHost,
+                             inst->stream));
+    CUDA_TRY(cudaStreamSynchronize(inst->stream));
+    if (rounds_out) *rounds_out = s.rounds;
+    const int32_t nr = std::min(std::min(s.rounds, cap_rounds), (int32_t)kTraceRounds);
+    if (rows_out)
+        for (int32_t r = 0; r < nr; ++r)
+            for (int c = 0; c < 3; ++c) rows_out[3 * r + c] = s.trace[r][c];
     return MHS_OK;
 }
 

@@ -20,6 +20,7 @@ constexpr int kTcM = 128;        // tcgen05 contraction: 128 rows (i) ...
 constexpr int kTcN = 256;        // ... x 256 columns (j) per tile
 constexpr int kTcK = 128;        // K bytes per pipeline stage (FP8)
 constexpr int kRowAlign = 256;   // row capacity rounded to this
+constexpr int kTraceRounds = 32; // rounds whose sizes an instance records
 
 enum Contraction : int32_t { kAuto = 0, kFp8 = 1, kPopcount = 2 };
 
@@ -29,6 +30,7 @@ enum : int32_t {
     kErrBadPtr = 2,        // edge_ptr not monotone / inconsistent
     kErrTimeout = 4,       // a bounded wait gave up
     kErrCapacity = 8,      // an index exceeded an allocated capacity
+    kErrBadDemand = 16,    // a demand f(e) < 1 in the input
 };
 
 struct InstState {
@@ -38,8 +40,7 @@ struct InstState {
     const int32_t *eptr;   // [m0+1] (int32 offsets into evtx)
     const int32_t *evtx;   // [nnz0] vertex ids
     const int32_t *f;      // [m0] demands
-    const int32_t *vptr;   // [n0+1] vertex -> hyperedge lists (built on device)
-    const int32_t *vedg;   // [nnz0]
+    int32_t *inc_e;        // [nnz0] hyperedge of each incidence (built on device)
     int64_t k;
 
     // ---- round state ----
@@ -78,16 +79,19 @@ struct InstState {
     // tcgen05 tensor maps (CUtensorMap, 128 bytes each) for A and At, in device memory
     const void *tmap_A;
     const void *tmap_At;
+    // offsets of this instance's ids in the concatenated ids of its batch
+    int64_t v_base, e_base;
+    // per round r < kTraceRounds: hyperedges and vertices entering DP, hyperedges after DP
+    int32_t trace[kTraceRounds][3];
 };
 
 // Per-phase work plan over a batch, rebuilt on the device before each phase.
 struct Plan {
     int32_t count;          // instances
-    int32_t total_rows;     // rows to encode this phase
-    int64_t total_tiles;    // contraction tiles this phase
     int32_t any_active;
-    int32_t pad_;
-    int32_t *row_off;       // [count+1] prefix of rows
+    int64_t total_inc;      // incidences to scatter this phase
+    int64_t total_tiles;    // contraction tiles this phase
+    int64_t *inc_off;       // [count+1] prefix of incidences of active instances
     int64_t *tile_off;      // [count+1] prefix of tiles
 };
 

@@ -108,12 +108,11 @@ extern "C" mhs_status mhs_kernelize_noalloc(int32_t n, int32_t m, const int32_t 
     Take take;
     const int64_t o_state = take(sizeof(InstState));
     const int64_t o_plan = take(sizeof(Plan));
-    const int64_t o_rowoff = take(2 * sizeof(int32_t));
+    const int64_t o_incoff = take(2 * sizeof(int64_t));
     const int64_t o_tileoff = take(2 * sizeof(int64_t));
     const int64_t o_ctr = take(sizeof(BatchCounters));
     const int64_t o_kerr = take(sizeof(int32_t));
-    const int64_t o_vptr = take(4 * ((int64_t)n + 1));
-    const int64_t o_vedg = take(4 * (int64_t)nnz);
+    const int64_t o_ince = take(4 * (int64_t)nnz);
     const int64_t o_vo2c = take(4 * (int64_t)n), o_vc2o = take(4 * (int64_t)n);
     const int64_t o_eo2c = take(4 * (int64_t)m), o_ec2o = take(4 * (int64_t)m);
     const int64_t o_ef = take(4 * (int64_t)m), o_es = take(4 * (int64_t)m);
@@ -134,8 +133,7 @@ extern "C" mhs_status mhs_kernelize_noalloc(int32_t n, int32_t m, const int32_t 
     st.eptr = edge_ptr;  // inputs are read in place
     st.evtx = edge_vtx;
     st.f = demand;
-    st.vptr = reinterpret_cast<int32_t *>(base + o_vptr);
-    st.vedg = reinterpret_cast<int32_t *>(base + o_vedg);
+    st.inc_e = reinterpret_cast<int32_t *>(base + o_ince);
     st.v_o2c = reinterpret_cast<int32_t *>(base + o_vo2c);
     st.v_c2o = reinterpret_cast<int32_t *>(base + o_vc2o);
     st.e_o2c = reinterpret_cast<int32_t *>(base + o_eo2c);
@@ -157,7 +155,7 @@ extern "C" mhs_status mhs_kernelize_noalloc(int32_t n, int32_t m, const int32_t 
     Plan pl;
     std::memset(&pl, 0, sizeof(pl));
     pl.count = 1;
-    pl.row_off = reinterpret_cast<int32_t *>(base + o_rowoff);
+    pl.inc_off = reinterpret_cast<int64_t *>(base + o_incoff);
     pl.tile_off = reinterpret_cast<int64_t *>(base + o_tileoff);
 
     InstState *dst = reinterpret_cast<InstState *>(base + o_state);
@@ -169,7 +167,7 @@ extern "C" mhs_status mhs_kernelize_noalloc(int32_t n, int32_t m, const int32_t 
     cudaError_t e = cudaMemcpyAsync(dst, &st, sizeof(st), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dplan, &pl, sizeof(pl), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(dkerr, 0, sizeof(int32_t), s);
-    if (e == cudaSuccess) e = launch_validate(dst, s);
+    if (e == cudaSuccess) e = launch_validate(dst, 1, s);
     int32_t status = 0;
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(&status, &dst->status, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
@@ -177,7 +175,10 @@ extern "C" mhs_status mhs_kernelize_noalloc(int32_t n, int32_t m, const int32_t 
     if (e != cudaSuccess) return err(err_buf, err_cap, MHS_ECUDA, cudaGetErrorString(e));
     if (status) return err(err_buf, err_cap, MHS_EINVAL, "malformed instance (bad edge_ptr or vertex id)");
 
-    e = launch_build(dst, 1, 0, nnz, m, n, s);
+    // the bit-packed operands must start all-zero (a call that stopped early
+    // may have left incidences set)
+    e = cudaMemsetAsync(base + o_ab, 0, (size_t)(o_atb - o_ab + atrows * words(m) * 4), s);
+    if (e == cudaSuccess) e = launch_build(dst, 1, 0, nnz, m, n, s);
     if (e != cudaSuccess) return err(err_buf, err_cap, MHS_ECUDA, cudaGetErrorString(e));
     BatchCounters ctr;
     int32_t kerr = 0;

@@ -61,12 +61,16 @@ _SIGS = {
                                ctypes.POINTER(_vp)]),
     "mhs_load_batch": (_i32, [_i32, _P32, _P32, _P64, _P32, _P32, _P64, ctypes.POINTER(Options),
                               _vp, ctypes.POINTER(_vp)]),
+    "mhs_load_batch_device": (_i32, [_i32, _P32, _P32, _vp, _vp, _vp, _P64,
+                                     ctypes.POINTER(Options), _vp, ctypes.POINTER(_vp)]),
     "mhs_count": (_i32, [_vp]),
     "mhs_reduce_round": (_i32, [_vp, ctypes.POINTER(RoundStats)]),
     "mhs_kernelize": (_i32, [_vp, ctypes.POINTER(RoundStats)]),
     "mhs_result_at": (_i32, [_vp, _i32, _P32, _i32, _P32, _P32, _P32, _i32, _P32, _P64, _P32]),
     "mhs_result": (_i32, [_vp, _P32, _i32, _P32, _P32, _P32, _i32, _P32, _P64, _P32]),
     "mhs_result_device": (_i32, [_vp, _i32, _vp, _vp]),
+    "mhs_result_batch_device": (_i32, [_vp, _vp, _vp]),
+    "mhs_trace_at": (_i32, [_vp, _i32, _P32, _i32, _P32]),
     "mhs_export": (_i32, [_vp, _i32, _P32, _i32, _P32, _i64, _P32, _P32, _P32, _P64]),
     "mhs_set_timing": (_i32, [_vp, _i32]),
     "mhs_last_timing": (_i32, [_vp, ctypes.POINTER(ctypes.c_float)]),
@@ -190,6 +194,24 @@ class Instance:
                                     ctypes.byref(opt), _stream_ptr(stream), ctypes.byref(h)))
         return cls(h)
 
+    @classmethod
+    def load_batch_device(cls, n, m, k, edge_ptr, edge_vtx, demand, contraction="auto",
+                          max_rounds=0, use_graphs=True, stream=None):
+        """mhs_load_batch_device: n, m, k host numpy arrays; edge_ptr (int64),
+        edge_vtx, demand (int32) CUDA tensors over the concatenated instances."""
+        n = np.ascontiguousarray(n, dtype=np.int32)
+        m = np.ascontiguousarray(m, dtype=np.int32)
+        k = np.ascontiguousarray(k, dtype=np.int64)
+        opt = make_options(contraction, max_rounds, use_graphs)
+        h = ctypes.c_void_p()
+        _check(lib().mhs_load_batch_device(int(n.size), _p32(n), _p32(m),
+                                           ctypes.c_void_p(edge_ptr.data_ptr()),
+                                           ctypes.c_void_p(edge_vtx.data_ptr()),
+                                           ctypes.c_void_p(demand.data_ptr()),
+                                           k.ctypes.data_as(_P64), ctypes.byref(opt),
+                                           _stream_ptr(stream), ctypes.byref(h)))
+        return cls(h)
+
     # ---- running ----
     def reduce_round(self) -> dict:
         st = RoundStats()
@@ -234,6 +256,18 @@ class Instance:
         """Write uint8 alive masks (CUDA tensors) over the input ids."""
         _check(lib().mhs_result_device(self._h, int(index), ctypes.c_void_p(alive_v.data_ptr()),
                                        ctypes.c_void_p(alive_e.data_ptr())))
+
+    def result_batch_device(self, alive_v, alive_e):
+        """Concatenated uint8 alive masks of all instances (CUDA tensors)."""
+        _check(lib().mhs_result_batch_device(self._h, ctypes.c_void_p(alive_v.data_ptr()),
+                                             ctypes.c_void_p(alive_e.data_ptr())))
+
+    def trace(self, index: int = 0):
+        """Per-round (hyperedges into DP, vertices into DP, hyperedges after DP)."""
+        rows = np.zeros((32, 3), np.int32)
+        r = ctypes.c_int32()
+        _check(lib().mhs_trace_at(self._h, int(index), _p32(rows), 32, ctypes.byref(r)))
+        return rows[:min(r.value, 32)].copy(), int(r.value)
 
     def export(self, index: int = 0):
         """The current reduced instance as (n, edge_ptr, edge_vtx, demand), renumbered."""

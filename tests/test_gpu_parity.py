@@ -220,3 +220,81 @@ def test_deterministic_repeats(mhs):
         again = mhs.kernelize(inst)
         for key in ("vertices", "edges", "rounds"):
             assert np.array_equal(first[key], again[key])
+
+
+def _concat(insts):
+    nnz = np.array([i.nnz for i in insts], np.int64)
+    base = np.concatenate([[0], np.cumsum(nnz)])
+    m_tot = sum(i.m for i in insts)
+    ptr = np.zeros(m_tot + 1, np.int64)
+    e0 = 0
+    for b, i in enumerate(insts):
+        ptr[e0:e0 + i.m + 1] = i.edge_ptr.astype(np.int64) + base[b]
+        e0 += i.m
+    vtx = np.concatenate([i.edge_vtx for i in insts] + [np.zeros(1, np.int32)])
+    dem = np.concatenate([i.demand for i in insts] + [np.zeros(1, np.int32)])
+    return ptr, vtx, dem
+
+
+def _oracle_trace_rows(inst):
+    """(hyperedges into DP, vertices into DP, hyperedges after DP) per round,
+    from the oracle's per-round deletion counts."""
+    _, _, _, _, tr = O.reduce_state(inst, trace_cap=64)
+    rows, m, n = [], inst.m, inst.n
+    for de, dv, am, an in tr.tolist():
+        rows.append([m, n, m - de])
+        m, n = am, an
+    return rows
+
+
+def test_batch_device_load_masks_and_trace(mhs):
+    import torch
+    insts = [I.config_batch_one(4100 + i) for i in range(20)]
+    insts += [I.from_edges(0, [], []), I.tiny_random(7), I.from_edges(4, [], [])]
+    ptr, vtx, dem = _concat(insts)
+    dev = torch.device("cuda:0")
+    n = np.array([i.n for i in insts], np.int32)
+    m = np.array([i.m for i in insts], np.int32)
+    k = np.array([i.k for i in insts], np.int64)
+    tp, tv, td = (torch.from_numpy(x).to(dev) for x in (ptr, vtx, dem))
+    refs = [O.reduce(i) for i in insts]
+    for mode in MODES:
+        with mhs.Instance.load_batch_device(n, m, k, tp, tv, td, contraction=mode) as h:
+            h.kernelize()
+            av = torch.zeros(int(n.sum()) + 1, dtype=torch.uint8, device=dev)
+            ae = torch.zeros(int(m.sum()) + 1, dtype=torch.uint8, device=dev)
+            h.result_batch_device(av, ae)
+            av, ae = av.cpu().numpy(), ae.cpu().numpy()
+            vb = eb = 0
+            for b, inst in enumerate(insts):
+                ref = refs[b]
+                _same(h.result(b), ref, f"{mode} instance {b}")
+                assert np.nonzero(av[vb:vb + inst.n])[0].tolist() == ref["vertices"].tolist()
+                assert np.nonzero(ae[eb:eb + inst.m])[0].tolist() == ref["edges"].tolist()
+                vb += inst.n
+                eb += inst.m
+                rows, rounds = h.trace(b)
+                assert rounds == ref["rounds"]
+                assert rows.tolist() == _oracle_trace_rows(inst)[:32], (mode, b)
+
+
+def test_batch_device_rejects_malformed(mhs):
+    import torch
+    insts = [I.config_batch_one(4200 + i) for i in range(5)]
+    insts[3].demand[2] = 0  # demand < 1 in instance 3
+    ptr, vtx, dem = _concat(insts)
+    dev = torch.device("cuda:0")
+    n = np.array([i.n for i in insts], np.int32)
+    m = np.array([i.m for i in insts], np.int32)
+    k = np.array([i.k for i in insts], np.int64)
+    tp, tv, td = (torch.from_numpy(x).to(dev) for x in (ptr, vtx, dem))
+    with pytest.raises(mhs.MhsError) as ei:
+        mhs.Instance.load_batch_device(n, m, k, tp, tv, td)
+    assert ei.value.status == mhs.MHS_EINVAL and "instance 3" in str(ei.value)
+    insts[3].demand[2] = 1
+    insts[1].edge_vtx[5] = insts[1].n  # vertex id out of range in instance 1
+    ptr, vtx, dem = _concat(insts)
+    tp, tv, td = (torch.from_numpy(x).to(dev) for x in (ptr, vtx, dem))
+    with pytest.raises(mhs.MhsError) as ei:
+        mhs.Instance.load_batch_device(n, m, k, tp, tv, td)
+    assert "instance 1" in str(ei.value)
