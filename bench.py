@@ -350,7 +350,7 @@ def run_ours(args, rank, world, dist):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(insts, desc, args.cpu_seconds)
 
-    load_kernels = 6 if batch else 4  # incl. the result-mask kernel
+    load_kernels = 5 if batch else 3  # load kernels incl. the result-mask kernel
     line = {
         "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),

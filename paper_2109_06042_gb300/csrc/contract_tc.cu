@@ -10,13 +10,14 @@
 // read them with tcgen05.ld and apply Algorithm 1 (DP) or Algorithm 2 (MD)
 // directly; the matrix I is never written.
 //
-// Warp roles (192 threads, one CTA per SM, persistent over the tile list):
+// Warp roles (320 threads, one CTA per SM, persistent over the tile list):
 //   warp 0      TMA producer: 128-byte-swizzled K slices of the i rows
 //               (128 x 128 B) and j rows (2 x 128 x 128 B) into a 4-stage
 //               shared-memory ring.
 //   warp 1      TMEM allocation (512 columns = two 128 x 256 FP32
 //               accumulators) and the single-thread tcgen05.mma issuer.
-//   warps 2-5   epilogue; warp w reads TMEM lanes 32*(w%4) .. +31.
+//   warps 2-9   epilogue; warp w reads TMEM lanes 32*(w%4) .. +31, warps
+//               2-5 columns 0-127 and warps 6-9 columns 128-255 of a tile.
 // Every mbarrier wait is bounded: on timeout the kernel records
 // kErrTimeout, stops issuing work, frees its TMEM and returns.
 #include <cuda.h>
@@ -38,8 +39,9 @@ constexpr int kBBytes = kTcN * kTcK;            // 32 KB
 constexpr int kStageBytes = kABytes + kBBytes;  // 48 KB
 constexpr int kAccCols = kTcN;                  // FP32 columns per accumulator
 constexpr int kTmemCols = 2 * kAccCols;         // 512
-constexpr int kThreads = 192;
-constexpr int kEpiThreads = 128;
+constexpr int kEpiWarps = 8;                    // two per TMEM lane quarter
+constexpr int kThreads = 64 + 32 * kEpiWarps;   // producer + MMA + epilogue
+constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr int kGroupRows = 8;                   // row blocks per L2 group
 constexpr uint64_t kWaitNs = 4000000000ull;     // 4 s bound on any wait
 
@@ -367,7 +369,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     } else {
         // ------------------------------------------------------ epilogue --
-        const int q = warp & 3;  // TMEM lane quarter
+        const int q = warp & 3;             // TMEM lane quarter
+        const int half = (warp - 2) >> 2;   // which 128 columns of the tile
         const int et = threadIdx.x - 64;
         int it = 0;
         TileInfo ti;
@@ -404,7 +407,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             {
                 const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + acc * kAccCols;
 #pragma unroll 1
-                for (int ch = 0; ch < kTcN / 32; ++ch) {
+                for (int ch = half * (kTcN / 64); ch < (half + 1) * (kTcN / 64); ++ch) {
                     float v[32];
                     tmem_ld32(taddr + ch * 32, v);
                     uint32_t colmask = 0;

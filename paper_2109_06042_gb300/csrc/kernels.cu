@@ -127,17 +127,6 @@ __global__ void k_gather_bounds(const int64_t *gptr, const int64_t *e0, int64_t 
         out[b] = gptr[e0[b]];
 }
 
-// Incidence -> hyperedge id (blockIdx.y = instance).
-__global__ void k_inc_build(InstState *st, int count) {
-    const int b = blockIdx.y;
-    if (b >= count) return;
-    InstState &s = st[b];
-    if (s.status) return;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < s.m0;
-         e += (int64_t)gridDim.x * blockDim.x)
-        for (int32_t p = s.eptr[e]; p < s.eptr[e + 1]; ++p) s.inc_e[p] = (int32_t)e;
-}
-
 // Round state, identity id maps and the hyperedge rows of round 1 (one
 // block per instance).
 __global__ void k_init(InstState *st, int count, int32_t max_rounds) {
@@ -163,28 +152,28 @@ __global__ void k_init(InstState *st, int count, int32_t max_rounds) {
 
 // phase 0: rows = current hyperedges (DP); phase 1: rows = current vertices (MD).
 __global__ void k_plan(InstState *st, Plan *plan, int phase, int tc, BatchCounters *ctr) {
+    __shared__ int32_t sh[33];
     __shared__ int64_t sh64[33];
     const int count = plan->count;
-    int64_t icarry = 0;
+    int32_t rcarry = 0;
     int64_t tcarry = 0;
     int32_t act_any = 0;
     for (int base = 0; base < count; base += blockDim.x) {
         int b = base + threadIdx.x;
-        int64_t inc = 0;
+        int32_t rows = 0;
         int64_t tiles = 0;
         if (b < count) {
             const InstState &s = st[b];
             if (s.active && s.status == 0) {
-                const int32_t rows = phase == 0 ? s.m : s.n;
-                inc = s.nnz0;
-                tiles = tc ? tc_tiles(rows) : pop_tiles(rows);
+                rows = phase == 0 ? s.m : s.m_dp;  // hyperedges to scatter
+                tiles = tc ? tc_tiles(phase == 0 ? s.m : s.n) : pop_tiles(phase == 0 ? s.m : s.n);
                 act_any = 1;
             }
         }
-        int64_t itot;
-        int64_t iex = block_exclusive_scan<int64_t>(inc, &itot, sh64);
-        if (b < count) plan->inc_off[b] = icarry + iex;
-        icarry += itot;
+        int32_t rtot;
+        int32_t rex = block_exclusive_scan<int32_t>(rows, &rtot, sh);
+        if (b < count) plan->row_off[b] = rcarry + rex;
+        rcarry += rtot;
         int64_t ttot;
         int64_t tex = block_exclusive_scan<int64_t>(tiles, &ttot, sh64);
         if (b < count) plan->tile_off[b] = tcarry + tex;
@@ -192,9 +181,9 @@ __global__ void k_plan(InstState *st, Plan *plan, int phase, int tc, BatchCounte
     }
     act_any = __syncthreads_or(act_any);
     if (threadIdx.x == 0) {
-        plan->inc_off[count] = icarry;
+        plan->row_off[count] = rcarry;
         plan->tile_off[count] = tcarry;
-        plan->total_inc = icarry;
+        plan->total_rows = rcarry;
         plan->total_tiles = tcarry;
         plan->any_active = act_any;
         if (phase == 0 && ctr) {
@@ -207,9 +196,10 @@ __global__ void k_plan(InstState *st, Plan *plan, int phase, int tc, BatchCounte
 
 // --------------------------------------------------------------- encode --
 
-// One thread per incidence (e, v) of the original instance.  Phase 0 sets
+// One thread per current hyperedge e' (rows of phase 0, K columns of phase
+// 1), walking the hyperedge's original vertex list.  Phase 0 sets
 // A[e'][v'] (rows = current hyperedges, K = current vertices) and counts
-// |e| (= I^E_ii); phase 1 sets At[v'][e''] (rows = current vertices, K =
+// |e| (= I^E_ii); phase 1 sets At[v'][e'] (rows = current vertices, K =
 // hyperedges alive after DP) and counts deg(v) (= I^V_jj) and the maximum
 // demand.  The operands are all-zero between phases: kClear writes zeros at
 // exactly the positions kSet wrote, with the same id maps, after the
@@ -217,50 +207,54 @@ __global__ void k_plan(InstState *st, Plan *plan, int phase, int tc, BatchCounte
 // already set, so a repeated id inside one hyperedge counts once.
 template <int kPhase, bool kSet, bool kDense>
 __global__ void k_scatter(InstState *st, const Plan *plan) {
-    const int64_t total = plan->total_inc;
-    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total;
-         g += (int64_t)gridDim.x * blockDim.x) {
-        const int b = find_owner(plan->inc_off, plan->count, g);
+    const int32_t total = plan->total_rows;
+    for (int32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < total;
+         g += gridDim.x * blockDim.x) {
+        const int b = find_owner(plan->row_off, plan->count, g);
         InstState &s = st[b];
-        const int64_t p = g - plan->inc_off[b];
-        const int32_t e = s.inc_e[p];
-        const int32_t v = s.evtx[p];
-        const int32_t ce = s.e_o2c[e], cv = s.v_o2c[v];
-        if (ce < 0 || cv < 0) continue;
-        const int32_t r = kPhase == 0 ? ce : cv;
-        const int32_t c = kPhase == 0 ? cv : ce;
+        const int32_t ce = g - plan->row_off[b];
+        const int32_t e = s.e_c2o[ce];
         const int32_t R = kPhase == 0 ? s.m : s.n;
         const int32_t K = kPhase == 0 ? s.n : s.m_dp;
-        if (r >= R || c >= K) { atomicOr(&s.status, kErrCapacity); continue; }
-        bool fresh = false;
-        if (kDense) {
-            uint8_t *row = (kPhase == 0 ? s.A : s.At) + (int64_t)r * (kPhase == 0 ? s.A_pitch : s.At_pitch);
-            if (kSet) {
-                uint32_t *w = reinterpret_cast<uint32_t *>(row + (c & ~3));
-                const uint32_t sh = 8u * (c & 3);
-                const uint32_t old = atomicOr(w, (uint32_t)kFp8One << sh);
-                fresh = ((old >> sh) & 0xffu) == 0;
+        int32_t fresh_cnt = 0;
+        for (int32_t p = s.eptr[e]; p < s.eptr[e + 1]; ++p) {
+            const int32_t cv = s.v_o2c[s.evtx[p]];
+            if (cv < 0) continue;
+            const int32_t r = kPhase == 0 ? ce : cv;
+            const int32_t c = kPhase == 0 ? cv : ce;
+            if (r >= R || c >= K) { atomicOr(&s.status, kErrCapacity); continue; }
+            bool fresh = false;
+            if (kDense) {
+                uint8_t *row = (kPhase == 0 ? s.A : s.At) +
+                               (int64_t)r * (kPhase == 0 ? s.A_pitch : s.At_pitch);
+                if (kSet) {
+                    uint32_t *w = reinterpret_cast<uint32_t *>(row + (c & ~3));
+                    const uint32_t sh = 8u * (c & 3);
+                    const uint32_t old = atomicOr(w, (uint32_t)kFp8One << sh);
+                    fresh = ((old >> sh) & 0xffu) == 0;
+                } else {
+                    row[c] = 0;
+                }
             } else {
-                row[c] = 0;
+                uint32_t *row = (kPhase == 0 ? s.Ab : s.Atb) +
+                                (int64_t)r * (kPhase == 0 ? s.Ab_pitch : s.Atb_pitch);
+                if (kSet) {
+                    const uint32_t bit = 1u << (c & 31);
+                    fresh = (atomicOr(&row[c >> 5], bit) & bit) == 0;
+                } else {
+                    row[c >> 5] = 0;  // every set bit of this word is cleared by some thread
+                }
             }
-        } else {
-            uint32_t *row = (kPhase == 0 ? s.Ab : s.Atb) +
-                            (int64_t)r * (kPhase == 0 ? s.Ab_pitch : s.Atb_pitch);
-            if (kSet) {
-                const uint32_t bit = 1u << (c & 31);
-                fresh = (atomicOr(&row[c >> 5], bit) & bit) == 0;
-            } else {
-                row[c >> 5] = 0;  // every set bit of this word is cleared by some thread
+            if (kSet && fresh) {
+                if (kPhase == 0) {
+                    ++fresh_cnt;
+                } else {
+                    atomicAdd(&s.v_deg[cv], 1);
+                    atomicMax(&s.v_maxf[cv], s.f[e]);
+                }
             }
         }
-        if (kSet && fresh) {
-            if (kPhase == 0) {
-                atomicAdd(&s.e_s[r], 1);
-            } else {
-                atomicAdd(&s.v_deg[r], 1);
-                atomicMax(&s.v_maxf[r], s.f[e]);
-            }
-        }
+        if (kSet && kPhase == 0) s.e_s[ce] = fresh_cnt;  // one thread owns the row
     }
 }
 
@@ -535,10 +529,7 @@ cudaError_t launch_build(InstState *st, int count, int32_t max_rounds, int64_t m
                          int64_t max_m, int64_t max_n, cudaStream_t s) {
     (void)max_nnz;
     (void)max_n;
-    int gx = (int)((max_m + 255) / 256);
-    if (gx > 1024) gx = 1024;
-    if (gx < 1) gx = 1;
-    k_inc_build<<<dim3(gx, count), 256, 0, s>>>(st, count);
+    (void)max_m;
     k_init<<<count, 1024, 0, s>>>(st, count, max_rounds);
     return cudaGetLastError();
 }

@@ -174,7 +174,7 @@ mhs_status validate_host(int32_t n, int32_t m, const int64_t *eptr64, const int3
 }
 
 struct Layout {  // byte offsets inside the arena for one instance
-    int64_t eptr, evtx, f, inc_e;
+    int64_t eptr, evtx, f;
     int64_t v_o2c, v_c2o, e_o2c, e_c2o, e_f, e_s, v_deg, v_maxf, v_cnt, e_del, v_del;
     int64_t A, At, Ab, Atb;
 };
@@ -234,7 +234,6 @@ mhs_status create(int32_t count, const int32_t *n, const int32_t *m, const int64
         c_m1 += m0 + 1;
         c_z += z;
         c_m += m0;
-        L.inc_e = ar.take(4 * z);
         L.v_o2c = ar.take(4 * n0);
         L.v_c2o = ar.take(4 * n0);
         L.e_o2c = ar.take(4 * m0);
@@ -270,7 +269,7 @@ mhs_status create(int32_t count, const int32_t *n, const int32_t *m, const int64
     // batch-level objects
     const int64_t off_state = ar.take((int64_t)sizeof(InstState) * count);
     const int64_t off_plan = ar.take(sizeof(Plan));
-    const int64_t off_incoff = ar.take(8 * (int64_t)(count + 1));
+    const int64_t off_rowoff = ar.take(4 * (int64_t)(count + 1));
     const int64_t off_tileoff = ar.take(8 * (int64_t)(count + 1));
     const int64_t off_ctr = ar.take(sizeof(BatchCounters));
     const int64_t off_kerr = ar.take(4);
@@ -315,7 +314,6 @@ mhs_status create(int32_t count, const int32_t *n, const int32_t *m, const int64
         s.eptr = reinterpret_cast<int32_t *>(base + L.eptr);
         s.evtx = reinterpret_cast<int32_t *>(base + L.evtx);
         s.f = reinterpret_cast<int32_t *>(base + L.f);
-        s.inc_e = reinterpret_cast<int32_t *>(base + L.inc_e);
         s.v_o2c = reinterpret_cast<int32_t *>(base + L.v_o2c);
         s.v_c2o = reinterpret_cast<int32_t *>(base + L.v_c2o);
         s.e_o2c = reinterpret_cast<int32_t *>(base + L.e_o2c);
@@ -351,7 +349,7 @@ mhs_status create(int32_t count, const int32_t *n, const int32_t *m, const int64
     Plan p;
     std::memset(&p, 0, sizeof(p));
     p.count = count;
-    p.inc_off = reinterpret_cast<int64_t *>(base + off_incoff);
+    p.row_off = reinterpret_cast<int32_t *>(base + off_rowoff);
     p.tile_off = reinterpret_cast<int64_t *>(base + off_tileoff);
     ce = cudaMemcpyAsync(h->dplan, &p, sizeof(p), cudaMemcpyHostToDevice, h->stream);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(h->dkerr, 0, 4, h->stream);

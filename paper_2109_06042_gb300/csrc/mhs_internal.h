@@ -40,7 +40,7 @@ struct InstState {
     const int32_t *eptr;   // [m0+1] (int32 offsets into evtx)
     const int32_t *evtx;   // [nnz0] vertex ids
     const int32_t *f;      // [m0] demands
-    int32_t *inc_e;        // [nnz0] hyperedge of each incidence (built on device)
+
     int64_t k;
 
     // ---- round state ----
@@ -89,9 +89,10 @@ struct InstState {
 struct Plan {
     int32_t count;          // instances
     int32_t any_active;
-    int64_t total_inc;      // incidences to scatter this phase
+    int32_t total_rows;     // current hyperedges to scatter this phase
+    int32_t pad_;
     int64_t total_tiles;    // contraction tiles this phase
-    int64_t *inc_off;       // [count+1] prefix of incidences of active instances
+    int32_t *row_off;       // [count+1] prefix of current hyperedges of active instances
     int64_t *tile_off;      // [count+1] prefix of tiles
 };
 

@@ -108,11 +108,10 @@ extern "C" mhs_status mhs_kernelize_noalloc(int32_t n, int32_t m, const int32_t 
     Take take;
     const int64_t o_state = take(sizeof(InstState));
     const int64_t o_plan = take(sizeof(Plan));
-    const int64_t o_incoff = take(2 * sizeof(int64_t));
+    const int64_t o_rowoff = take(2 * sizeof(int32_t));
     const int64_t o_tileoff = take(2 * sizeof(int64_t));
     const int64_t o_ctr = take(sizeof(BatchCounters));
     const int64_t o_kerr = take(sizeof(int32_t));
-    const int64_t o_ince = take(4 * (int64_t)nnz);
     const int64_t o_vo2c = take(4 * (int64_t)n), o_vc2o = take(4 * (int64_t)n);
     const int64_t o_eo2c = take(4 * (int64_t)m), o_ec2o = take(4 * (int64_t)m);
     const int64_t o_ef = take(4 * (int64_t)m), o_es = take(4 * (int64_t)m);
@@ -133,7 +132,6 @@ extern "C" mhs_status mhs_kernelize_noalloc(int32_t n, int32_t m, const int32_t 
     st.eptr = edge_ptr;  // inputs are read in place
     st.evtx = edge_vtx;
     st.f = demand;
-    st.inc_e = reinterpret_cast<int32_t *>(base + o_ince);
     st.v_o2c = reinterpret_cast<int32_t *>(base + o_vo2c);
     st.v_c2o = reinterpret_cast<int32_t *>(base + o_vc2o);
     st.e_o2c = reinterpret_cast<int32_t *>(base + o_eo2c);
@@ -155,7 +153,7 @@ extern "C" mhs_status mhs_kernelize_noalloc(int32_t n, int32_t m, const int32_t 
     Plan pl;
     std::memset(&pl, 0, sizeof(pl));
     pl.count = 1;
-    pl.inc_off = reinterpret_cast<int64_t *>(base + o_incoff);
+    pl.row_off = reinterpret_cast<int32_t *>(base + o_rowoff);
     pl.tile_off = reinterpret_cast<int64_t *>(base + o_tileoff);
 
     InstState *dst = reinterpret_cast<InstState *>(base + o_state);
