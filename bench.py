@@ -52,7 +52,7 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", choices=["powerlaw", "uniform", "interval", "batch"],
+    p.add_argument("--workload", choices=["powerlaw", "uniform", "interval", "batch", "stream"],
                    default="powerlaw")
     p.add_argument("--contraction", choices=["fp8", "popcount"], default="fp8")
     p.add_argument("--seed", type=int, default=0)
@@ -62,6 +62,10 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-loop", action="store_true", help="batch: skip the per-instance loop")
+    p.add_argument("--requests", type=int, default=1000, help="stream: requests per rate")
+    p.add_argument("--pool", type=int, default=300, help="stream: distinct request instances")
+    p.add_argument("--rates", type=str, default="0.25,0.5,1,1.5,2",
+                   help="stream: arrival rates as multiples of the saturating rate")
     return p.parse_args()
 
 
@@ -374,6 +378,91 @@ def run_ours(args, rank, world, dist):
     return line
 
 
+def run_stream(args, rank, world):
+    """Serving: Poisson arrivals of stream-shaped requests through the
+    continuous-batching server, against the plain one-instance-at-a-time form
+    (mhs_load + mhs_kernelize + mhs_result) on the same GPU."""
+    import torch
+    from paper_2109_06042_gb300 import build as B
+    B.build()
+    from paper_2109_06042_gb300 import instances as I
+    from paper_2109_06042_gb300 import mhs
+    rng = np.random.Generator(np.random.PCG64(777 + rank))
+    pool = [I.config_stream_one(50_000 + rank * 100_000 + i) for i in range(args.pool)]
+    order = rng.integers(0, len(pool), size=args.requests)
+    reqs = [pool[i] for i in order]
+    desc = (f"stream of {args.requests} requests per rate from {len(pool)} seeded instances "
+            f"(n log-uniform [100,20000], m~U[n,3n], |e|~U[2,16], f<=3)")
+    # plain form: service time of every request, back to back
+    for i in reqs[:3]:
+        mhs.kernelize(i, contraction=args.contraction)
+    torch.cuda.synchronize()
+    svc = np.zeros(len(reqs))
+    for j, i in enumerate(reqs):
+        t0 = time.perf_counter()
+        mhs.kernelize(i, contraction=args.contraction)
+        svc[j] = time.perf_counter() - t0
+    plain_rate = len(reqs) / svc.sum()
+
+    def serve(arrivals):
+        """Submit at the given arrival offsets (s); returns (latencies s, makespan s)."""
+        with mhs.Server(contraction=args.contraction) as srv:
+            t0 = time.perf_counter()
+            tickets = []
+            for a, inst in zip(arrivals, reqs):
+                now = time.perf_counter() - t0
+                if a > now:
+                    time.sleep(a - now)
+                tickets.append(srv.submit(inst))
+            lat = []
+            for t in tickets:
+                r = srv.poll(t, timeout_us=600_000_000)
+                lat.append(r["times_ns"][2] / 1e9)
+            makespan = time.perf_counter() - t0
+        return np.array(lat), makespan
+
+    # saturating rate: everything at once (closed loop)
+    serve(np.zeros(min(len(reqs), 64)))  # warm-up
+    lat0, mk0 = serve(np.zeros(len(reqs)))
+    sat = len(reqs) / mk0
+    sweep = []
+    for mult in [float(x) for x in args.rates.split(",")]:
+        rate = mult * sat
+        arr = np.cumsum(rng.exponential(1.0 / rate, size=len(reqs)))
+        lat, mk = serve(arr)
+        # plain form under the same arrivals: single FIFO server with the measured times
+        fin = np.zeros(len(reqs))
+        t = 0.0
+        for j in range(len(reqs)):
+            t = max(t, arr[j]) + svc[j]
+            fin[j] = t
+        plat = fin - arr
+        sweep.append({
+            "rate_per_s": round(rate, 2), "x_saturating": mult,
+            "served": {"p50_ms": round(1e3 * float(np.percentile(lat, 50)), 3),
+                       "p99_ms": round(1e3 * float(np.percentile(lat, 99)), 3),
+                       "instances_per_s": round(len(reqs) / mk, 2)},
+            "plain": {"p50_ms": round(1e3 * float(np.percentile(plat, 50)), 3),
+                      "p99_ms": round(1e3 * float(np.percentile(plat, 99)), 3),
+                      "instances_per_s": round(len(reqs) / fin[-1], 2)},
+        })
+    return {
+        "metric": "served instances/s (continuous batching) with p50/p99 latency",
+        "value": round(sat, 3), "unit": UNIT, "n_gpus": world, "steps": len(sweep),
+        "warmup": 1, "ms_per_step": round(1e3 * mk0, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "e4m3" if args.contraction == "fp8" else "u32-popcount", "data": DATA,
+        "config": {"workload": desc, "contraction": args.contraction,
+                   "server": "max_slots 256, budget 3/4 of free HBM"},
+        "serving": {"saturating_rate_per_s": round(sat, 2),
+                    "plain_rate_per_s": round(plain_rate, 2),
+                    "speedup_vs_plain": round(sat / plain_rate, 3),
+                    "closed_loop_p50_ms": round(1e3 * float(np.percentile(lat0, 50)), 3),
+                    "closed_loop_p99_ms": round(1e3 * float(np.percentile(lat0, 99)), 3),
+                    "sweep": sweep},
+    }
+
+
 def cpu_baseline(insts, desc, seconds):
     """The oracle, as it stands, on a bounded sample of the workload."""
     from oracle import oracle as O
@@ -446,6 +535,11 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if torch.cuda.is_available():
         torch.cuda.set_device(local)
+    if args.workload == "stream":
+        line = run_stream(args, rank, world)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        return
     dist = None
     if world > 1:
         import torch.distributed as Dd

@@ -259,6 +259,71 @@ mhs_status mhs_kernelize_noalloc(int32_t n, int32_t m, const int32_t *edge_ptr,
                                  uint8_t *alive_v, uint8_t *alive_e, int32_t *rounds_out,
                                  void *cuda_stream, char *err_buf, size_t err_cap);
 
+/* ------------------------------------------------------------------------ */
+/* Serving: continuous batching of independent requests on one GPU.          */
+/*                                                                          */
+/* The paper reduces one instance at a time; the server keeps many in      */
+/* flight.  A worker thread admits queued requests into free slots while   */
+/* their device footprint fits the HBM budget, runs one round of           */
+/* Algorithm 3 for all admitted instances at once (one captured CUDA graph */
+/* over the slot table), retires the instances that reached their          */
+/* fixpoint and admits new ones at every round boundary.  Each result is   */
+/* exactly what mhs_kernelize gives for the instance alone.                */
+/* ------------------------------------------------------------------------ */
+
+typedef struct mhs_server mhs_server;
+
+typedef struct {
+    int64_t hbm_budget_bytes; /* device bytes the admitted instances may hold (0: 3/4 of free) */
+    int32_t max_slots;        /* instances in flight at most, 1..4096 (default 256) */
+    int32_t queue_capacity;   /* queued requests at most; beyond it mhs_submit gives MHS_EBUSY */
+    int32_t contraction;      /* mhs_contraction */
+    int32_t reserved[3];      /* must be zero */
+} mhs_server_options;
+
+typedef struct {
+    int64_t submitted, admitted, completed, rounds;
+    int32_t pending, active;
+    int64_t bytes_in_use, peak_bytes, budget_bytes;
+} mhs_server_stats;
+
+mhs_status mhs_server_default_options(mhs_server_options *opt);
+
+/* Start a server on the current device; all its GPU work runs on cuda_stream
+ * (NULL: a stream of its own).  opt may be NULL (defaults). */
+mhs_status mhs_server_create(const mhs_server_options *opt, void *cuda_stream, mhs_server **out);
+
+/*
+ * Queue one request (HOST arrays, layout and checks of mhs_load; copied
+ * before the call returns).  *ticket identifies it for mhs_poll.
+ * MHS_EBUSY: the queue is full; MHS_ENOMEM: the instance alone exceeds the
+ * budget; MHS_EINVAL: malformed input.
+ */
+mhs_status mhs_submit(mhs_server *srv, int32_t n, int32_t m, const int32_t *edge_ptr,
+                      const int32_t *edge_vtx, const int32_t *demand, int64_t k,
+                      uint64_t *ticket);
+
+/*
+ * Wait up to timeout_us (0: do not wait, < 0: no limit) for request
+ * `ticket`.  MHS_EAGAIN if it is not finished.  When finished, the outputs
+ * are those of mhs_result; times_ns (may be NULL) receives 3 values: time
+ * queued, time in service, total (nanoseconds, server clock).  With all of
+ * vtx_out, edge_out and demand_out NULL only the counts are returned and
+ * the result is kept; otherwise it is copied out and released.
+ */
+mhs_status mhs_poll(mhs_server *srv, uint64_t ticket, int64_t timeout_us, int32_t *vtx_out,
+                    int32_t vtx_cap, int32_t *n_out, int32_t *edge_out, int32_t *demand_out,
+                    int32_t edge_cap, int32_t *m_out, int64_t *k_out, int32_t *rounds_out,
+                    int64_t *times_ns);
+
+/* Stop (paused != 0) or resume admitting queued requests; running ones finish. */
+mhs_status mhs_server_pause(mhs_server *srv, int32_t paused);
+
+mhs_status mhs_server_get_stats(mhs_server *srv, mhs_server_stats *out);
+
+/* Stop the worker, fail unfinished requests and free everything. */
+void mhs_server_destroy(mhs_server *srv);
+
 /* Free all device and host memory of the instance (synchronises its stream). */
 void mhs_free(mhs_instance *inst);
 

@@ -189,7 +189,7 @@ __global__ void k_plan(InstState *st, Plan *plan, int phase, int tc, BatchCounte
         if (phase == 0 && ctr) {
             ctr->active = 0; ctr->n_alive = 0; ctr->m_alive = 0; ctr->dp_deleted = 0;
             ctr->md_deleted = 0; ctr->max_rounds_seen = 0; ctr->changed_any = 0;
-            ctr->status_any = 0;
+            ctr->status_any = 0; ctr->n_done = 0;
         }
     }
 }
@@ -304,7 +304,8 @@ __global__ void k_compact_edges(InstState *st, int count) {
 
 // MD decision (Algorithm 2: delete v_j iff C_j >= max f over E(v_j)),
 // order-preserving compaction of the vertices, and round bookkeeping.
-__global__ void k_compact_vertices(InstState *st, int count, BatchCounters *ctr) {
+__global__ void k_compact_vertices(InstState *st, int count, BatchCounters *ctr,
+                                   int32_t *done_list) {
     __shared__ int32_t sh[33];
     const int b = blockIdx.x;
     if (b >= count) return;
@@ -332,7 +333,10 @@ __global__ void k_compact_vertices(InstState *st, int count, BatchCounters *ctr)
             s.m = s.m_dp;
             s.n = carry;
             s.rounds += 1;
-            if (!s.changed || (s.max_rounds > 0 && s.rounds >= s.max_rounds)) s.active = 0;
+            if (!s.changed || (s.max_rounds > 0 && s.rounds >= s.max_rounds)) {
+                s.active = 0;
+                if (done_list && ctr) done_list[atomicAdd(&ctr->n_done, 1)] = b;
+            }
         }
         __syncthreads();
         // hyperedge rows of the next round's DP pass
@@ -549,7 +553,7 @@ static void launch_scatter(InstState *st, const Plan *plan, bool set, bool dense
 cudaError_t launch_round_phase(InstState *st, Plan *plan, BatchCounters *ctr, int count,
                                int phase, int contraction, int sms, int32_t *kerr,
                                cudaStream_t s, cudaEvent_t ev_contract_begin,
-                               cudaEvent_t ev_contract_end) {
+                               cudaEvent_t ev_contract_end, int32_t *done_list) {
     const bool tc = contraction == kFp8;
     k_plan<<<1, 1024, 0, s>>>(st, plan, phase, tc ? 1 : 0, ctr);
     const int grid = grid_for(sms, 8);
@@ -566,7 +570,7 @@ cudaError_t launch_round_phase(InstState *st, Plan *plan, BatchCounters *ctr, in
     if (phase == 0) launch_scatter<0>(st, plan, false, tc, grid, s);
     else launch_scatter<1>(st, plan, false, tc, grid, s);
     if (phase == 0) k_compact_edges<<<count, 1024, 0, s>>>(st, count);
-    else k_compact_vertices<<<count, 1024, 0, s>>>(st, count, ctr);
+    else k_compact_vertices<<<count, 1024, 0, s>>>(st, count, ctr, done_list);
     return cudaGetLastError();
 }
 

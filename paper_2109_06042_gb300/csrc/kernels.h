@@ -20,6 +20,8 @@ struct BatchCounters {
     int32_t max_rounds_seen;
     int32_t changed_any;
     int32_t status_any;
+    int32_t n_done;           // instances that reached their fixpoint in the last round
+    int32_t pad_;
 };
 
 cudaError_t launch_validate(InstState *st, int count, cudaStream_t s);
@@ -30,10 +32,12 @@ cudaError_t launch_gather_bounds(const int64_t *gptr, const int64_t *e0, int64_t
 cudaError_t launch_build(InstState *st, int count, int32_t max_rounds, int64_t max_nnz,
                          int64_t max_m, int64_t max_n, cudaStream_t s);
 // One phase of a round: phase 0 = DP (Algorithm 1), phase 1 = MD (Algorithm 2).
+// done_list (may be NULL): receives the index of every instance that stops
+// in this round (phase 1); ctr->n_done counts them.
 cudaError_t launch_round_phase(InstState *st, Plan *plan, BatchCounters *ctr, int count,
                                int phase, int contraction, int sms, int32_t *kerr,
                                cudaStream_t s, cudaEvent_t ev_contract_begin,
-                               cudaEvent_t ev_contract_end);
+                               cudaEvent_t ev_contract_end, int32_t *done_list = nullptr);
 cudaError_t launch_alive_masks(const InstState *st, uint8_t *alive_v, uint8_t *alive_e,
                                cudaStream_t s);
 cudaError_t launch_alive_masks_batch(const InstState *st, int count, uint8_t *alive_v,

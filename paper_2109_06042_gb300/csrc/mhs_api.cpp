@@ -12,16 +12,16 @@
 #include <string>
 #include <vector>
 
+#include "host_internal.h"
 #include "kernels.h"
 #include "mhs_internal.h"
 
 using namespace mhs;
 
-namespace {
-
+namespace mhs {
 thread_local std::string g_err;
 
-mhs_status fail(mhs_status st, const char *fmt, ...) {
+mhs_status set_error(mhs_status st, const char *fmt, ...) {
     char buf[512];
     va_list ap;
     va_start(ap, fmt);
@@ -30,6 +30,11 @@ mhs_status fail(mhs_status st, const char *fmt, ...) {
     g_err = buf;
     return st;
 }
+}  // namespace mhs
+
+namespace {
+
+#define fail mhs::set_error
 
 #define CUDA_TRY(expr)                                                                   \
     do {                                                                                 \
@@ -45,11 +50,15 @@ inline int64_t kpad_words(int64_t K) {
     return round_up(std::max<int64_t>((K + 31) / 32, 1), 4);
 }
 
+}  // namespace
+
 // Library-owned stream-ordered memory pool (keeps freed blocks for reuse).
+namespace {
 std::mutex g_pool_mu;
 cudaMemPool_t g_pool[64] = {};
+}  // namespace
 
-cudaError_t pool_for(int dev, cudaMemPool_t *out) {
+cudaError_t mhs::pool_for(int dev, cudaMemPool_t *out) {
     std::lock_guard<std::mutex> lk(g_pool_mu);
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!g_pool[dev]) {
@@ -67,6 +76,8 @@ cudaError_t pool_for(int dev, cudaMemPool_t *out) {
     *out = g_pool[dev];
     return cudaSuccess;
 }
+
+namespace {
 
 // Sub-allocation plan of one arena.
 struct Arena {

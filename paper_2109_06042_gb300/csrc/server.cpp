@@ -1,0 +1,631 @@
+// server.cpp -- continuous-batching server: mhs_server_create / mhs_submit /
+// mhs_poll / mhs_server_destroy.
+//
+// A worker thread owns the GPU side.  Each iteration of its loop:
+//   1. admits pending requests into free slots while their device
+//      footprint fits the HBM budget (each admitted request gets its own
+//      arena from the library's memory pool, its inputs uploaded and its
+//      state written into the slot table);
+//   2. runs ONE round of Algorithm 3 (DP then MD) for every busy slot at
+//      once, by replaying a CUDA graph captured over the whole slot table;
+//   3. retires the slots whose instance reached its fixpoint in that round
+//      (the round kernels append them to a device-side done list): copies
+//      their results to the host, returns their arenas to the pool and
+//      wakes the pollers.
+// Requests that arrive while others are on the GPU join at the next round
+// boundary, so work of different sizes overlaps in the same launches.
+// The result of an instance does not depend on what else is in flight:
+// instances share no state, and every per-instance quantity lives in the
+// instance's own arena.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "host_internal.h"
+#include "kernels.h"
+#include "mhs.h"
+#include "mhs_internal.h"
+
+using namespace mhs;
+
+namespace {
+
+inline int64_t up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+inline int64_t kbytes(int64_t K) { return up(K > 0 ? K : 1, kTcK); }
+inline int64_t kwords(int64_t K) { return up(((K + 31) / 32) > 0 ? (K + 31) / 32 : 1, 4); }
+inline int64_t now_ns() {
+    return std::chrono::duration_cast<std::chrono::nanoseconds>(
+               std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
+
+struct Request {
+    uint64_t ticket = 0;
+    int32_t n = 0, m = 0;
+    int64_t k = 0;
+    std::vector<int32_t> ptr, vtx, dem;
+    int64_t footprint = 0;
+    int64_t t_submit = 0, t_admit = 0, t_done = 0;
+    bool done = false;
+    mhs_status status = MHS_OK;
+    std::vector<int32_t> vout, eout, dout;
+    int32_t rounds = 0;
+};
+
+// Device layout of one admitted instance inside its arena.
+struct Layout {
+    int64_t eptr, evtx, f, v_o2c, v_c2o, e_o2c, e_c2o, e_f, e_s, v_deg, v_maxf, v_cnt, e_del,
+        v_del, tmaps, dense, dense_bytes, bytes;
+};
+
+Layout plan_layout(int32_t n, int32_t m, int64_t nnz, bool dense) {
+    Layout L;
+    int64_t b = 0;
+    auto take = [&b](int64_t x) {
+        int64_t o = b;
+        b += up(x > 0 ? x : 1, 256);
+        return o;
+    };
+    L.eptr = take(4 * ((int64_t)m + 1));
+    L.evtx = take(4 * nnz);
+    L.f = take(4 * (int64_t)m);
+    L.v_o2c = take(4 * (int64_t)n);
+    L.v_c2o = take(4 * (int64_t)n);
+    L.e_o2c = take(4 * (int64_t)m);
+    L.e_c2o = take(4 * (int64_t)m);
+    L.e_f = take(4 * (int64_t)m);
+    L.e_s = take(4 * (int64_t)m);
+    L.v_deg = take(4 * (int64_t)n);
+    L.v_maxf = take(4 * (int64_t)n);
+    L.v_cnt = take(4 * (int64_t)n);
+    L.e_del = take(m);
+    L.v_del = take(n);
+    L.tmaps = take(dense ? 2 * (int64_t)tmap_bytes() : 0);
+    L.dense = b;
+    const int64_t arows = up(m > 0 ? m : 1, kRowAlign), atrows = up(n > 0 ? n : 1, kRowAlign);
+    if (dense) {
+        take(arows * kbytes(n));
+        take(atrows * kbytes(m));
+    } else {
+        take(arows * kwords(n) * 4);
+        take(atrows * kwords(m) * 4);
+    }
+    L.dense_bytes = b - L.dense;
+    L.bytes = b;
+    return L;
+}
+
+struct Slot {
+    bool busy = false;
+    std::shared_ptr<Request> req;
+    uint8_t *arena = nullptr;
+    int64_t bytes = 0;
+};
+
+}  // namespace
+
+struct mhs_server {
+    mhs_server_options opt{};
+    int contraction = kFp8;
+    int device = 0, sms = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaMemPool_t pool = nullptr;
+    int32_t slots_n = 0;
+    // device slot table and round bookkeeping
+    uint8_t *ctl = nullptr;  // one allocation: states, plan, offsets, counters, done list
+    InstState *dstate = nullptr;
+    Plan *dplan = nullptr;
+    BatchCounters *dctr = nullptr;
+    int32_t *dkerr = nullptr, *ddone = nullptr;
+    BatchCounters *hctr = nullptr;  // pinned
+    int32_t *hkerr = nullptr, *hdone = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    std::vector<Slot> slots;   // owned by the worker thread
+    int32_t active_count = 0;  // busy slots (guarded by mu)
+    int64_t in_use = 0, peak = 0;
+    // queues
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<std::shared_ptr<Request>> pending;
+    std::unordered_map<uint64_t, std::shared_ptr<Request>> table;
+    uint64_t next_ticket = 1;
+    bool stop = false, paused = false;
+    mhs_status fatal = MHS_OK;
+    std::thread worker;
+    // stats
+    int64_t submitted = 0, admitted = 0, completed = 0, rounds = 0;
+};
+
+namespace {
+
+// Upload and initialise one request into slot `si` (worker thread only).
+mhs_status admit(mhs_server *S, int si, std::shared_ptr<Request> req) {
+    const bool dense = S->contraction == kFp8;
+    const int64_t nnz = req->ptr.empty() ? 0 : req->ptr.back();
+    Layout L = plan_layout(req->n, req->m, nnz, dense);
+    uint8_t *a = nullptr;
+    cudaError_t e = cudaMallocFromPoolAsync(reinterpret_cast<void **>(&a), (size_t)L.bytes, S->pool,
+                                            S->stream);
+    if (e != cudaSuccess) return set_error(MHS_ENOMEM, "server: arena allocation failed");
+    InstState s;
+    std::memset(&s, 0, sizeof(s));
+    s.n0 = req->n;
+    s.m0 = req->m;
+    s.nnz0 = nnz;
+    s.k = req->k;
+    s.eptr = reinterpret_cast<int32_t *>(a + L.eptr);
+    s.evtx = reinterpret_cast<int32_t *>(a + L.evtx);
+    s.f = reinterpret_cast<int32_t *>(a + L.f);
+    s.v_o2c = reinterpret_cast<int32_t *>(a + L.v_o2c);
+    s.v_c2o = reinterpret_cast<int32_t *>(a + L.v_c2o);
+    s.e_o2c = reinterpret_cast<int32_t *>(a + L.e_o2c);
+    s.e_c2o = reinterpret_cast<int32_t *>(a + L.e_c2o);
+    s.e_f = reinterpret_cast<int32_t *>(a + L.e_f);
+    s.e_s = reinterpret_cast<int32_t *>(a + L.e_s);
+    s.v_deg = reinterpret_cast<int32_t *>(a + L.v_deg);
+    s.v_maxf = reinterpret_cast<int32_t *>(a + L.v_maxf);
+    s.v_cnt = reinterpret_cast<int32_t *>(a + L.v_cnt);
+    s.e_del = a + L.e_del;
+    s.v_del = a + L.v_del;
+    const int64_t arows = up(req->m > 0 ? req->m : 1, kRowAlign);
+    const int64_t atrows = up(req->n > 0 ? req->n : 1, kRowAlign);
+    s.A_rows = (int32_t)arows;
+    s.At_rows = (int32_t)atrows;
+    std::vector<uint8_t> maps;
+    if (dense) {
+        s.A = a + L.dense;
+        s.At = s.A + arows * kbytes(req->n);
+        s.A_pitch = kbytes(req->n);
+        s.At_pitch = kbytes(req->m);
+        s.tmap_A = a + L.tmaps;
+        s.tmap_At = a + L.tmaps + tmap_bytes();
+        maps.resize(2 * tmap_bytes());
+        if (!make_operand_tmap(maps.data(), s.A, s.A_pitch, s.A_rows) ||
+            !make_operand_tmap(maps.data() + tmap_bytes(), s.At, s.At_pitch, s.At_rows)) {
+            cudaFreeAsync(a, S->stream);
+            return set_error(MHS_ECUDA, "server: tensor map encoding failed");
+        }
+    } else {
+        s.Ab = reinterpret_cast<uint32_t *>(a + L.dense);
+        s.Atb = s.Ab + arows * kwords(req->n);
+        s.Ab_pitch = (int32_t)kwords(req->n);
+        s.Atb_pitch = (int32_t)kwords(req->m);
+    }
+    // pageable sources: each copy has staged its source when it returns
+    e = cudaMemcpyAsync(a + L.eptr, req->ptr.data(), 4 * req->ptr.size(), cudaMemcpyHostToDevice,
+                        S->stream);
+    if (e == cudaSuccess && nnz > 0)
+        e = cudaMemcpyAsync(a + L.evtx, req->vtx.data(), 4 * (size_t)nnz, cudaMemcpyHostToDevice,
+                            S->stream);
+    if (e == cudaSuccess && req->m > 0)
+        e = cudaMemcpyAsync(a + L.f, req->dem.data(), 4 * (size_t)req->m, cudaMemcpyHostToDevice,
+                            S->stream);
+    if (e == cudaSuccess && dense)
+        e = cudaMemcpyAsync(a + L.tmaps, maps.data(), maps.size(), cudaMemcpyHostToDevice,
+                            S->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(a + L.dense, 0, (size_t)L.dense_bytes, S->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(S->dstate + si, &s, sizeof(s), cudaMemcpyHostToDevice, S->stream);
+    if (e == cudaSuccess) e = launch_build(S->dstate + si, 1, 0, nnz, req->m, req->n, S->stream);
+    if (e == cudaSuccess && dense) e = cudaStreamSynchronize(S->stream);  // `maps` is local
+    if (e != cudaSuccess) {
+        cudaFreeAsync(a, S->stream);
+        return set_error(MHS_ECUDA, "server: admission failed: %s", cudaGetErrorString(e));
+    }
+    Slot &sl = S->slots[si];
+    sl.busy = true;
+    sl.req = std::move(req);
+    sl.arena = a;
+    sl.bytes = L.bytes;
+    std::lock_guard<std::mutex> lk(S->mu);
+    ++S->active_count;
+    return MHS_OK;
+}
+
+// Fail every request that has not finished (device error or shutdown).
+void fail_all_locked(mhs_server *S, mhs_status st) {
+    const int64_t t = now_ns();
+    for (auto &kv : S->table) {
+        Request &r = *kv.second;
+        if (!r.done) {
+            r.status = st;
+            r.done = true;
+            r.t_done = t;
+        }
+    }
+    S->pending.clear();
+}
+
+// Copy the result of slot si to its request and release the slot.
+mhs_status retire(mhs_server *S, int si) {
+    Slot &sl = S->slots[si];
+    InstState s;
+    cudaError_t e = cudaMemcpyAsync(&s, S->dstate + si, sizeof(s), cudaMemcpyDeviceToHost, S->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
+    Request &r = *sl.req;
+    if (e == cudaSuccess) {
+        r.vout.resize(s.n);
+        r.eout.resize(s.m);
+        std::vector<int32_t> f(s.m0 > 0 ? s.m0 : 1);
+        if (s.n > 0)
+            e = cudaMemcpyAsync(r.vout.data(), s.v_c2o, 4 * (size_t)s.n, cudaMemcpyDeviceToHost,
+                                S->stream);
+        if (e == cudaSuccess && s.m > 0)
+            e = cudaMemcpyAsync(r.eout.data(), s.e_c2o, 4 * (size_t)s.m, cudaMemcpyDeviceToHost,
+                                S->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
+        if (e == cudaSuccess) {
+            r.dout.resize(s.m);
+            for (int32_t i = 0; i < s.m; ++i) r.dout[i] = r.dem[r.eout[i]];
+            r.rounds = s.rounds;
+            r.status = s.status ? MHS_EDEVICE : MHS_OK;
+        }
+    }
+    if (e != cudaSuccess) r.status = MHS_ECUDA;
+    InstState z;
+    std::memset(&z, 0, sizeof(z));
+    cudaMemcpyAsync(S->dstate + si, &z, sizeof(z), cudaMemcpyHostToDevice, S->stream);
+    cudaFreeAsync(sl.arena, S->stream);
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->in_use -= sl.bytes;
+        r.t_done = now_ns();
+        r.done = true;
+        r.ptr.clear();
+        r.vtx.clear();
+        r.dem.clear();
+        ++S->completed;
+        --S->active_count;
+    }
+    sl = Slot();
+    S->cv_done.notify_all();
+    return e == cudaSuccess ? MHS_OK : MHS_ECUDA;
+}
+
+void worker_loop(mhs_server *S) {
+    cudaSetDevice(S->device);
+    for (;;) {
+        // ---- admission at the round boundary ----
+        std::vector<std::pair<int, std::shared_ptr<Request>>> to_admit;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            bool any_busy = false;
+            for (auto &sl : S->slots) any_busy |= sl.busy;
+            if (!any_busy)
+                S->cv_work.wait(lk, [&] { return S->stop || (!S->paused && !S->pending.empty()); });
+            if (S->stop) break;
+            if (!S->paused) {
+                int si = 0;
+                while (!S->pending.empty()) {
+                    auto &front = S->pending.front();
+                    if (S->in_use + front->footprint > S->opt.hbm_budget_bytes) break;
+                    while (si < S->slots_n && (S->slots[si].busy ||
+                                               std::any_of(to_admit.begin(), to_admit.end(),
+                                                           [si](auto &p) { return p.first == si; })))
+                        ++si;
+                    if (si >= S->slots_n) break;
+                    S->in_use += front->footprint;
+                    S->peak = std::max(S->peak, S->in_use);
+                    front->t_admit = now_ns();
+                    to_admit.emplace_back(si, front);
+                    S->pending.pop_front();
+                    ++S->admitted;
+                    ++si;
+                }
+            }
+        }
+        for (auto &p : to_admit) {
+            mhs_status st = admit(S, p.first, p.second);
+            if (st != MHS_OK) {
+                std::lock_guard<std::mutex> lk(S->mu);
+                S->in_use -= p.second->footprint;
+                p.second->status = st;
+                p.second->done = true;
+                p.second->t_done = now_ns();
+                S->cv_done.notify_all();
+            }
+        }
+        bool any_busy = false;
+        for (auto &sl : S->slots) any_busy |= sl.busy;
+        if (!any_busy) continue;
+        // ---- one round for every busy slot ----
+        cudaError_t e = cudaGraphLaunch(S->graph, S->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
+        if (e != cudaSuccess || *S->hkerr) {
+            std::lock_guard<std::mutex> lk(S->mu);
+            S->fatal = e != cudaSuccess ? MHS_ECUDA : MHS_EDEVICE;
+            fail_all_locked(S, S->fatal);
+            S->active_count = 0;
+            S->cv_done.notify_all();
+            break;
+        }
+        ++S->rounds;
+        const int nd = S->hctr->n_done;
+        for (int i = 0; i < nd && i < S->slots_n; ++i) {
+            const int si = S->hdone[i];
+            if (si >= 0 && si < S->slots_n && S->slots[si].busy) retire(S, si);
+        }
+    }
+}
+
+mhs_status capture_graph(mhs_server *S) {
+    cudaGraph_t g;
+    cudaError_t e = cudaStreamBeginCapture(S->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return set_error(MHS_ECUDA, "server capture: %s", cudaGetErrorString(e));
+    cudaError_t e1 = launch_round_phase(S->dstate, S->dplan, S->dctr, S->slots_n, 0, S->contraction,
+                                        S->sms, S->dkerr, S->stream, nullptr, nullptr, nullptr);
+    if (e1 == cudaSuccess)
+        e1 = launch_round_phase(S->dstate, S->dplan, S->dctr, S->slots_n, 1, S->contraction,
+                                S->sms, S->dkerr, S->stream, nullptr, nullptr, S->ddone);
+    if (e1 == cudaSuccess)
+        e1 = cudaMemcpyAsync(S->hctr, S->dctr, sizeof(BatchCounters), cudaMemcpyDeviceToHost,
+                             S->stream);
+    if (e1 == cudaSuccess)
+        e1 = cudaMemcpyAsync(S->hdone, S->ddone, 4 * (size_t)S->slots_n, cudaMemcpyDeviceToHost,
+                             S->stream);
+    if (e1 == cudaSuccess)
+        e1 = cudaMemcpyAsync(S->hkerr, S->dkerr, 4, cudaMemcpyDeviceToHost, S->stream);
+    cudaError_t e2 = cudaStreamEndCapture(S->stream, &g);
+    if (e1 != cudaSuccess || e2 != cudaSuccess)
+        return set_error(MHS_ECUDA, "server capture failed: %s",
+                         cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
+    e = cudaGraphInstantiate(&S->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return set_error(MHS_ECUDA, "server graph: %s", cudaGetErrorString(e));
+    return MHS_OK;
+}
+
+void destroy_server(mhs_server *S) {
+    if (!S) return;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+    }
+    S->cv_work.notify_all();
+    if (S->worker.joinable()) S->worker.join();
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        fail_all_locked(S, MHS_ECUDA);
+    }
+    S->cv_done.notify_all();
+    if (S->stream) cudaStreamSynchronize(S->stream);
+    for (auto &sl : S->slots)
+        if (sl.arena) cudaFreeAsync(sl.arena, S->stream);
+    if (S->graph) cudaGraphExecDestroy(S->graph);
+    if (S->ctl) cudaFreeAsync(S->ctl, S->stream);
+    if (S->stream) cudaStreamSynchronize(S->stream);
+    if (S->hctr) cudaFreeHost(S->hctr);
+    if (S->hkerr) cudaFreeHost(S->hkerr);
+    if (S->hdone) cudaFreeHost(S->hdone);
+    if (S->own_stream && S->stream) cudaStreamDestroy(S->stream);
+    S->cv_done.notify_all();
+    delete S;
+}
+
+}  // namespace
+
+extern "C" {
+
+mhs_status mhs_server_default_options(mhs_server_options *opt) {
+    if (!opt) return set_error(MHS_EINVAL, "opt is NULL");
+    std::memset(opt, 0, sizeof(*opt));
+    opt->hbm_budget_bytes = 0;
+    opt->max_slots = 256;
+    opt->queue_capacity = 65536;
+    opt->contraction = MHS_CONTRACT_AUTO;
+    return MHS_OK;
+}
+
+mhs_status mhs_server_create(const mhs_server_options *opt_in, void *cuda_stream,
+                             mhs_server **out) {
+    if (!out) return set_error(MHS_EINVAL, "out is NULL");
+    *out = nullptr;
+    mhs_server_options opt;
+    mhs_server_default_options(&opt);
+    if (opt_in) opt = *opt_in;
+    if (opt.max_slots < 1 || opt.max_slots > 4096)
+        return set_error(MHS_EINVAL, "max_slots must be in [1, 4096]");
+    if (opt.queue_capacity < 1) return set_error(MHS_EINVAL, "queue_capacity must be >= 1");
+    if (opt.contraction < 0 || opt.contraction > 2)
+        return set_error(MHS_EINVAL, "contraction must be 0, 1 or 2");
+    if (opt.hbm_budget_bytes < 0) return set_error(MHS_EINVAL, "hbm_budget_bytes must be >= 0");
+    for (int i = 0; i < 3; ++i)
+        if (opt.reserved[i]) return set_error(MHS_EINVAL, "reserved options must be zero");
+    auto *S = new mhs_server();
+    S->opt = opt;
+    S->contraction = opt.contraction == MHS_CONTRACT_POPCOUNT ? kPopcount : kFp8;
+    S->slots_n = opt.max_slots;
+    S->slots.resize(opt.max_slots);
+    auto bail = [&](mhs_status st) {
+        destroy_server(S);
+        return st;
+    };
+    if (cudaGetDevice(&S->device) != cudaSuccess) return bail(set_error(MHS_ECUDA, "no device"));
+    cudaDeviceGetAttribute(&S->sms, cudaDevAttrMultiProcessorCount, S->device);
+    if (S->opt.hbm_budget_bytes == 0) {
+        size_t fr = 0, tot = 0;
+        cudaMemGetInfo(&fr, &tot);
+        S->opt.hbm_budget_bytes = (int64_t)(fr / 4 * 3);
+    }
+    if (cuda_stream) {
+        S->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking) != cudaSuccess)
+            return bail(set_error(MHS_ECUDA, "stream creation failed"));
+        S->own_stream = true;
+    }
+    if (pool_for(S->device, &S->pool) != cudaSuccess)
+        return bail(set_error(MHS_ECUDA, "memory pool unavailable"));
+    if (S->contraction == kFp8 && prepare_tc_contract() != cudaSuccess)
+        return bail(set_error(MHS_ECUDA, "tcgen05 kernel setup failed"));
+    // slot table, plan, counters and done list in one allocation
+    const int64_t ns = S->slots_n;
+    const int64_t o_state = 0;
+    const int64_t o_plan = up(sizeof(InstState) * ns, 256);
+    const int64_t o_row = o_plan + up(sizeof(Plan), 256);
+    const int64_t o_tile = o_row + up(4 * (ns + 1), 256);
+    const int64_t o_ctr = o_tile + up(8 * (ns + 1), 256);
+    const int64_t o_kerr = o_ctr + up(sizeof(BatchCounters), 256);
+    const int64_t o_done = o_kerr + 256;
+    const int64_t total = o_done + up(4 * ns, 256);
+    if (cudaMallocFromPoolAsync(reinterpret_cast<void **>(&S->ctl), (size_t)total, S->pool,
+                                S->stream) != cudaSuccess)
+        return bail(set_error(MHS_ENOMEM, "server control allocation failed"));
+    S->dstate = reinterpret_cast<InstState *>(S->ctl + o_state);
+    S->dplan = reinterpret_cast<Plan *>(S->ctl + o_plan);
+    S->dctr = reinterpret_cast<BatchCounters *>(S->ctl + o_ctr);
+    S->dkerr = reinterpret_cast<int32_t *>(S->ctl + o_kerr);
+    S->ddone = reinterpret_cast<int32_t *>(S->ctl + o_done);
+    if (cudaMallocHost(&S->hctr, sizeof(BatchCounters)) != cudaSuccess ||
+        cudaMallocHost(&S->hkerr, 4) != cudaSuccess ||
+        cudaMallocHost(&S->hdone, 4 * (size_t)ns) != cudaSuccess)
+        return bail(set_error(MHS_ENOMEM, "pinned allocation failed"));
+    *S->hkerr = 0;
+    Plan p;
+    std::memset(&p, 0, sizeof(p));
+    p.count = S->slots_n;
+    p.row_off = reinterpret_cast<int32_t *>(S->ctl + o_row);
+    p.tile_off = reinterpret_cast<int64_t *>(S->ctl + o_tile);
+    cudaError_t e = cudaMemsetAsync(S->ctl, 0, (size_t)total, S->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(S->dplan, &p, sizeof(p), cudaMemcpyHostToDevice, S->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
+    if (e != cudaSuccess) return bail(set_error(MHS_ECUDA, "server setup: %s", cudaGetErrorString(e)));
+    mhs_status st = capture_graph(S);
+    if (st) return bail(st);
+    S->worker = std::thread(worker_loop, S);
+    *out = S;
+    return MHS_OK;
+}
+
+mhs_status mhs_submit(mhs_server *S, int32_t n, int32_t m, const int32_t *edge_ptr,
+                      const int32_t *edge_vtx, const int32_t *demand, int64_t k,
+                      uint64_t *ticket) {
+    if (!S || !ticket) return set_error(MHS_EINVAL, "NULL argument");
+    if (n < 0 || m < 0 || n >= (1 << 24) || m >= (1 << 24))
+        return set_error(MHS_EINVAL, "n and m must be in [0, 2^24)");
+    if (!edge_ptr || (m > 0 && !demand)) return set_error(MHS_EINVAL, "NULL input array");
+    if (edge_ptr[0] != 0) return set_error(MHS_EINVAL, "edge_ptr[0] must be 0");
+    const int32_t nnz = edge_ptr[m];
+    if (nnz > 0 && !edge_vtx) return set_error(MHS_EINVAL, "edge_vtx is NULL");
+    // structural checks on the host, before anything is queued
+    std::vector<int32_t> mark((size_t)n, -1);
+    for (int32_t e = 0; e < m; ++e) {
+        if (edge_ptr[e + 1] < edge_ptr[e])
+            return set_error(MHS_EINVAL, "edge_ptr decreases at hyperedge %d", e);
+        if (demand[e] < 1) return set_error(MHS_EINVAL, "demand of hyperedge %d is < 1", e);
+        for (int32_t p = edge_ptr[e]; p < edge_ptr[e + 1]; ++p) {
+            const int32_t v = edge_vtx[p];
+            if (v < 0 || v >= n)
+                return set_error(MHS_EINVAL, "hyperedge %d has vertex id %d outside [0,%d)", e, v, n);
+            if (mark[v] == e) return set_error(MHS_EINVAL, "hyperedge %d lists vertex %d twice", e, v);
+            mark[v] = e;
+        }
+    }
+    auto r = std::make_shared<Request>();
+    r->n = n;
+    r->m = m;
+    r->k = k;
+    r->ptr.assign(edge_ptr, edge_ptr + m + 1);
+    r->vtx.assign(edge_vtx, edge_vtx + nnz);
+    r->dem.assign(demand, demand + m);
+    r->footprint = plan_layout(n, m, nnz, S->contraction == kFp8).bytes;
+    if (r->footprint > S->opt.hbm_budget_bytes)
+        return set_error(MHS_ENOMEM, "instance needs %lld bytes, over the server budget %lld",
+                         (long long)r->footprint, (long long)S->opt.hbm_budget_bytes);
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (S->fatal) return set_error(S->fatal, "server stopped after a device error");
+        if ((int64_t)S->pending.size() >= S->opt.queue_capacity)
+            return set_error(MHS_EBUSY, "request queue full (%d)", S->opt.queue_capacity);
+        r->ticket = S->next_ticket++;
+        r->t_submit = now_ns();
+        S->pending.push_back(r);
+        S->table[r->ticket] = r;
+        ++S->submitted;
+        *ticket = r->ticket;
+    }
+    S->cv_work.notify_one();
+    return MHS_OK;
+}
+
+mhs_status mhs_poll(mhs_server *S, uint64_t ticket, int64_t timeout_us, int32_t *vtx_out,
+                    int32_t vtx_cap, int32_t *n_out, int32_t *edge_out, int32_t *demand_out,
+                    int32_t edge_cap, int32_t *m_out, int64_t *k_out, int32_t *rounds_out,
+                    int64_t *times_ns) {
+    if (!S) return set_error(MHS_EINVAL, "server is NULL");
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->table.find(ticket);
+    if (it == S->table.end()) return set_error(MHS_EINVAL, "unknown ticket %llu", (unsigned long long)ticket);
+    std::shared_ptr<Request> r = it->second;
+    if (!r->done) {
+        if (timeout_us != 0) {
+            auto pred = [&] { return r->done; };
+            if (timeout_us < 0) S->cv_done.wait(lk, pred);
+            else S->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), pred);
+        }
+        if (!r->done) return set_error(MHS_EAGAIN, "request %llu not finished", (unsigned long long)ticket);
+    }
+    if (r->status != MHS_OK) {
+        S->table.erase(it);
+        return set_error(r->status, "request %llu failed on the device", (unsigned long long)ticket);
+    }
+    const int32_t nv = (int32_t)r->vout.size(), ne = (int32_t)r->eout.size();
+    if (n_out) *n_out = nv;
+    if (m_out) *m_out = ne;
+    if (k_out) *k_out = r->k;
+    if (rounds_out) *rounds_out = r->rounds;
+    if (times_ns) {
+        times_ns[0] = r->t_admit - r->t_submit;
+        times_ns[1] = r->t_done - r->t_admit;
+        times_ns[2] = r->t_done - r->t_submit;
+    }
+    if (!vtx_out && !edge_out && !demand_out) return MHS_OK;  // counts only; kept
+    if ((vtx_out && vtx_cap < nv) || ((edge_out || demand_out) && edge_cap < ne))
+        return set_error(MHS_EINVAL, "output capacity too small (need %d vertices, %d edges)", nv, ne);
+    if (vtx_out) std::copy(r->vout.begin(), r->vout.end(), vtx_out);
+    if (edge_out) std::copy(r->eout.begin(), r->eout.end(), edge_out);
+    if (demand_out) std::copy(r->dout.begin(), r->dout.end(), demand_out);
+    S->table.erase(it);
+    return MHS_OK;
+}
+
+mhs_status mhs_server_pause(mhs_server *S, int32_t paused) {
+    if (!S) return set_error(MHS_EINVAL, "server is NULL");
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->paused = paused != 0;
+    }
+    S->cv_work.notify_all();
+    return MHS_OK;
+}
+
+mhs_status mhs_server_get_stats(mhs_server *S, mhs_server_stats *out) {
+    if (!S || !out) return set_error(MHS_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(S->mu);
+    std::memset(out, 0, sizeof(*out));
+    out->submitted = S->submitted;
+    out->admitted = S->admitted;
+    out->completed = S->completed;
+    out->rounds = S->rounds;
+    out->pending = (int32_t)S->pending.size();
+    out->active = S->active_count;
+    out->bytes_in_use = S->in_use;
+    out->peak_bytes = S->peak;
+    out->budget_bytes = S->opt.hbm_budget_bytes;
+    return MHS_OK;
+}
+
+void mhs_server_destroy(mhs_server *S) { destroy_server(S); }
+
+}  // extern "C"

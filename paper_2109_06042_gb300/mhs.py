@@ -46,6 +46,23 @@ class RoundStats(ctypes.Structure):
         return {f: int(getattr(self, f)) for f, _ in self._fields_}
 
 
+class ServerOptions(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("max_slots", ctypes.c_int32),
+                ("queue_capacity", ctypes.c_int32), ("contraction", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("admitted", ctypes.c_int64),
+                ("completed", ctypes.c_int64), ("rounds", ctypes.c_int64),
+                ("pending", ctypes.c_int32), ("active", ctypes.c_int32),
+                ("bytes_in_use", ctypes.c_int64), ("peak_bytes", ctypes.c_int64),
+                ("budget_bytes", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
+
+
 _lib = None
 
 _i32, _i64, _vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
@@ -76,6 +93,15 @@ _SIGS = {
     "mhs_last_timing": (_i32, [_vp, ctypes.POINTER(ctypes.c_float)]),
     "mhs_kernelize_noalloc": (_i32, [_i32, _i32, _vp, _vp, _vp, _i32, _vp, _vp, _P32, _vp,
                                      ctypes.c_char_p, ctypes.c_size_t]),
+    "mhs_server_default_options": (_i32, [ctypes.POINTER(ServerOptions)]),
+    "mhs_server_create": (_i32, [ctypes.POINTER(ServerOptions), _vp, ctypes.POINTER(_vp)]),
+    "mhs_submit": (_i32, [_vp, _i32, _i32, _P32, _P32, _P32, _i64,
+                          ctypes.POINTER(ctypes.c_uint64)]),
+    "mhs_poll": (_i32, [_vp, ctypes.c_uint64, _i64, _P32, _i32, _P32, _P32, _P32, _i32, _P32,
+                        _P64, _P32, _P64]),
+    "mhs_server_pause": (_i32, [_vp, _i32]),
+    "mhs_server_get_stats": (_i32, [_vp, ctypes.POINTER(ServerStats)]),
+    "mhs_server_destroy": (None, [_vp]),
     "mhs_free": (None, [_vp]),
     "mhs_last_error": (ctypes.c_char_p, []),
     "mhs_version": (ctypes.c_char_p, []),
@@ -306,6 +332,83 @@ def kernelize(inst, contraction="auto", max_rounds=0, use_graphs=True) -> dict:
     with Instance.load(inst, contraction, max_rounds, use_graphs) as h:
         h.kernelize()
         return h.result()
+
+
+class Server:
+    """Continuous-batching server (mhs_server_*): submit host instances, poll results."""
+
+    def __init__(self, hbm_budget_bytes=0, max_slots=256, queue_capacity=65536,
+                 contraction="auto", stream=None):
+        o = ServerOptions()
+        _check(lib().mhs_server_default_options(ctypes.byref(o)))
+        o.hbm_budget_bytes = int(hbm_budget_bytes)
+        o.max_slots = int(max_slots)
+        o.queue_capacity = int(queue_capacity)
+        o.contraction = CONTRACTIONS[contraction] if isinstance(contraction, str) else int(contraction)
+        h = ctypes.c_void_p()
+        _check(lib().mhs_server_create(ctypes.byref(o), _stream_ptr(stream), ctypes.byref(h)))
+        self._h = h
+
+    def submit(self, inst) -> int:
+        ptr = np.ascontiguousarray(inst.edge_ptr, dtype=np.int32)
+        vtx = np.ascontiguousarray(inst.edge_vtx, dtype=np.int32)
+        dem = np.ascontiguousarray(inst.demand, dtype=np.int32)
+        if vtx.size == 0:
+            vtx = np.zeros(1, np.int32)
+        if dem.size == 0:
+            dem = np.zeros(1, np.int32)
+        t = ctypes.c_uint64()
+        _check(lib().mhs_submit(self._h, int(inst.n), int(inst.m), _p32(ptr), _p32(vtx),
+                                _p32(dem), int(inst.k), ctypes.byref(t)))
+        return int(t.value)
+
+    def poll(self, ticket, timeout_us=-1):
+        """Result dict (with 'times_ns': queued, in service, total), or None if
+        the request is not finished within timeout_us."""
+        n = ctypes.c_int32()
+        m = ctypes.c_int32()
+        k = ctypes.c_int64()
+        r = ctypes.c_int32()
+        tm = (ctypes.c_int64 * 3)()
+        st = lib().mhs_poll(self._h, ctypes.c_uint64(ticket), int(timeout_us), None, 0,
+                            ctypes.byref(n), None, None, 0, ctypes.byref(m), ctypes.byref(k),
+                            ctypes.byref(r), tm)
+        if st == MHS_EAGAIN:
+            return None
+        _check(st)
+        vtx = np.zeros(max(n.value, 1), np.int32)
+        edg = np.zeros(max(m.value, 1), np.int32)
+        dem = np.zeros(max(m.value, 1), np.int32)
+        _check(lib().mhs_poll(self._h, ctypes.c_uint64(ticket), 0, _p32(vtx), vtx.size,
+                              ctypes.byref(n), _p32(edg), _p32(dem), edg.size, ctypes.byref(m),
+                              ctypes.byref(k), ctypes.byref(r), tm))
+        return {"vertices": vtx[:n.value], "edges": edg[:m.value], "demands": dem[:m.value],
+                "k": int(k.value), "rounds": int(r.value), "times_ns": [int(x) for x in tm]}
+
+    def pause(self, paused=True):
+        _check(lib().mhs_server_pause(self._h, int(bool(paused))))
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        _check(lib().mhs_server_get_stats(self._h, ctypes.byref(s)))
+        return s.as_dict()
+
+    def close(self):
+        if self._h:
+            lib().mhs_server_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def kernelize_noalloc(n, m, edge_ptr, edge_vtx, demand, nnz, alive_v, alive_e, stream=None):

@@ -1,0 +1,102 @@
+"""The continuous-batching server (mhs_server_*).
+
+Every served result must equal the oracle's and the result of the same
+instance reduced alone (bit-exact), whatever else is in flight; admission
+respects the HBM budget; queue limits, early polls, oversize requests and
+shutdown with work pending behave as the C ABI documents.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2109_06042_gb300 import instances as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mhs():
+    from paper_2109_06042_gb300 import build
+    build.build()
+    from paper_2109_06042_gb300 import mhs as M
+    return M
+
+
+def _mix():
+    insts = [I.config_batch_one(9000 + i) for i in range(24)]
+    insts += [I.config_uniform(s) for s in range(6)]
+    insts += [I.config_powerlaw(s, n=2500, m=5000) for s in range(2)]
+    insts += [I.from_edges(0, [], []), I.from_edges(6, [], []), I.tiny_random(3),
+              I.from_edges(5, [[0, 1], [1, 2, 3], [1, 2, 4]], [2, 2, 2], k=3)]
+    return insts
+
+
+def _same(a, b, ctx):
+    for key in ("vertices", "edges", "demands"):
+        assert a[key].tolist() == b[key].tolist(), (key, ctx)
+    assert a["k"] == b["k"] and a["rounds"] == b["rounds"], ctx
+
+
+@pytest.mark.parametrize("mode", ["fp8", "popcount"])
+def test_served_equals_alone_and_oracle(mhs, mode):
+    insts = _mix()
+    with mhs.Server(max_slots=16, contraction=mode) as srv:
+        tickets = [srv.submit(i) for i in insts]
+        results = [srv.poll(t, timeout_us=60_000_000) for t in tickets]
+        st = srv.stats()
+    assert st["completed"] == len(insts) and st["pending"] == 0 and st["active"] == 0
+    for idx, (inst, res) in enumerate(zip(insts, results)):
+        assert res is not None
+        _same(res, O.reduce(inst), f"oracle {idx}")
+        _same(res, mhs.kernelize(inst, contraction=mode), f"alone {idx}")
+
+
+def test_admission_by_footprint(mhs):
+    insts = [I.config_batch_one(9100 + i) for i in range(12)]
+    with mhs.Server(max_slots=64) as probe:
+        pass
+    # a budget that holds about two of these instances at a time
+    big = max(i.m * i.n for i in insts)
+    budget = 2 * (3 * big + 16 * (max(i.m for i in insts) + max(i.n for i in insts)) + (1 << 20))
+    with mhs.Server(hbm_budget_bytes=budget, max_slots=64) as srv:
+        tickets = [srv.submit(i) for i in insts]
+        results = [srv.poll(t, timeout_us=60_000_000) for t in tickets]
+        st = srv.stats()
+    assert st["peak_bytes"] <= budget
+    for inst, res in zip(insts, results):
+        _same(res, O.reduce(inst), inst.name)
+
+
+def test_queue_full_and_early_poll(mhs):
+    insts = [I.config_uniform(s) for s in range(4)]
+    with mhs.Server(max_slots=4, queue_capacity=3) as srv:
+        srv.pause(True)
+        tickets = [srv.submit(i) for i in insts[:3]]
+        with pytest.raises(mhs.MhsError) as ei:
+            srv.submit(insts[3])
+        assert ei.value.status == mhs.MHS_EBUSY
+        assert srv.poll(tickets[0], timeout_us=0) is None          # not started
+        assert srv.poll(tickets[0], timeout_us=20_000) is None      # paused: still waiting
+        assert srv.stats()["pending"] == 3
+        srv.pause(False)
+        for t, inst in zip(tickets, insts):
+            _same(srv.poll(t, timeout_us=60_000_000), O.reduce(inst), inst.name)
+        with pytest.raises(mhs.MhsError):
+            srv.poll(tickets[0])                                     # already consumed
+
+
+def test_oversize_request_rejected(mhs):
+    with mhs.Server(hbm_budget_bytes=1 << 20) as srv:
+        with pytest.raises(mhs.MhsError) as ei:
+            srv.submit(I.config_powerlaw(0, n=3000, m=6000))
+        assert ei.value.status == mhs.MHS_ENOMEM
+        res = srv.poll(srv.submit(I.config_uniform(0, n=40, m=60)), timeout_us=60_000_000)
+        _same(res, O.reduce(I.config_uniform(0, n=40, m=60)), "small fits")
+
+
+def test_destroy_with_pending_work(mhs):
+    srv = mhs.Server(max_slots=2)
+    srv.pause(True)
+    for s in range(5):
+        srv.submit(I.config_uniform(s))
+    srv.close()  # must not hang
