@@ -327,6 +327,16 @@ void mhs_server_destroy(mhs_server *srv);
 /* Free all device and host memory of the instance (synchronises its stream). */
 void mhs_free(mhs_instance *inst);
 
+/*
+ * Diagnostic (no counterpart in the paper): run one kernel that waits on a
+ * barrier nothing ever arrives at, with the bounded wait every tcgen05 wait
+ * uses, limited to limit_ns (<= 2 s).  *status_out receives the kernel's
+ * status (4 = the wait timed out, as it must) and *waited_ns_out how long
+ * it waited.  The context stays usable afterwards.
+ */
+mhs_status mhs_selftest_bounded_wait(int64_t limit_ns, int32_t *status_out,
+                                     int64_t *waited_ns_out);
+
 /* Thread-local message for the last failing call on this thread. */
 const char *mhs_last_error(void);
 

@@ -26,6 +26,7 @@
 
 #include <cstring>
 
+#include "bounded_wait.cuh"
 #include "kernels.h"
 #include "mhs_internal.h"
 
@@ -47,57 +48,6 @@ constexpr uint64_t kWaitNs = 4000000000ull;     // 4 s bound on any wait
 
 // ------------------------------------------------------------- PTX glue --
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ uint64_t globaltimer() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
-                 "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n"
-        " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Bounded wait; returns false (and raises *abort) once the limit passes or
-// another warp has aborted.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort) {
-    if (mbar_try(bar, parity)) return true;
-    uint64_t t0 = globaltimer();
-    for (uint32_t it = 1;; ++it) {
-        if (mbar_try(bar, parity)) return true;
-        if ((it & 255u) == 0) {
-            if (*abort) return false;
-            if (globaltimer() - t0 > kWaitNs) { *abort = 1; return false; }
-        }
-    }
-}
-// Bounded wait used only while draining after an abort.
-__device__ __forceinline__ bool mbar_wait_ns(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
-    uint64_t t0 = globaltimer();
-    for (;;) {
-        if (mbar_try(bar, parity)) return true;
-        if (globaltimer() - t0 > limit_ns) return false;
-    }
-}
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const void *tmap, int32_t x, int32_t y,
                                             uint32_t bar) {
     asm volatile(
@@ -306,7 +256,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 const int32_t yi = ti.bi * kTcM, yj = ti.bj * kTcN;
                 for (int32_t kb = 0; kb < ti.nk; ++kb) {
-                    if (!mbar_wait(smem_u32(&ctl->empty[stage]), phase_bit ^ 1, abort)) {
+                    if (!mbar_wait(smem_u32(&ctl->empty[stage]), phase_bit ^ 1, abort, kWaitNs)) {
                         aborted = true;
                         break;
                     }
@@ -339,14 +289,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                  t += gridDim.x, ++it) {
                 const int acc = it & 1;
                 const uint32_t acc_phase = (it >> 1) & 1;
-                if (!mbar_wait(smem_u32(&ctl->tmem_empty[acc]), acc_phase ^ 1, abort)) {
+                if (!mbar_wait(smem_u32(&ctl->tmem_empty[acc]), acc_phase ^ 1, abort, kWaitNs)) {
                     aborted = true;
                     break;
                 }
                 tc_fence_after();
                 const uint32_t d = tmem + acc * kAccCols;
                 for (int32_t kb = 0; kb < ti.nk; ++kb) {
-                    if (!mbar_wait(smem_u32(&ctl->full[stage]), phase_bit, abort)) {
+                    if (!mbar_wait(smem_u32(&ctl->full[stage]), phase_bit, abort, kWaitNs)) {
                         aborted = true;
                         break;
                     }
@@ -399,7 +349,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 else ri_f = (float)s.v_deg[i];
             }
             epi_bar();
-            const bool ok = epi_bar_and(mbar_wait(smem_u32(&ctl->tmem_full[acc]), acc_phase, abort));
+            const bool ok = epi_bar_and(mbar_wait(smem_u32(&ctl->tmem_full[acc]), acc_phase, abort, kWaitNs));
             if (!ok) { *abort = 1; break; }
             tc_fence_after();
             bool rowflag = false;

@@ -506,9 +506,27 @@ __global__ void k_alive_masks(const InstState *st, int count, bool batch, uint8_
     }
 }
 
+__global__ void k_loop_cond(cudaGraphConditionalHandle h, BatchCounters *ctr, int32_t *kerr,
+                            int32_t round_cap) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int32_t it = ++ctr->loop_iters;
+    bool go = ctr->active > 0 && *kerr == 0 && ctr->status_any == 0;
+    if (go && it >= round_cap) {
+        atomicOr(kerr, kErrRoundCap);
+        go = false;
+    }
+    cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
 }  // namespace
 
 // ------------------------------------------------------- host launchers --
+
+cudaError_t launch_loop_cond(cudaGraphConditionalHandle h, BatchCounters *ctr, int32_t *kerr,
+                             int32_t round_cap, cudaStream_t s) {
+    k_loop_cond<<<1, 32, 0, s>>>(h, ctr, kerr, round_cap);
+    return cudaGetLastError();
+}
 
 static int grid_for(int sms, int per_sm) { return sms * per_sm; }
 

@@ -21,7 +21,7 @@ struct BatchCounters {
     int32_t changed_any;
     int32_t status_any;
     int32_t n_done;           // instances that reached their fixpoint in the last round
-    int32_t pad_;
+    int32_t loop_iters;       // rounds run by the device-side loop in this launch
 };
 
 cudaError_t launch_validate(InstState *st, int count, cudaStream_t s);
@@ -38,6 +38,11 @@ cudaError_t launch_round_phase(InstState *st, Plan *plan, BatchCounters *ctr, in
                                int phase, int contraction, int sms, int32_t *kerr,
                                cudaStream_t s, cudaEvent_t ev_contract_begin,
                                cudaEvent_t ev_contract_end, int32_t *done_list = nullptr);
+// End of one round of the device-side fixpoint loop: keep looping while
+// some instance is active, no error was raised and fewer than round_cap
+// rounds ran (hitting the cap raises kErrRoundCap).
+cudaError_t launch_loop_cond(cudaGraphConditionalHandle h, BatchCounters *ctr, int32_t *kerr,
+                             int32_t round_cap, cudaStream_t s);
 cudaError_t launch_alive_masks(const InstState *st, uint8_t *alive_v, uint8_t *alive_e,
                                cudaStream_t s);
 cudaError_t launch_alive_masks_batch(const InstState *st, int count, uint8_t *alive_v,

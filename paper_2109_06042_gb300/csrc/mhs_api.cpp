@@ -121,6 +121,9 @@ struct mhs_instance {
     int64_t dense_off = 0, dense_bytes = 0;
     // round graphs: graph[0] plain, graph[1] with timing events
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    // the whole fixpoint: a conditional WHILE node whose body is one round
+    cudaGraphExec_t loop_graph = nullptr;
+    int32_t round_cap = 0;
     // timing
     bool timing = false;
     cudaEvent_t ev[6] = {};
@@ -135,6 +138,7 @@ void destroy(mhs_instance *h) {
     if (h->stream) cudaStreamSynchronize(h->stream);
     for (auto &g : h->graph)
         if (g) cudaGraphExecDestroy(g);
+    if (h->loop_graph) cudaGraphExecDestroy(h->loop_graph);
     for (auto &e : h->ev)
         if (e) cudaEventDestroy(e);
     if (h->arena) cudaFreeAsync(h->arena, h->stream);
@@ -239,6 +243,9 @@ mhs_status create(int32_t count, const int32_t *n, const int32_t *m, const int64
         h->max_nnz = std::max(h->max_nnz, z);
         h->max_m = std::max(h->max_m, m0);
         h->max_n = std::max(h->max_n, n0);
+        // every changing round deletes an item, so n + m + 1 rounds always suffice
+        h->round_cap = (int32_t)std::min<int64_t>(std::max<int64_t>(h->round_cap, n0 + m0 + 2),
+                                                  INT32_MAX);
         L.eptr = off_eptr + 4 * c_m1;
         L.evtx = off_evtx + 4 * c_z;
         L.f = off_f + 4 * c_m;
@@ -447,7 +454,86 @@ mhs_status capture_round(mhs_instance *h, bool with_events, cudaGraphExec_t *out
     return MHS_OK;
 }
 
+// One graph for Algorithm 3 to its fixpoint: reset the loop counter, then
+// WHILE(condition) { DP phase; MD phase; condition kernel }, then copy the
+// counters and the error word to pinned host memory.
+mhs_status build_loop_graph(mhs_instance *h) {
+    cudaGraph_t g = nullptr;
+    CUDA_TRY(cudaGraphCreate(&g, 0));
+    auto bail = [&](cudaError_t e, const char *what) {
+        cudaGraphDestroy(g);
+        return fail(MHS_ECUDA, "loop graph (%s): %s", what, cudaGetErrorString(e));
+    };
+    cudaGraphConditionalHandle cond;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) return bail(e, "handle");
+    cudaGraphNode_t reset;
+    cudaMemsetParams mp;
+    std::memset(&mp, 0, sizeof(mp));
+    mp.dst = &h->dctr->loop_iters;
+    mp.value = 0;
+    mp.elementSize = 4;
+    mp.width = 1;
+    mp.height = 1;
+    e = cudaGraphAddMemsetNode(&reset, g, nullptr, 0, &mp);
+    if (e != cudaSuccess) return bail(e, "reset");
+    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t loop;
+    e = cudaGraphAddNode(&loop, g, &reset, nullptr, 1, &cp);
+    if (e != cudaSuccess) return bail(e, "conditional node");
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(h->stream, body, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return bail(e, "capture");
+    cudaError_t e1 = launch_round_phase(h->dstate, h->dplan, h->dctr, h->count, 0, h->contraction,
+                                        h->sms, h->dkerr, h->stream, nullptr, nullptr);
+    if (e1 == cudaSuccess)
+        e1 = launch_round_phase(h->dstate, h->dplan, h->dctr, h->count, 1, h->contraction, h->sms,
+                                h->dkerr, h->stream, nullptr, nullptr);
+    if (e1 == cudaSuccess)
+        e1 = launch_loop_cond(cond, h->dctr, h->dkerr, h->round_cap, h->stream);
+    cudaGraph_t captured = nullptr;
+    e = cudaStreamEndCapture(h->stream, &captured);
+    if (e1 != cudaSuccess) return bail(e1, "round");
+    if (e != cudaSuccess) return bail(e, "end capture");
+    cudaGraphNode_t c1, c2;
+    e = cudaGraphAddMemcpyNode1D(&c1, g, &loop, 1, h->hctr, h->dctr, sizeof(BatchCounters),
+                                 cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess)
+        e = cudaGraphAddMemcpyNode1D(&c2, g, &c1, 1, h->hkerr, h->dkerr, sizeof(int32_t),
+                                     cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return bail(e, "copies");
+    e = cudaGraphInstantiate(&h->loop_graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(MHS_ECUDA, "loop graph instantiate: %s", cudaGetErrorString(e));
+    return MHS_OK;
+}
+
 mhs_status run_rounds(mhs_instance *h, int32_t limit, mhs_round_stats *stats) {
+    if (limit <= 0 && h->opt.use_graphs && !h->timing) {
+        if (!h->loop_graph) {
+            mhs_status st = build_loop_graph(h);
+            if (st) return st;
+        }
+        CUDA_TRY(cudaGraphLaunch(h->loop_graph, h->stream));
+        CUDA_TRY(cudaStreamSynchronize(h->stream));
+        if (*h->hkerr & kErrRoundCap)
+            return fail(MHS_EDEVICE, "device round loop reached its cap of %d rounds", h->round_cap);
+        mhs_status st = check_device_status(h);
+        if (st) return st;
+        if (stats) {
+            stats->n_alive = h->hctr->n_alive;
+            stats->m_alive = h->hctr->m_alive;
+            stats->rounds = h->hctr->max_rounds_seen;
+            stats->changed = h->hctr->changed_any;
+            stats->dp_deleted = h->hctr->dp_deleted;
+            stats->md_deleted = h->hctr->md_deleted;
+        }
+        return MHS_OK;
+    }
     if (h->timing) {
         for (auto &e : h->ev)
             if (!e) CUDA_TRY(cudaEventCreate(&e));

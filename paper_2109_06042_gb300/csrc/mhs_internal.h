@@ -31,6 +31,7 @@ enum : int32_t {
     kErrTimeout = 4,       // a bounded wait gave up
     kErrCapacity = 8,      // an index exceeded an allocated capacity
     kErrBadDemand = 16,    // a demand f(e) < 1 in the input
+    kErrRoundCap = 32,     // the device-side round loop hit its hard cap
 };
 
 struct InstState {

@@ -102,6 +102,7 @@ _SIGS = {
     "mhs_server_pause": (_i32, [_vp, _i32]),
     "mhs_server_get_stats": (_i32, [_vp, ctypes.POINTER(ServerStats)]),
     "mhs_server_destroy": (None, [_vp]),
+    "mhs_selftest_bounded_wait": (_i32, [_i64, _P32, _P64]),
     "mhs_free": (None, [_vp]),
     "mhs_last_error": (ctypes.c_char_p, []),
     "mhs_version": (ctypes.c_char_p, []),
@@ -426,6 +427,14 @@ def kernelize_noalloc(n, m, edge_ptr, edge_vtx, demand, nnz, alive_v, alive_e, s
     if st != MHS_OK:
         raise MhsError(st, buf.value.decode(errors="replace"))
     return int(rounds.value)
+
+
+def selftest_bounded_wait(limit_ns=20_000_000):
+    """Run the bounded-wait diagnostic; returns (status, waited_ns)."""
+    st = ctypes.c_int32()
+    w = ctypes.c_int64()
+    _check(lib().mhs_selftest_bounded_wait(int(limit_ns), ctypes.byref(st), ctypes.byref(w)))
+    return int(st.value), int(w.value)
 
 
 def version() -> str:

@@ -298,3 +298,13 @@ def test_batch_device_rejects_malformed(mhs):
     with pytest.raises(mhs.MhsError) as ei:
         mhs.Instance.load_batch_device(n, m, k, tp, tv, td)
     assert "instance 1" in str(ei.value)
+
+
+def test_bounded_wait_times_out_and_context_survives(mhs):
+    """A wait that nothing satisfies ends after its limit with the timeout
+    status; the context then still runs a full kernelization."""
+    status, waited = mhs.selftest_bounded_wait(20_000_000)
+    assert status == 4
+    assert 20_000_000 <= waited < 2_000_000_000
+    inst = I.config_uniform(11)
+    _same(mhs.kernelize(inst), O.reduce(inst), "after timeout")
