@@ -63,11 +63,21 @@ typedef enum {
     MHS_CONTRACT_POPCOUNT = 2  /* bit-packed AND + popcount on the integer units */
 } mhs_contraction;
 
+/* Order of the rows (and K columns) of the dense operands.  Results never
+ * depend on it (ties are broken by input index); performance does. */
+typedef enum {
+    MHS_LAYOUT_AUTO = 0,    /* library choice (currently MHS_LAYOUT_SORTED) */
+    MHS_LAYOUT_INPUT = 1,   /* input order */
+    MHS_LAYOUT_SORTED = 2   /* hyperedges by their smallest vertex id: interval-like
+                               (low Dilworth number) inputs become banded */
+} mhs_layout;
+
 typedef struct {
     int32_t contraction; /* mhs_contraction */
     int32_t max_rounds;  /* mhs_kernelize stops after this many rounds; 0 = fixpoint */
-    int32_t use_graphs;  /* 1: replay one captured CUDA graph per round */
-    int32_t reserved[5]; /* must be zero */
+    int32_t use_graphs;  /* 1: replay captured CUDA graphs (the whole fixpoint in one launch) */
+    int32_t layout;      /* mhs_layout */
+    int32_t reserved[4]; /* must be zero */
 } mhs_options;
 
 typedef struct {
@@ -278,7 +288,8 @@ typedef struct {
     int32_t max_slots;        /* instances in flight at most, 1..4096 (default 256) */
     int32_t queue_capacity;   /* queued requests at most; beyond it mhs_submit gives MHS_EBUSY */
     int32_t contraction;      /* mhs_contraction */
-    int32_t reserved[3];      /* must be zero */
+    int32_t layout;           /* mhs_layout */
+    int32_t reserved[2];      /* must be zero */
 } mhs_server_options;
 
 typedef struct {

@@ -195,6 +195,7 @@ struct __align__(8) SharedCtl {
     int abort;
     float colA[kTcN];  // DP: f_j        MD: d_j
     float colB[kTcN];  // DP: f_j - s_j  MD: unused
+    int32_t colO[kTcN];  // input index of column j (tie-breaks)
     int32_t ccnt[kTcN];
 };
 
@@ -336,17 +337,32 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int c = et; c < kTcN; c += kEpiThreads) {
                 const int32_t j = j0 + c;
                 float a = 0.f, bb = 0.f;
+                int32_t o = 0;
                 if (j < R) {
-                    if (phase == 0) { a = (float)s.e_f[j]; bb = (float)(s.e_f[j] - s.e_s[j]); }
-                    else a = (float)s.v_deg[j];
+                    if (phase == 0) {
+                        a = (float)s.e_f[j];
+                        bb = (float)(s.e_f[j] - s.e_s[j]);
+                        o = s.e_c2o[j];
+                    } else {
+                        a = (float)s.v_deg[j];
+                        o = s.v_c2o[j];
+                    }
                 }
                 ctl->colA[c] = a;
                 ctl->colB[c] = bb;
+                ctl->colO[c] = o;
             }
             float ri_f = 0.f, ri_a = 0.f;  // DP: f_i, f_i - s_i ; MD: d_i
+            int32_t ri_o = 0;              // input index of row i
             if (i < R) {
-                if (phase == 0) { ri_f = (float)s.e_f[i]; ri_a = (float)(s.e_f[i] - s.e_s[i]); }
-                else ri_f = (float)s.v_deg[i];
+                if (phase == 0) {
+                    ri_f = (float)s.e_f[i];
+                    ri_a = (float)(s.e_f[i] - s.e_s[i]);
+                    ri_o = s.e_c2o[i];
+                } else {
+                    ri_f = (float)s.v_deg[i];
+                    ri_o = s.v_c2o[i];
+                }
             }
             epi_bar();
             const bool ok = epi_bar_and(mbar_wait(smem_u32(&ctl->tmem_full[acc]), acc_phase, abort, kWaitNs));
@@ -367,18 +383,20 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const int32_t j = j0 + cc;
                         const bool valid = (i < j) && (j < R);
                         const float x = v[c];
+                        const bool i_first = ri_o < ctl->colO[cc];  // input-index tie-break
                         if (phase == 0) {
-                            // Algorithm 1: D_ij = [f_i - (s_i - x) >= f_j]
+                            // Algorithm 1: D_ij = [f_i - (s_i - x) >= f_j]; e_j goes iff
+                            // D_ij and (not D_ji or i before j)
                             const bool dij = x + ri_a >= ctl->colA[cc];
                             const bool dji = x + ctl->colB[cc] >= ri_f;
-                            colmask |= (uint32_t)(valid && dij) << c;
-                            rowflag |= valid && dji && !dij;
+                            colmask |= (uint32_t)(valid && dij && (!dji || i_first)) << c;
+                            rowflag |= valid && dji && (!dij || !i_first);
                         } else {
-                            // Algorithm 2: D_ij = [x = d_j] and D_ji = [x = d_i, x != d_j] for i < j
-                            const bool dij = x == ctl->colA[cc];
-                            const bool dji = (x == ri_f) && !dij;
-                            colmask |= (uint32_t)(valid && dij) << c;
-                            rowcnt += (int32_t)(valid && dji);
+                            // Algorithm 2: D_ij = [x = d_j and (x != d_i or i before j)]
+                            const bool eqj = x == ctl->colA[cc];
+                            const bool eqi = x == ri_f;
+                            colmask |= (uint32_t)(valid && eqj && (!eqi || i_first)) << c;
+                            rowcnt += (int32_t)(valid && eqi && (!eqj || !i_first));
                         }
                     }
                     const uint32_t any = __reduce_or_sync(0xffffffffu, colmask);

@@ -127,24 +127,88 @@ __global__ void k_gather_bounds(const int64_t *gptr, const int64_t *e0, int64_t 
         out[b] = gptr[e0[b]];
 }
 
-// Round state, identity id maps and the hyperedge rows of round 1 (one
-// block per instance).
+// Round state and vertex id maps (one block per instance).  In input
+// layout the hyperedge maps are the identity too; in sorted layout they are
+// filled by the k_layout_* kernels below, whose buckets (v_cnt) and cursors
+// (v_deg) are zeroed here.
 __global__ void k_init(InstState *st, int count, int32_t max_rounds) {
     const int b = blockIdx.x;
     if (b >= count) return;
     InstState &s = st[b];
     for (int32_t v = threadIdx.x; v < s.n0; v += blockDim.x) { s.v_o2c[v] = v; s.v_c2o[v] = v; }
-    for (int32_t e = threadIdx.x; e < s.m0; e += blockDim.x) {
-        s.e_o2c[e] = e;
-        s.e_c2o[e] = e;
-        s.e_f[e] = s.f[e];
-        s.e_s[e] = 0;
-        s.e_del[e] = 0;
+    if (s.layout_sorted) {
+        for (int32_t v = threadIdx.x; v <= s.n0; v += blockDim.x) { s.v_cnt[v] = 0; s.v_deg[v] = 0; }
+    } else {
+        for (int32_t e = threadIdx.x; e < s.m0; e += blockDim.x) { s.e_o2c[e] = e; s.e_c2o[e] = e; }
     }
     if (threadIdx.x == 0) {
         s.n = s.n0; s.m = s.m0; s.m_dp = s.m0; s.n_next = s.n0;
         s.rounds = 0; s.active = s.status == 0; s.max_rounds = max_rounds; s.changed = 0;
         s.dp_deleted = 0; s.md_deleted = 0;
+    }
+}
+
+// Sorted layout, step 1 (blockIdx.y = instance): key of each hyperedge =
+// its smallest vertex id (n0 if empty), kept in e_s; bucket counts in v_cnt.
+__global__ void k_layout_keys(InstState *st, int count) {
+    const int b = blockIdx.y;
+    if (b >= count) return;
+    InstState &s = st[b];
+    if (!s.layout_sorted || s.status) return;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < s.m0;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int32_t key = s.n0;
+        for (int32_t p = s.eptr[e]; p < s.eptr[e + 1]; ++p) key = min(key, s.evtx[p]);
+        s.e_s[e] = key;
+        atomicAdd(&s.v_cnt[key], 1);
+    }
+}
+
+// Sorted layout, step 2 (one block per instance): bucket starts in v_deg.
+__global__ void k_layout_scan(InstState *st, int count) {
+    __shared__ int32_t sh[33];
+    const int b = blockIdx.x;
+    if (b >= count) return;
+    InstState &s = st[b];
+    if (!s.layout_sorted || s.status) return;
+    int32_t carry = 0;
+    for (int32_t base = 0; base <= s.n0; base += blockDim.x) {
+        const int32_t i = base + threadIdx.x;
+        const int32_t x = i <= s.n0 ? s.v_cnt[i] : 0;
+        int32_t tot;
+        const int32_t ex = block_exclusive_scan<int32_t>(x, &tot, sh);
+        if (i <= s.n0) s.v_deg[i] = carry + ex;
+        carry += tot;
+    }
+}
+
+// Sorted layout, step 3: place every hyperedge at the next slot of its
+// bucket (the order inside a bucket is arbitrary; results do not depend
+// on it, since ties compare original ids).
+__global__ void k_layout_place(InstState *st, int count) {
+    const int b = blockIdx.y;
+    if (b >= count) return;
+    InstState &s = st[b];
+    if (!s.layout_sorted || s.status) return;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < s.m0;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t pos = atomicAdd(&s.v_deg[s.e_s[e]], 1);
+        s.e_c2o[pos] = (int32_t)e;
+        s.e_o2c[e] = pos;
+    }
+}
+
+// Hyperedge rows of round 1, by position.
+__global__ void k_edge_rows(InstState *st, int count) {
+    const int b = blockIdx.y;
+    if (b >= count) return;
+    InstState &s = st[b];
+    if (s.status) return;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < s.m0;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        s.e_f[r] = s.f[s.e_c2o[r]];
+        s.e_s[r] = 0;
+        s.e_del[r] = 0;
     }
 }
 
@@ -433,13 +497,12 @@ __global__ void __launch_bounds__(256) k_pop_contract(InstState *st, const Plan 
         // ---- fused epilogue: pairs i < j < R ----
         if (phase == 0) {
             // Algorithm 1: D_ij = [f_i - (s_i - x) >= f_j]; delete j iff
-            // D_ij and (not D_ji or i < j).  For i < j that is D_ij; e_i is
-            // deleted through this pair iff D_ji and not D_ij.
+            // D_ij and (not D_ji or i < j), i < j comparing input indices.
 #pragma unroll
             for (int a = 0; a < 4; ++a) {
                 const int32_t i = i0 + ty + 16 * a;
                 if (i >= R) continue;
-                const int32_t fi = s.e_f[i], si = s.e_s[i];
+                const int32_t fi = s.e_f[i], si = s.e_s[i], oi = s.e_c2o[i];
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
                     const int32_t j = j0 + tx + 16 * c;
@@ -448,28 +511,30 @@ __global__ void __launch_bounds__(256) k_pop_contract(InstState *st, const Plan 
                     const int32_t fj = s.e_f[j], sj = s.e_s[j];
                     const bool dij = fi - (si - x) >= fj;
                     const bool dji = fj - (sj - x) >= fi;
-                    if (dij) s.e_del[j] = 1;            // same-value stores
-                    else if (dji) s.e_del[i] = 1;
+                    const bool i_first = oi < s.e_c2o[j];  // tie-break by input index
+                    if (dij && (!dji || i_first)) s.e_del[j] = 1;   // same-value stores
+                    if (dji && (!dij || !i_first)) s.e_del[i] = 1;
                 }
             }
         } else {
-            // Algorithm 2: D_ij = [x = d_j and (x != d_i or i < j)].  For
-            // i < j: D_ij = [x = d_j], D_ji = [x = d_i and x != d_j].
+            // Algorithm 2: D_ij = [x = d_j and (x != d_i or i < j)], i < j
+            // comparing input indices.
             if (threadIdx.x < kPopTile) { rcnt[threadIdx.x] = 0; ccnt[threadIdx.x] = 0; }
             __syncthreads();
 #pragma unroll
             for (int a = 0; a < 4; ++a) {
                 const int32_t i = i0 + ty + 16 * a;
                 if (i >= R) continue;
-                const int32_t di = s.v_deg[i];
+                const int32_t di = s.v_deg[i], oi = s.v_c2o[i];
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
                     const int32_t j = j0 + tx + 16 * c;
                     if (j <= i || j >= R) continue;
                     const int32_t x = acc[a][c];
                     const int32_t dj = s.v_deg[j];
-                    if (x == dj) atomicAdd(&ccnt[tx + 16 * c], 1);
-                    else if (x == di) atomicAdd(&rcnt[ty + 16 * a], 1);
+                    const bool i_first = oi < s.v_c2o[j];  // tie-break by input index
+                    if (x == dj && (x != di || i_first)) atomicAdd(&ccnt[tx + 16 * c], 1);
+                    if (x == di && (x != dj || !i_first)) atomicAdd(&rcnt[ty + 16 * a], 1);
                 }
             }
             __syncthreads();
@@ -551,8 +616,14 @@ cudaError_t launch_build(InstState *st, int count, int32_t max_rounds, int64_t m
                          int64_t max_m, int64_t max_n, cudaStream_t s) {
     (void)max_nnz;
     (void)max_n;
-    (void)max_m;
+    int gx = (int)((max_m + 255) / 256);
+    if (gx > 256) gx = 256;
+    if (gx < 1) gx = 1;
     k_init<<<count, 1024, 0, s>>>(st, count, max_rounds);
+    k_layout_keys<<<dim3(gx, count), 256, 0, s>>>(st, count);
+    k_layout_scan<<<count, 1024, 0, s>>>(st, count);
+    k_layout_place<<<dim3(gx, count), 256, 0, s>>>(st, count);
+    k_edge_rows<<<dim3(gx, count), 256, 0, s>>>(st, count);
     return cudaGetLastError();
 }
 

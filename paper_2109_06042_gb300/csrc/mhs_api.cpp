@@ -156,7 +156,9 @@ mhs_status check_options(const mhs_options *opt, mhs_options *out) {
     if (out->contraction < 0 || out->contraction > 2)
         return fail(MHS_EINVAL, "options.contraction must be 0 (auto), 1 (fp8) or 2 (popcount)");
     if (out->max_rounds < 0) return fail(MHS_EINVAL, "options.max_rounds must be >= 0");
-    for (int i = 0; i < 5; ++i)
+    if (out->layout < 0 || out->layout > 2)
+        return fail(MHS_EINVAL, "options.layout must be 0 (auto), 1 (input) or 2 (sorted)");
+    for (int i = 0; i < 4; ++i)
         if (out->reserved[i] != 0) return fail(MHS_EINVAL, "options.reserved must be zero");
     return MHS_OK;
 }
@@ -258,9 +260,9 @@ mhs_status create(int32_t count, const int32_t *n, const int32_t *m, const int64
         L.e_c2o = ar.take(4 * m0);
         L.e_f = ar.take(4 * m0);
         L.e_s = ar.take(4 * m0);
-        L.v_deg = ar.take(4 * n0);
+        L.v_deg = ar.take(4 * (n0 + 1));
         L.v_maxf = ar.take(4 * n0);
-        L.v_cnt = ar.take(4 * n0);
+        L.v_cnt = ar.take(4 * (n0 + 1));
         L.e_del = ar.take(m0);
         L.v_del = ar.take(n0);
     }
@@ -329,6 +331,7 @@ mhs_status create(int32_t count, const int32_t *n, const int32_t *m, const int64
         s.m0 = m[b];
         s.nnz0 = nnz[b];
         s.k = k[b];
+        s.layout_sorted = opt.layout != MHS_LAYOUT_INPUT;
         s.eptr = reinterpret_cast<int32_t *>(base + L.eptr);
         s.evtx = reinterpret_cast<int32_t *>(base + L.evtx);
         s.f = reinterpret_cast<int32_t *>(base + L.f);
@@ -913,6 +916,9 @@ mhs_status mhs_result_at(const mhs_instance *inst, int32_t index, int32_t *vtx_o
         CUDA_TRY(cudaMemcpyAsync(f.data(), s.f, 4 * (size_t)s.m0, cudaMemcpyDeviceToHost, cs));
     }
     CUDA_TRY(cudaStreamSynchronize(cs));
+    // positions are in layout order: report input ids ascending
+    if (vtx_out) std::sort(vtx_out, vtx_out + s.n);
+    if (eo) std::sort(eo, eo + s.m);
     if (demand_out)
         for (int32_t i = 0; i < s.m; ++i) demand_out[i] = f[eo[i]];
     return MHS_OK;
@@ -979,6 +985,12 @@ mhs_status mhs_export(const mhs_instance *inst, int32_t index, int32_t *edge_ptr
     if (s.m > 0)
         CUDA_TRY(cudaMemcpyAsync(ec2o.data(), s.e_c2o, 4 * (size_t)s.m, cudaMemcpyDeviceToHost, cs));
     CUDA_TRY(cudaStreamSynchronize(cs));
+    // renumber in input order: vertex v -> number of surviving vertices before it
+    std::sort(ec2o.begin(), ec2o.begin() + s.m);
+    {
+        int32_t next = 0;
+        for (int32_t v = 0; v < s.n0; ++v) vmap[v] = vmap[v] >= 0 ? next++ : -1;
+    }
     int64_t nnz = 0;
     for (int32_t i = 0; i < s.m; ++i) {
         const int32_t e = ec2o[i];

@@ -5,9 +5,12 @@
 // launches use fixed persistent grids and a round can be captured as one
 // CUDA graph for any batch.
 //
-// Ids.  "Original" ids are the input ids.  "Current" ids number the items
-// still alive, in input order (compaction is order-preserving), so comparing
-// current ids is the lowest-index tie-break of Algorithms 1 and 2.
+// Ids.  "Original" ids are the input ids.  "Current" ids (positions) number
+// the items still alive in the layout order of the dense operands: input
+// order, or hyperedges sorted by smallest vertex id.  Compaction preserves
+// the layout order.  The lowest-index tie-breaks of Algorithms 1 and 2
+// always compare ORIGINAL ids (e_c2o / v_c2o), so results do not depend on
+// the layout.
 #pragma once
 
 #include <cstdint>
@@ -54,7 +57,7 @@ struct InstState {
     int32_t changed;       // last round deleted something
     int32_t dp_deleted, md_deleted;
     int32_t status;        // kErr* bits
-    int32_t pad_;
+    int32_t layout_sorted; // 1: hyperedge rows ordered by smallest vertex id
 
     // id maps (capacity n0 / m0)
     int32_t *v_o2c, *v_c2o;
@@ -63,9 +66,9 @@ struct InstState {
     // epilogue inputs, indexed by current id
     int32_t *e_f;          // f of current hyperedge
     int32_t *e_s;          // alive size |e| of current hyperedge (= I^E_ii)
-    int32_t *v_deg;        // degree over alive hyperedges (= I^V_jj)
+    int32_t *v_deg;        // degree over alive hyperedges (= I^V_jj)   [n0 + 1]
     int32_t *v_maxf;       // max demand over alive hyperedges (0 if none)
-    int32_t *v_cnt;        // C_j of Algorithm 2
+    int32_t *v_cnt;        // C_j of Algorithm 2                         [n0 + 1]
     uint8_t *e_del;        // DP deletion flags
     uint8_t *v_del;        // MD deletion flags
 

@@ -115,8 +115,8 @@ extern "C" mhs_status mhs_kernelize_noalloc(int32_t n, int32_t m, const int32_t 
     const int64_t o_vo2c = take(4 * (int64_t)n), o_vc2o = take(4 * (int64_t)n);
     const int64_t o_eo2c = take(4 * (int64_t)m), o_ec2o = take(4 * (int64_t)m);
     const int64_t o_ef = take(4 * (int64_t)m), o_es = take(4 * (int64_t)m);
-    const int64_t o_vdeg = take(4 * (int64_t)n), o_vmaxf = take(4 * (int64_t)n);
-    const int64_t o_vcnt = take(4 * (int64_t)n);
+    const int64_t o_vdeg = take(4 * ((int64_t)n + 1)), o_vmaxf = take(4 * (int64_t)n);
+    const int64_t o_vcnt = take(4 * ((int64_t)n + 1));
     const int64_t o_edel = take(m), o_vdel = take(n);
     const int64_t arows = up(m > 0 ? m : 1, kRowAlign), atrows = up(n > 0 ? n : 1, kRowAlign);
     const int64_t o_ab = take(arows * words(n) * 4);

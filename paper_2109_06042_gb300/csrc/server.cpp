@@ -84,9 +84,9 @@ Layout plan_layout(int32_t n, int32_t m, int64_t nnz, bool dense) {
     L.e_c2o = take(4 * (int64_t)m);
     L.e_f = take(4 * (int64_t)m);
     L.e_s = take(4 * (int64_t)m);
-    L.v_deg = take(4 * (int64_t)n);
+    L.v_deg = take(4 * ((int64_t)n + 1));
     L.v_maxf = take(4 * (int64_t)n);
-    L.v_cnt = take(4 * (int64_t)n);
+    L.v_cnt = take(4 * ((int64_t)n + 1));
     L.e_del = take(m);
     L.v_del = take(n);
     L.tmaps = take(dense ? 2 * (int64_t)tmap_bytes() : 0);
@@ -166,6 +166,7 @@ mhs_status admit(mhs_server *S, int si, std::shared_ptr<Request> req) {
     s.m0 = req->m;
     s.nnz0 = nnz;
     s.k = req->k;
+    s.layout_sorted = S->opt.layout != MHS_LAYOUT_INPUT;
     s.eptr = reinterpret_cast<int32_t *>(a + L.eptr);
     s.evtx = reinterpret_cast<int32_t *>(a + L.evtx);
     s.f = reinterpret_cast<int32_t *>(a + L.f);
@@ -278,6 +279,8 @@ void retire(mhs_server *S, const std::vector<int> &fin) {
         Request &r = *sl.req;
         if (e == cudaSuccess) {
             const InstState &s = S->hstates[i];
+            std::sort(r.vout.begin(), r.vout.end());  // layout order -> input ids ascending
+            std::sort(r.eout.begin(), r.eout.end());
             r.dout.resize(s.m);
             for (int32_t q = 0; q < s.m; ++q) r.dout[q] = r.dem[r.eout[q]];
             r.rounds = s.rounds;
@@ -459,7 +462,8 @@ mhs_status mhs_server_create(const mhs_server_options *opt_in, void *cuda_stream
     if (opt.contraction < 0 || opt.contraction > 2)
         return set_error(MHS_EINVAL, "contraction must be 0, 1 or 2");
     if (opt.hbm_budget_bytes < 0) return set_error(MHS_EINVAL, "hbm_budget_bytes must be >= 0");
-    for (int i = 0; i < 3; ++i)
+    if (opt.layout < 0 || opt.layout > 2) return set_error(MHS_EINVAL, "layout must be 0, 1 or 2");
+    for (int i = 0; i < 2; ++i)
         if (opt.reserved[i]) return set_error(MHS_EINVAL, "reserved options must be zero");
     auto *S = new mhs_server();
     S->opt = opt;

@@ -32,9 +32,13 @@ class MhsError(RuntimeError):
         self.status = status
 
 
+LAYOUTS = {"auto": 0, "input": 1, "sorted": 2}
+
+
 class Options(ctypes.Structure):
     _fields_ = [("contraction", ctypes.c_int32), ("max_rounds", ctypes.c_int32),
-                ("use_graphs", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("use_graphs", ctypes.c_int32), ("layout", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 class RoundStats(ctypes.Structure):
@@ -49,7 +53,7 @@ class RoundStats(ctypes.Structure):
 class ServerOptions(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("max_slots", ctypes.c_int32),
                 ("queue_capacity", ctypes.c_int32), ("contraction", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 3)]
+                ("layout", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class ServerStats(ctypes.Structure):
@@ -138,12 +142,22 @@ def _p32(a):
     return a.ctypes.data_as(_P32)
 
 
-def make_options(contraction="auto", max_rounds=0, use_graphs=True) -> Options:
+_DEFAULT_LAYOUT = ["auto"]
+
+
+def set_default_layout(layout: str):
+    """Layout used by the helpers below when none is given ('auto', 'input', 'sorted')."""
+    _DEFAULT_LAYOUT[0] = layout
+
+
+def make_options(contraction="auto", max_rounds=0, use_graphs=True, layout=None) -> Options:
     o = Options()
     _check(lib().mhs_default_options(ctypes.byref(o)))
     o.contraction = CONTRACTIONS[contraction] if isinstance(contraction, str) else int(contraction)
     o.max_rounds = int(max_rounds)
     o.use_graphs = int(bool(use_graphs))
+    lay = _DEFAULT_LAYOUT[0] if layout is None else layout
+    o.layout = LAYOUTS[lay] if isinstance(lay, str) else int(lay)
     return o
 
 
@@ -164,7 +178,8 @@ class Instance:
 
     # ---- loading ----
     @classmethod
-    def load(cls, inst, contraction="auto", max_rounds=0, use_graphs=True, stream=None):
+    def load(cls, inst, contraction="auto", max_rounds=0, use_graphs=True, stream=None,
+             layout=None):
         """mhs_load from host arrays of an ``instances.Instance``-like object."""
         ptr = np.ascontiguousarray(inst.edge_ptr, dtype=np.int32)
         vtx = np.ascontiguousarray(inst.edge_vtx, dtype=np.int32)
@@ -173,7 +188,7 @@ class Instance:
             vtx = np.zeros(1, np.int32)
         if dem.size == 0:
             dem = np.zeros(1, np.int32)
-        opt = make_options(contraction, max_rounds, use_graphs)
+        opt = make_options(contraction, max_rounds, use_graphs, layout)
         h = ctypes.c_void_p()
         _check(lib().mhs_load(int(inst.n), int(inst.m), _p32(ptr), _p32(vtx), _p32(dem),
                               int(inst.k), ctypes.byref(opt), _stream_ptr(stream),
@@ -328,9 +343,9 @@ class Instance:
             pass
 
 
-def kernelize(inst, contraction="auto", max_rounds=0, use_graphs=True) -> dict:
+def kernelize(inst, contraction="auto", max_rounds=0, use_graphs=True, layout=None) -> dict:
     """Load, reduce to the fixpoint and return the result of one host instance."""
-    with Instance.load(inst, contraction, max_rounds, use_graphs) as h:
+    with Instance.load(inst, contraction, max_rounds, use_graphs, layout=layout) as h:
         h.kernelize()
         return h.result()
 
@@ -339,13 +354,15 @@ class Server:
     """Continuous-batching server (mhs_server_*): submit host instances, poll results."""
 
     def __init__(self, hbm_budget_bytes=0, max_slots=256, queue_capacity=65536,
-                 contraction="auto", stream=None):
+                 contraction="auto", stream=None, layout=None):
         o = ServerOptions()
         _check(lib().mhs_server_default_options(ctypes.byref(o)))
         o.hbm_budget_bytes = int(hbm_budget_bytes)
         o.max_slots = int(max_slots)
         o.queue_capacity = int(queue_capacity)
         o.contraction = CONTRACTIONS[contraction] if isinstance(contraction, str) else int(contraction)
+        lay = _DEFAULT_LAYOUT[0] if layout is None else layout
+        o.layout = LAYOUTS[lay] if isinstance(lay, str) else int(lay)
         h = ctypes.c_void_p()
         _check(lib().mhs_server_create(ctypes.byref(o), _stream_ptr(stream), ctypes.byref(h)))
         self._h = h

@@ -308,3 +308,19 @@ def test_bounded_wait_times_out_and_context_survives(mhs):
     assert 20_000_000 <= waited < 2_000_000_000
     inst = I.config_uniform(11)
     _same(mhs.kernelize(inst), O.reduce(inst), "after timeout")
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("layout", ["input", "sorted"])
+def test_layouts_and_tie_breaks(mhs, mode, layout):
+    """Rows in input order or sorted by smallest vertex: the lowest-index
+    tie-breaks compare input ids, so the result is the same either way.
+    Tiny instances carry duplicate hyperedges and twin vertices."""
+    for seed in range(300):
+        inst = I.tiny_random(seed, nmax=24, mmax=30)
+        _same(mhs.kernelize(inst, contraction=mode, layout=layout), O.reduce(inst),
+              f"{layout} seed {seed}")
+    for seed in range(3):
+        inst = I.config_interval(seed, n=3000, m=6000)
+        _same(mhs.kernelize(inst, contraction=mode, layout=layout), O.reduce(inst),
+              f"{layout} interval {seed}")
