@@ -72,12 +72,22 @@ typedef enum {
                                (low Dilworth number) inputs become banded */
 } mhs_layout;
 
+/* Block-sparse skipping in the tcgen05 contraction.  Exact either way: a
+ * skipped K block or tile contributes only zero products. */
+typedef enum {
+    MHS_SPARSITY_AUTO = 0,  /* skip (currently the same as MHS_SPARSITY_SKIP) */
+    MHS_SPARSITY_SKIP = 1,  /* contract only K blocks where both operands hold a nonzero,
+                               and only tiles that can change a flag or a count */
+    MHS_SPARSITY_DENSE = 2  /* every tile of the upper triangle, every K block */
+} mhs_sparsity;
+
 typedef struct {
     int32_t contraction; /* mhs_contraction */
     int32_t max_rounds;  /* mhs_kernelize stops after this many rounds; 0 = fixpoint */
     int32_t use_graphs;  /* 1: replay captured CUDA graphs (the whole fixpoint in one launch) */
     int32_t layout;      /* mhs_layout */
-    int32_t reserved[4]; /* must be zero */
+    int32_t sparsity;    /* mhs_sparsity */
+    int32_t reserved[3]; /* must be zero */
 } mhs_options;
 
 typedef struct {
@@ -235,6 +245,12 @@ mhs_status mhs_export(const mhs_instance *inst, int32_t index, int32_t *edge_ptr
  * ms[3] total.  Timing is recorded only if enabled with mhs_set_timing.
  */
 mhs_status mhs_set_timing(mhs_instance *inst, int32_t enable);
+/*
+ * Tensor-core work done since load (tcgen05 contraction): K blocks of
+ * 128 x 256 x 128 MACs issued and tiles contracted.  With block-sparse
+ * skipping this is below the dense formulation's count.
+ */
+mhs_status mhs_work_stats(const mhs_instance *inst, int64_t *mma_kblocks, int64_t *mma_tiles);
 mhs_status mhs_last_timing(const mhs_instance *inst, float *ms4);
 
 /*
@@ -289,7 +305,8 @@ typedef struct {
     int32_t queue_capacity;   /* queued requests at most; beyond it mhs_submit gives MHS_EBUSY */
     int32_t contraction;      /* mhs_contraction */
     int32_t layout;           /* mhs_layout */
-    int32_t reserved[2];      /* must be zero */
+    int32_t sparsity;         /* mhs_sparsity */
+    int32_t reserved[1];      /* must be zero */
 } mhs_server_options;
 
 typedef struct {

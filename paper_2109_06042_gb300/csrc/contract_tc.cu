@@ -168,21 +168,100 @@ struct TileInfo {
     int32_t bi, bj, R, nk;
 };
 
+// The t-th entry of this phase's tile list.
 __device__ __forceinline__ bool next_tile(const InstState *st, const Plan *plan, int phase,
                                           int64_t t, TileInfo *ti) {
-    if (t >= plan->total_tiles) return false;
-    int lo = 0, hi = plan->count;
-    while (hi - lo > 1) {
-        int mid = (lo + hi) >> 1;
-        if (plan->tile_off[mid] <= t) lo = mid; else hi = mid;
-    }
-    const InstState &s = st[lo];
-    ti->b = lo;
+    if (t >= plan->list_count) return false;
+    unpack_tile(plan->tile_list[t], &ti->b, &ti->bi, &ti->bj);
+    const InstState &s = st[ti->b];
     ti->R = phase == 0 ? s.m : s.n;
     const int32_t K = phase == 0 ? s.n : s.m_dp;
     ti->nk = ((K > 0 ? K : 1) + kTcK - 1) / kTcK;
-    tc_tile_coords(t - plan->tile_off[lo], ti->R, &ti->bi, &ti->bj);
     return true;
+}
+
+// K blocks of a tile where both operands hold a nonzero: the occupancy
+// bits of row block bi AND those of the two row blocks of column block bj.
+// Every role walks the same sequence.
+struct KIter {
+    const uint32_t *a, *b0, *b1;
+    int32_t nkw, w, nk;
+    uint32_t mask;
+    bool all;
+};
+__device__ __forceinline__ void kit_init(KIter &k, const InstState &s, int phase,
+                                         const TileInfo &ti) {
+    const uint32_t *base = s.occ[phase];
+    const int64_t W = s.occ_words[phase];
+    k.a = base + (int64_t)ti.bi * W;
+    k.b0 = base + (int64_t)(2 * ti.bj) * W;
+    k.b1 = k.b0 + W;
+    k.nk = ti.nk;
+    k.nkw = (ti.nk + 31) / 32;
+    k.w = -1;
+    k.mask = 0;
+    k.all = s.no_skip != 0;
+}
+__device__ __forceinline__ int32_t kit_next(KIter &k) {
+    while (k.mask == 0) {
+        if (++k.w >= k.nkw) return -1;
+        if (k.all) {
+            const int32_t left = k.nk - 32 * k.w;
+            k.mask = left >= 32 ? 0xffffffffu : ((1u << left) - 1u);
+        } else {
+            k.mask = __ldg(k.a + k.w) & (__ldg(k.b0 + k.w) | __ldg(k.b1 + k.w));
+        }
+    }
+    const int32_t bit = __ffs(k.mask) - 1;
+    k.mask &= k.mask - 1;
+    return k.w * 32 + bit;
+}
+
+// Build this phase's tile list: every tile of the upper triangle (in the
+// grouped order of tc_tile_coords) that shares a nonzero K block -- and, in
+// a DP pass of an instance with a hyperedge f > |e|, every tile, since zero
+// counts can then supersede.  Zero tiles otherwise change nothing: in DP a
+// zero count supersedes only from a hyperedge with f > |e|, and in MD a
+// zero count only adds dominators of a vertex in no hyperedge, which is
+// deleted anyway (its maximum demand is 0).  Warp-aggregated appends keep
+// runs of 32 consecutive tiles together.
+__global__ void k_tile_list(InstState *st, Plan *plan, int phase) {
+    const int lane = threadIdx.x & 31;
+    const int64_t total = plan->total_tiles;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane); base < total;
+         base += nw * 32) {
+        const int64_t t = base + lane;
+        bool keep = false;
+        int64_t packed = 0;
+        if (t < total) {
+            int lo = 0, hi = plan->count;
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (plan->tile_off[mid] <= t) lo = mid; else hi = mid;
+            }
+            const InstState &s = st[lo];
+            TileInfo ti;
+            ti.b = lo;
+            ti.R = phase == 0 ? s.m : s.n;
+            const int32_t K = phase == 0 ? s.n : s.m_dp;
+            ti.nk = ((K > 0 ? K : 1) + kTcK - 1) / kTcK;
+            tc_tile_coords(t - plan->tile_off[lo], ti.R, &ti.bi, &ti.bj);
+            if ((phase == 0 && s.has_loose) || s.no_skip) {
+                keep = true;
+            } else {
+                KIter k;
+                kit_init(k, s, phase, ti);
+                keep = kit_next(k) >= 0;
+            }
+            packed = pack_tile(lo, ti.bi, ti.bj);
+        }
+        const uint32_t ballot = __ballot_sync(0xffffffffu, keep);
+        int32_t start = 0;
+        if (lane == 0 && ballot) start = atomicAdd(&plan->list_count, __popc(ballot));
+        start = __shfl_sync(0xffffffffu, start, 0);
+        if (keep) plan->tile_list[start + __popc(ballot & ((1u << lane) - 1))] = packed;
+    }
 }
 
 struct __align__(8) SharedCtl {
@@ -193,14 +272,13 @@ struct __align__(8) SharedCtl {
     uint64_t drain;
     uint32_t tmem_base;
     int abort;
-    float colA[kTcN];  // DP: f_j        MD: d_j
-    float colB[kTcN];  // DP: f_j - s_j  MD: unused
+    float2 colAB[kTcN];  // DP: (f_j, f_j - s_j)   MD: (d_j, 0)
     int32_t colO[kTcN];  // input index of column j (tie-breaks)
     int32_t ccnt[kTcN];
 };
 
 __global__ void __launch_bounds__(kThreads, 1)
-    k_tc_contract(InstState *st, const Plan *plan, int phase, int32_t *kerr) {
+    k_tc_contract(InstState *st, const Plan *plan, BatchCounters *ctr, int phase, int32_t *kerr) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     // 1024-byte alignment for the swizzle atoms
     uint8_t *smem = reinterpret_cast<uint8_t *>(
@@ -245,9 +323,24 @@ __global__ void __launch_bounds__(kThreads, 1)
             int64_t issued = 0;
             bool aborted = false;
             const void *fenced = nullptr;
-            TileInfo ti;
-            for (int64_t t = blockIdx.x; !aborted && next_tile(st, plan, phase, t, &ti);
-                 t += gridDim.x) {
+            // The next tile (list entry and first shared K block) is fetched
+            // while the current one is issued, so a tile start does not wait
+            // on global-memory latency.
+            TileInfo ti, nx;
+            KIter kit, nkit;
+            int32_t kb = -1, nkb = -1;
+            int64_t t = blockIdx.x;
+            bool have = next_tile(st, plan, phase, t, &ti);
+            if (have) {
+                kit_init(kit, st[ti.b], phase, ti);
+                kb = kit_next(kit);
+            }
+            while (have && !aborted) {
+                const bool have_nx = next_tile(st, plan, phase, t + gridDim.x, &nx);
+                if (have_nx) {
+                    kit_init(nkit, st[nx.b], phase, nx);
+                    nkb = kit_next(nkit);
+                }
                 const InstState &s = st[ti.b];
                 const void *tmap = phase == 0 ? s.tmap_A : s.tmap_At;
                 if (tmap != fenced) {  // the maps were written to global memory by a copy
@@ -256,7 +349,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     fenced = tmap;
                 }
                 const int32_t yi = ti.bi * kTcM, yj = ti.bj * kTcN;
-                for (int32_t kb = 0; kb < ti.nk; ++kb) {
+                for (; kb >= 0; kb = kit_next(kit)) {
                     if (!mbar_wait(smem_u32(&ctl->empty[stage]), phase_bit ^ 1, abort, kWaitNs)) {
                         aborted = true;
                         break;
@@ -271,6 +364,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                     ++issued;
                     if (++stage == kStages) { stage = 0; phase_bit ^= 1; }
                 }
+                have = have_nx;
+                ti = nx;
+                kit = nkit;
+                kb = nkb;
+                t += gridDim.x;
             }
             if (aborted) {  // let the loads still in flight land before exiting
                 for (int64_t k = issued > kStages ? issued - kStages : 0; k < issued; ++k)
@@ -285,9 +383,22 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t phase_bit = 0;
             int it = 0;
             bool aborted = false;
-            TileInfo ti;
-            for (int64_t t = blockIdx.x; !aborted && next_tile(st, plan, phase, t, &ti);
-                 t += gridDim.x, ++it) {
+            unsigned long long n_kblocks = 0, n_tiles = 0;
+            TileInfo ti, nx;
+            KIter kit, nkit;
+            int32_t kb = -1, nkb = -1;
+            int64_t t = blockIdx.x;
+            bool have = next_tile(st, plan, phase, t, &ti);
+            if (have) {
+                kit_init(kit, st[ti.b], phase, ti);
+                kb = kit_next(kit);
+            }
+            while (have && !aborted) {
+                const bool have_nx = next_tile(st, plan, phase, t + gridDim.x, &nx);
+                if (have_nx) {  // prefetch the next tile's first K block
+                    kit_init(nkit, st[nx.b], phase, nx);
+                    nkb = kit_next(nkit);
+                }
                 const int acc = it & 1;
                 const uint32_t acc_phase = (it >> 1) & 1;
                 if (!mbar_wait(smem_u32(&ctl->tmem_empty[acc]), acc_phase ^ 1, abort, kWaitNs)) {
@@ -296,7 +407,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 tc_fence_after();
                 const uint32_t d = tmem + acc * kAccCols;
-                for (int32_t kb = 0; kb < ti.nk; ++kb) {
+                bool first = true;
+                ++n_tiles;
+                for (; kb >= 0; kb = kit_next(kit)) {
                     if (!mbar_wait(smem_u32(&ctl->full[stage]), phase_bit, abort, kWaitNs)) {
                         aborted = true;
                         break;
@@ -307,15 +420,27 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                     for (int k = 0; k < kTcK / 32; ++k)
                         mma_f8(d, smem_desc(sa + 32 * k), smem_desc(sb + 32 * k),
-                               (kb > 0 || k > 0) ? 1u : 0u);
+                               (!first || k > 0) ? 1u : 0u);
+                    first = false;
+                    ++n_kblocks;
                     mma_commit(smem_u32(&ctl->empty[stage]));
                     if (++stage == kStages) { stage = 0; phase_bit ^= 1; }
                 }
                 if (!aborted) mma_commit(smem_u32(&ctl->tmem_full[acc]));
+                have = have_nx;
+                ti = nx;
+                kit = nkit;
+                kb = nkb;
+                t += gridDim.x;
+                ++it;
             }
             if (aborted) {  // wait for the MMAs already issued before freeing TMEM
                 mma_commit(smem_u32(&ctl->drain));
                 mbar_wait_ns(smem_u32(&ctl->drain), 0, 100000000ull);
+            }
+            if (ctr && n_tiles) {
+                atomicAdd(&ctr->mma_kblocks, n_kblocks);
+                atomicAdd(&ctr->mma_tiles, n_tiles);
             }
         }
     } else {
@@ -348,8 +473,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         o = s.v_c2o[j];
                     }
                 }
-                ctl->colA[c] = a;
-                ctl->colB[c] = bb;
+                ctl->colAB[c] = make_float2(a, bb);
                 ctl->colO[c] = o;
             }
             float ri_f = 0.f, ri_a = 0.f;  // DP: f_i, f_i - s_i ; MD: d_i
@@ -370,33 +494,95 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc_fence_after();
             bool rowflag = false;
             int32_t rowcnt = 0;
+            // a tile with no shared K block has all counts 0 and no accumulator
+            bool nonzero;
+            {
+                KIter kit;
+                kit_init(kit, s, phase, ti);
+                nonzero = kit_next(kit) >= 0;
+            }
+            // A count of 0 changes nothing unless some hyperedge has f > |e| (DP):
+            // in DP, x = 0 supersedes only from such a hyperedge; in MD it only
+            // adds dominators of a vertex in no hyperedge, deleted anyway.
+            const bool zero_matters = phase == 0 && s.has_loose;
             {
                 const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + acc * kAccCols;
 #pragma unroll 1
                 for (int ch = half * (kTcN / 64); ch < (half + 1) * (kTcN / 64); ++ch) {
                     float v[32];
-                    tmem_ld32(taddr + ch * 32, v);
-                    uint32_t colmask = 0;
+                    if (nonzero) {
+                        tmem_ld32(taddr + ch * 32, v);
+                    } else {
 #pragma unroll
-                    for (int c = 0; c < 32; ++c) {
-                        const int cc = ch * 32 + c;
-                        const int32_t j = j0 + cc;
-                        const bool valid = (i < j) && (j < R);
-                        const float x = v[c];
-                        const bool i_first = ri_o < ctl->colO[cc];  // input-index tie-break
-                        if (phase == 0) {
-                            // Algorithm 1: D_ij = [f_i - (s_i - x) >= f_j]; e_j goes iff
-                            // D_ij and (not D_ji or i before j)
-                            const bool dij = x + ri_a >= ctl->colA[cc];
-                            const bool dji = x + ctl->colB[cc] >= ri_f;
-                            colmask |= (uint32_t)(valid && dij && (!dji || i_first)) << c;
-                            rowflag |= valid && dji && (!dij || !i_first);
-                        } else {
-                            // Algorithm 2: D_ij = [x = d_j and (x != d_i or i before j)]
-                            const bool eqj = x == ctl->colA[cc];
-                            const bool eqi = x == ri_f;
-                            colmask |= (uint32_t)(valid && eqj && (!eqi || i_first)) << c;
-                            rowcnt += (int32_t)(valid && eqi && (!eqj || !i_first));
+                        for (int c = 0; c < 32; ++c) v[c] = 0.f;
+                    }
+                    if (!zero_matters) {  // skip 32 x 32 blocks of zero counts
+                        uint32_t orv = 0;
+#pragma unroll
+                        for (int c = 0; c < 32; ++c) orv |= __float_as_uint(v[c]);
+                        if (!__any_sync(0xffffffffu, orv != 0)) continue;
+                    }
+                    uint32_t colmask = 0;
+                    const float2 *cab = ctl->colAB + ch * 32;
+                    // Fast path for a chunk whose pairs are all valid (i < j < R for
+                    // every row of the warp and every column): without a mutual
+                    // pair (both D_ij and D_ji) the tie-breaks reduce to D_ij for
+                    // column j and D_ji for row i.
+                    const int32_t jc0 = j0 + ch * 32;
+                    const int32_t wi0 = ti.bi * kTcM + 32 * q;  // first row of this warp
+                    bool slow = !(wi0 + 31 < R && jc0 + 31 < R && jc0 > wi0 + 31);
+                    if (!slow) {
+                        uint32_t cm = 0;
+                        bool rf = false, mut = false;
+                        int32_t rc = 0;
+#pragma unroll
+                        for (int c = 0; c < 32; ++c) {
+                            const float x = v[c];
+                            const float2 ab = cab[c];
+                            if (phase == 0) {
+                                const bool dij = x + ri_a >= ab.x;  // f_i - (s_i - x) >= f_j
+                                const bool dji = x + ab.y >= ri_f;  // f_j - (s_j - x) >= f_i
+                                cm |= (uint32_t)dij << c;
+                                rf |= dji;
+                                mut |= dij && dji;
+                            } else {
+                                const bool eqj = x == ab.x;  // x = d_j
+                                const bool eqi = x == ri_f;  // x = d_i
+                                cm |= (uint32_t)eqj << c;
+                                rc += (int32_t)eqi;
+                                mut |= eqj && eqi;
+                            }
+                        }
+                        slow = __any_sync(0xffffffffu, mut);
+                        if (!slow) {
+                            colmask = cm;
+                            rowflag |= rf;
+                            rowcnt += rc;
+                        }
+                    }
+                    if (slow) {  // diagonal / ragged chunks, or a mutual pair present
+#pragma unroll
+                        for (int c = 0; c < 32; ++c) {
+                            const int cc = ch * 32 + c;
+                            const int32_t j = j0 + cc;
+                            const bool valid = (i < j) && (j < R);
+                            const float x = v[c];
+                            const float2 ab = cab[c];
+                            const bool i_first = ri_o < ctl->colO[cc];  // input-index tie-break
+                            if (phase == 0) {
+                                // Algorithm 1: D_ij = [f_i - (s_i - x) >= f_j]; e_j goes iff
+                                // D_ij and (not D_ji or i before j)
+                                const bool dij = x + ri_a >= ab.x;
+                                const bool dji = x + ab.y >= ri_f;
+                                colmask |= (uint32_t)(valid && dij && (!dji || i_first)) << c;
+                                rowflag |= valid && dji && (!dij || !i_first);
+                            } else {
+                                // Algorithm 2: D_ij = [x = d_j and (x != d_i or i before j)]
+                                const bool eqj = x == ab.x;
+                                const bool eqi = x == ri_f;
+                                colmask |= (uint32_t)(valid && eqj && (!eqi || i_first)) << c;
+                                rowcnt += (int32_t)(valid && eqi && (!eqj || !i_first));
+                            }
                         }
                     }
                     const uint32_t any = __reduce_or_sync(0xffffffffu, colmask);
@@ -486,9 +672,14 @@ cudaError_t prepare_tc_contract() {
                                 (int)kSmemBytes);
 }
 
-cudaError_t launch_tc_contract(InstState *st, Plan *plan, int phase, int sms, int32_t *kerr,
-                               cudaStream_t s) {
-    k_tc_contract<<<sms, kThreads, kSmemBytes, s>>>(st, plan, phase, kerr);
+cudaError_t launch_tc_contract(InstState *st, Plan *plan, BatchCounters *ctr, int phase, int sms,
+                               int32_t *kerr, cudaStream_t s) {
+    k_tc_contract<<<sms, kThreads, kSmemBytes, s>>>(st, plan, ctr, phase, kerr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc_tile_list(InstState *st, Plan *plan, int phase, int sms, cudaStream_t s) {
+    k_tile_list<<<sms * 4, 256, 0, s>>>(st, plan, phase);
     return cudaGetLastError();
 }
 

@@ -127,6 +127,14 @@ __global__ void k_gather_bounds(const int64_t *gptr, const int64_t *e0, int64_t 
         out[b] = gptr[e0[b]];
 }
 
+// Zero the occupancy bits of phase p's operand for its first R rows (all
+// row blocks a tile over R rows can touch).  Block-cooperative.
+__device__ __forceinline__ void zero_occupancy(InstState &s, int p, int32_t R) {
+    if (!s.occ[p]) return;
+    const int64_t words = (int64_t)((R + 255) / 256) * 2 * s.occ_words[p];
+    for (int64_t w = threadIdx.x; w < words; w += blockDim.x) s.occ[p][w] = 0;
+}
+
 // Round state and vertex id maps (one block per instance).  In input
 // layout the hyperedge maps are the identity too; in sorted layout they are
 // filled by the k_layout_* kernels below, whose buckets (v_cnt) and cursors
@@ -141,10 +149,11 @@ __global__ void k_init(InstState *st, int count, int32_t max_rounds) {
     } else {
         for (int32_t e = threadIdx.x; e < s.m0; e += blockDim.x) { s.e_o2c[e] = e; s.e_c2o[e] = e; }
     }
+    zero_occupancy(s, 0, s.m0);
     if (threadIdx.x == 0) {
         s.n = s.n0; s.m = s.m0; s.m_dp = s.m0; s.n_next = s.n0;
         s.rounds = 0; s.active = s.status == 0; s.max_rounds = max_rounds; s.changed = 0;
-        s.dp_deleted = 0; s.md_deleted = 0;
+        s.dp_deleted = 0; s.md_deleted = 0; s.has_loose = 0;
     }
 }
 
@@ -248,6 +257,7 @@ __global__ void k_plan(InstState *st, Plan *plan, int phase, int tc, BatchCounte
         plan->row_off[count] = rcarry;
         plan->tile_off[count] = tcarry;
         plan->total_rows = rcarry;
+        plan->list_count = 0;
         plan->total_tiles = tcarry;
         plan->any_active = act_any;
         if (phase == 0 && ctr) {
@@ -296,6 +306,11 @@ __global__ void k_scatter(InstState *st, const Plan *plan) {
                     const uint32_t sh = 8u * (c & 3);
                     const uint32_t old = atomicOr(w, (uint32_t)kFp8One << sh);
                     fresh = ((old >> sh) & 0xffu) == 0;
+                    // occupancy of (row block r/128, K block c/128)
+                    uint32_t *ow = s.occ[kPhase] + (int64_t)(r >> 7) * s.occ_words[kPhase] +
+                                   ((c >> 7) >> 5);
+                    const uint32_t ob = 1u << ((c >> 7) & 31);
+                    if (!(*reinterpret_cast<volatile uint32_t *>(ow) & ob)) atomicOr(ow, ob);
                 } else {
                     row[c] = 0;
                 }
@@ -318,7 +333,10 @@ __global__ void k_scatter(InstState *st, const Plan *plan) {
                 }
             }
         }
-        if (kSet && kPhase == 0) s.e_s[ce] = fresh_cnt;  // one thread owns the row
+        if (kSet && kPhase == 0) {
+            s.e_s[ce] = fresh_cnt;  // one thread owns the row
+            if (kDense && s.e_f[ce] > fresh_cnt) s.has_loose = 1;  // f > |e|
+        }
     }
 }
 
@@ -357,6 +375,7 @@ __global__ void k_compact_edges(InstState *st, int count) {
             s.trace[s.rounds][2] = carry;
         }
     }
+    zero_occupancy(s, 1, s.n);
     // vertex rows of this round's MD pass
     for (int32_t r = threadIdx.x; r < s.n; r += blockDim.x) {
         s.v_deg[r] = 0;
@@ -404,12 +423,15 @@ __global__ void k_compact_vertices(InstState *st, int count, BatchCounters *ctr,
         }
         __syncthreads();
         // hyperedge rows of the next round's DP pass
-        if (s.active)
+        if (s.active) {
             for (int32_t r = threadIdx.x; r < s.m; r += blockDim.x) {
                 s.e_f[r] = s.f[s.e_c2o[r]];
                 s.e_s[r] = 0;
                 s.e_del[r] = 0;
             }
+            zero_occupancy(s, 0, s.m);
+            if (threadIdx.x == 0) s.has_loose = 0;
+        }
     }
     if (threadIdx.x == 0 && ctr) {
         atomicAdd(&ctr->active, s.active);
@@ -648,9 +670,13 @@ cudaError_t launch_round_phase(InstState *st, Plan *plan, BatchCounters *ctr, in
     const int grid = grid_for(sms, 8);
     if (phase == 0) launch_scatter<0>(st, plan, true, tc, grid, s);
     else launch_scatter<1>(st, plan, true, tc, grid, s);
+    if (tc) {
+        cudaError_t e = launch_tc_tile_list(st, plan, phase, sms, s);
+        if (e != cudaSuccess) return e;
+    }
     if (ev_contract_begin) cudaEventRecordWithFlags(ev_contract_begin, s, cudaEventRecordExternal);
     if (tc) {
-        cudaError_t e = launch_tc_contract(st, plan, phase, sms, kerr, s);
+        cudaError_t e = launch_tc_contract(st, plan, ctr, phase, sms, kerr, s);
         if (e != cudaSuccess) return e;
     } else {
         k_pop_contract<<<grid_for(sms, 6), 256, 0, s>>>(st, plan, phase);

@@ -22,6 +22,8 @@ struct BatchCounters {
     int32_t status_any;
     int32_t n_done;           // instances that reached their fixpoint in the last round
     int32_t loop_iters;       // rounds run by the device-side loop in this launch
+    unsigned long long mma_kblocks;  // K blocks contracted since load (tcgen05 path)
+    unsigned long long mma_tiles;    // tiles contracted since load (tcgen05 path)
 };
 
 cudaError_t launch_validate(InstState *st, int count, cudaStream_t s);
@@ -49,8 +51,11 @@ cudaError_t launch_alive_masks_batch(const InstState *st, int count, uint8_t *al
                                      uint8_t *alive_e, cudaStream_t s);
 
 // tcgen05 contraction (contract_tc.cu)
-cudaError_t launch_tc_contract(InstState *st, Plan *plan, int phase, int sms, int32_t *kerr,
-                               cudaStream_t s);
+cudaError_t launch_tc_contract(InstState *st, Plan *plan, BatchCounters *ctr, int phase, int sms,
+                               int32_t *kerr, cudaStream_t s);
+// The tiles of phase `phase` that hold nonzero counts (or, in a DP pass of
+// an instance with a hyperedge f > |e|, all tiles), into plan->tile_list.
+cudaError_t launch_tc_tile_list(InstState *st, Plan *plan, int phase, int sms, cudaStream_t s);
 cudaError_t prepare_tc_contract();  // once per process, before any capture
 bool make_operand_tmap(void *out128, const void *base, int64_t pitch, int64_t rows);
 size_t tmap_bytes();

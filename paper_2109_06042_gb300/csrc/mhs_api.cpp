@@ -49,6 +49,8 @@ inline int64_t kpad_bytes(int64_t K) { return round_up(std::max<int64_t>(K, 1), 
 inline int64_t kpad_words(int64_t K) {
     return round_up(std::max<int64_t>((K + 31) / 32, 1), 4);
 }
+// occupancy words per row block: one bit per K block of kTcK columns
+inline int64_t occ_words(int64_t K) { return (kpad_bytes(K) / kTcK + 31) / 32; }
 
 }  // namespace
 
@@ -158,7 +160,9 @@ mhs_status check_options(const mhs_options *opt, mhs_options *out) {
     if (out->max_rounds < 0) return fail(MHS_EINVAL, "options.max_rounds must be >= 0");
     if (out->layout < 0 || out->layout > 2)
         return fail(MHS_EINVAL, "options.layout must be 0 (auto), 1 (input) or 2 (sorted)");
-    for (int i = 0; i < 4; ++i)
+    if (out->sparsity < 0 || out->sparsity > 2)
+        return fail(MHS_EINVAL, "options.sparsity must be 0 (auto), 1 (skip) or 2 (dense)");
+    for (int i = 0; i < 3; ++i)
         if (out->reserved[i] != 0) return fail(MHS_EINVAL, "options.reserved must be zero");
     return MHS_OK;
 }
@@ -191,6 +195,7 @@ mhs_status validate_host(int32_t n, int32_t m, const int64_t *eptr64, const int3
 }
 
 struct Layout {  // byte offsets inside the arena for one instance
+    int64_t occ0, occ1;
     int64_t eptr, evtx, f;
     int64_t v_o2c, v_c2o, e_o2c, e_c2o, e_f, e_s, v_deg, v_maxf, v_cnt, e_del, v_del;
     int64_t A, At, Ab, Atb;
@@ -238,6 +243,7 @@ mhs_status create(int32_t count, const int32_t *n, const int32_t *m, const int64
     h->sum_nnz = sum_z;
     h->sum_m = sum_m;
     int64_t c_m1 = 0, c_z = 0, c_m = 0;
+    int64_t tiles_dp = 0, tiles_md = 0;
     for (int b = 0; b < count; ++b) {
         Layout &L = lay[b];
         const int64_t n0 = n[b], m0 = m[b], z = nnz[b];
@@ -265,6 +271,16 @@ mhs_status create(int32_t count, const int32_t *n, const int32_t *m, const int64
         L.v_cnt = ar.take(4 * (n0 + 1));
         L.e_del = ar.take(m0);
         L.v_del = ar.take(n0);
+        if (dense) {
+            const int64_t arows = round_up(std::max<int64_t>(m0, 1), kRowAlign);
+            const int64_t atrows = round_up(std::max<int64_t>(n0, 1), kRowAlign);
+            L.occ0 = ar.take(4 * (arows / kTcM) * occ_words(n0));
+            L.occ1 = ar.take(4 * (atrows / kTcM) * occ_words(m0));
+        } else {
+            L.occ0 = L.occ1 = -1;
+        }
+        tiles_dp += tc_tiles((int32_t)m0);
+        tiles_md += tc_tiles((int32_t)n0);
     }
     // the operands of all instances, contiguous, zeroed once at load: the
     // scatter/clear passes leave them all-zero between phases
@@ -294,6 +310,8 @@ mhs_status create(int32_t count, const int32_t *n, const int32_t *m, const int64
     const int64_t off_ctr = ar.take(sizeof(BatchCounters));
     const int64_t off_kerr = ar.take(4);
     const int64_t off_tmaps = ar.take(dense ? (int64_t)tmap_bytes() * 2 * count : 0);
+    const int64_t list_cap = dense ? std::max<int64_t>(std::max(tiles_dp, tiles_md), 1) : 0;
+    const int64_t off_list = ar.take(8 * list_cap);
     glob_off = off_tmaps;
 
     cudaMemPool_t pool;
@@ -332,6 +350,7 @@ mhs_status create(int32_t count, const int32_t *n, const int32_t *m, const int64
         s.nnz0 = nnz[b];
         s.k = k[b];
         s.layout_sorted = opt.layout != MHS_LAYOUT_INPUT;
+        s.no_skip = opt.sparsity == MHS_SPARSITY_DENSE;
         s.eptr = reinterpret_cast<int32_t *>(base + L.eptr);
         s.evtx = reinterpret_cast<int32_t *>(base + L.evtx);
         s.f = reinterpret_cast<int32_t *>(base + L.f);
@@ -351,6 +370,10 @@ mhs_status create(int32_t count, const int32_t *n, const int32_t *m, const int64
         s.A_rows = (int32_t)arows;
         s.At_rows = (int32_t)atrows;
         if (dense) {
+            s.occ[0] = reinterpret_cast<uint32_t *>(base + L.occ0);
+            s.occ[1] = reinterpret_cast<uint32_t *>(base + L.occ1);
+            s.occ_words[0] = (int32_t)occ_words(n[b]);
+            s.occ_words[1] = (int32_t)occ_words(m[b]);
             s.A = base + L.A;
             s.At = base + L.At;
             s.A_pitch = kpad_bytes(n[b]);
@@ -372,8 +395,11 @@ mhs_status create(int32_t count, const int32_t *n, const int32_t *m, const int64
     p.count = count;
     p.row_off = reinterpret_cast<int32_t *>(base + off_rowoff);
     p.tile_off = reinterpret_cast<int64_t *>(base + off_tileoff);
+    p.tile_list = reinterpret_cast<int64_t *>(base + off_list);
+    p.list_cap = (int32_t)std::min<int64_t>(list_cap, INT32_MAX);
     ce = cudaMemcpyAsync(h->dplan, &p, sizeof(p), cudaMemcpyHostToDevice, h->stream);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(h->dkerr, 0, 4, h->stream);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(h->dctr, 0, sizeof(BatchCounters), h->stream);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);  // p is a stack object
     if (ce != cudaSuccess) {
         destroy(h);
@@ -1017,6 +1043,16 @@ mhs_status mhs_export(const mhs_instance *inst, int32_t index, int32_t *edge_ptr
         if (edge_ptr_out) edge_ptr_out[i + 1] = (int32_t)w;
         if (demand_out) demand_out[i] = f[e];
     }
+    return MHS_OK;
+}
+
+mhs_status mhs_work_stats(const mhs_instance *inst, int64_t *mma_kblocks, int64_t *mma_tiles) {
+    if (!inst) return fail(MHS_EINVAL, "instance is NULL");
+    BatchCounters c;
+    CUDA_TRY(cudaMemcpyAsync(&c, inst->dctr, sizeof(c), cudaMemcpyDeviceToHost, inst->stream));
+    CUDA_TRY(cudaStreamSynchronize(inst->stream));
+    if (mma_kblocks) *mma_kblocks = (int64_t)c.mma_kblocks;
+    if (mma_tiles) *mma_tiles = (int64_t)c.mma_tiles;
     return MHS_OK;
 }
 

@@ -83,6 +83,13 @@ struct InstState {
     // tcgen05 tensor maps (CUtensorMap, 128 bytes each) for A and At, in device memory
     const void *tmap_A;
     const void *tmap_At;
+    // block-sparse skipping (tcgen05 path): per row block of 128 rows, one
+    // bit per K block of 128 columns that holds a nonzero of the operand of
+    // phase p (0: A, 1: At); occ_words[p] words per row block
+    uint32_t *occ[2];
+    int32_t occ_words[2];
+    int32_t has_loose;     // DP: some hyperedge has f > |e| (zero counts then matter)
+    int32_t no_skip;       // 1: contract every tile and K block (dense formulation)
     // offsets of this instance's ids in the concatenated ids of its batch
     int64_t v_base, e_base;
     // per round r < kTraceRounds: hyperedges and vertices entering DP, hyperedges after DP
@@ -93,6 +100,9 @@ struct InstState {
 struct Plan {
     int32_t count;          // instances
     int32_t any_active;
+    int64_t *tile_list;     // tcgen05: packed (instance, row block, column block) to contract
+    int32_t list_count;     // entries in tile_list this phase
+    int32_t list_cap;
     int32_t total_rows;     // current hyperedges to scatter this phase
     int32_t pad_;
     int64_t total_tiles;    // contraction tiles this phase
@@ -104,6 +114,16 @@ struct Plan {
 __host__ __device__ inline int64_t pop_tiles(int32_t R) {
     int64_t t = (R + kPopTile - 1) / kPopTile;
     return R > 1 ? t * (t + 1) / 2 : 0;
+}
+
+// Packed tile-list entries.
+__host__ __device__ inline int64_t pack_tile(int b, int32_t bi, int32_t bj) {
+    return ((int64_t)b << 40) | ((int64_t)bi << 20) | (int64_t)bj;
+}
+__host__ __device__ inline void unpack_tile(int64_t v, int *b, int32_t *bi, int32_t *bj) {
+    *b = (int)(v >> 40);
+    *bi = (int32_t)((v >> 20) & 0xFFFFF);
+    *bj = (int32_t)(v & 0xFFFFF);
 }
 
 // tcgen05 tiles: row blocks of kTcM, column blocks of kTcN; a tile is needed

@@ -42,6 +42,8 @@ namespace {
 inline int64_t up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 inline int64_t kbytes(int64_t K) { return up(K > 0 ? K : 1, kTcK); }
 inline int64_t kwords(int64_t K) { return up(((K + 31) / 32) > 0 ? (K + 31) / 32 : 1, 4); }
+inline int64_t occ_words(int64_t K) { return (kbytes(K) / kTcK + 31) / 32; }
+constexpr int64_t kServerListCap = 16 << 20;  // tile-list entries shared by the slots
 inline int64_t now_ns() {
     return std::chrono::duration_cast<std::chrono::nanoseconds>(
                std::chrono::steady_clock::now().time_since_epoch())
@@ -54,6 +56,7 @@ struct Request {
     int64_t k = 0;
     std::vector<int32_t> ptr, vtx, dem;
     int64_t footprint = 0;
+    int64_t tiles = 0;  // most tile-list entries one of its phases can need
     int64_t t_submit = 0, t_admit = 0, t_done = 0;
     bool done = false;
     mhs_status status = MHS_OK;
@@ -64,7 +67,7 @@ struct Request {
 // Device layout of one admitted instance inside its arena.
 struct Layout {
     int64_t eptr, evtx, f, v_o2c, v_c2o, e_o2c, e_c2o, e_f, e_s, v_deg, v_maxf, v_cnt, e_del,
-        v_del, tmaps, dense, dense_bytes, bytes;
+        v_del, occ0, occ1, tmaps, dense, dense_bytes, bytes;
 };
 
 Layout plan_layout(int32_t n, int32_t m, int64_t nnz, bool dense) {
@@ -89,6 +92,11 @@ Layout plan_layout(int32_t n, int32_t m, int64_t nnz, bool dense) {
     L.v_cnt = take(4 * ((int64_t)n + 1));
     L.e_del = take(m);
     L.v_del = take(n);
+    {
+        const int64_t arows = up(m > 0 ? m : 1, kRowAlign), atrows = up(n > 0 ? n : 1, kRowAlign);
+        L.occ0 = take(dense ? 4 * (arows / kTcM) * occ_words(n) : 0);
+        L.occ1 = take(dense ? 4 * (atrows / kTcM) * occ_words(m) : 0);
+    }
     L.tmaps = take(dense ? 2 * (int64_t)tmap_bytes() : 0);
     L.dense = b;
     const int64_t arows = up(m > 0 ? m : 1, kRowAlign), atrows = up(n > 0 ? n : 1, kRowAlign);
@@ -109,6 +117,7 @@ struct Slot {
     std::shared_ptr<Request> req;
     uint8_t *arena = nullptr;
     int64_t bytes = 0;
+    int64_t tiles = 0;
 };
 
 }  // namespace
@@ -135,6 +144,7 @@ struct mhs_server {
     std::vector<Slot> slots;   // owned by the worker thread
     int32_t active_count = 0;  // busy slots (guarded by mu)
     int64_t in_use_release = 0;
+    int64_t tiles_in_use = 0, tiles_release = 0;  // tile-list entries reserved by busy slots
     int64_t in_use = 0, peak = 0;
     // queues
     std::mutex mu;
@@ -167,6 +177,7 @@ mhs_status admit(mhs_server *S, int si, std::shared_ptr<Request> req) {
     s.nnz0 = nnz;
     s.k = req->k;
     s.layout_sorted = S->opt.layout != MHS_LAYOUT_INPUT;
+    s.no_skip = S->opt.sparsity == MHS_SPARSITY_DENSE;
     s.eptr = reinterpret_cast<int32_t *>(a + L.eptr);
     s.evtx = reinterpret_cast<int32_t *>(a + L.evtx);
     s.f = reinterpret_cast<int32_t *>(a + L.f);
@@ -187,6 +198,10 @@ mhs_status admit(mhs_server *S, int si, std::shared_ptr<Request> req) {
     s.At_rows = (int32_t)atrows;
     uint8_t *maps = S->hmaps + (size_t)si * 2 * tmap_bytes();
     if (dense) {
+        s.occ[0] = reinterpret_cast<uint32_t *>(a + L.occ0);
+        s.occ[1] = reinterpret_cast<uint32_t *>(a + L.occ1);
+        s.occ_words[0] = (int32_t)occ_words(req->n);
+        s.occ_words[1] = (int32_t)occ_words(req->m);
         s.A = a + L.dense;
         s.At = s.A + arows * kbytes(req->n);
         s.A_pitch = kbytes(req->n);
@@ -229,6 +244,7 @@ mhs_status admit(mhs_server *S, int si, std::shared_ptr<Request> req) {
     sl.req = std::move(req);
     sl.arena = a;
     sl.bytes = L.bytes;
+    sl.tiles = sl.req->tiles;
     std::lock_guard<std::mutex> lk(S->mu);
     ++S->active_count;
     return MHS_OK;
@@ -292,6 +308,7 @@ void retire(mhs_server *S, const std::vector<int> &fin) {
         cudaFreeAsync(sl.arena, S->stream);
         done.push_back(sl.req);
         S->in_use_release += sl.bytes;
+        S->tiles_release += sl.tiles;
         sl = Slot();
     }
     {
@@ -307,6 +324,8 @@ void retire(mhs_server *S, const std::vector<int> &fin) {
         }
         S->in_use -= S->in_use_release;
         S->in_use_release = 0;
+        S->tiles_in_use -= S->tiles_release;
+        S->tiles_release = 0;
     }
     S->cv_done.notify_all();
 }
@@ -328,12 +347,14 @@ void worker_loop(mhs_server *S) {
                 while (!S->pending.empty()) {
                     auto &front = S->pending.front();
                     if (S->in_use + front->footprint > S->opt.hbm_budget_bytes) break;
+                    if (S->tiles_in_use + front->tiles > kServerListCap) break;
                     while (si < S->slots_n && (S->slots[si].busy ||
                                                std::any_of(to_admit.begin(), to_admit.end(),
                                                            [si](auto &p) { return p.first == si; })))
                         ++si;
                     if (si >= S->slots_n) break;
                     S->in_use += front->footprint;
+                    S->tiles_in_use += front->tiles;
                     S->peak = std::max(S->peak, S->in_use);
                     front->t_admit = now_ns();
                     to_admit.emplace_back(si, front);
@@ -348,6 +369,7 @@ void worker_loop(mhs_server *S) {
             if (st != MHS_OK) {
                 std::lock_guard<std::mutex> lk(S->mu);
                 S->in_use -= p.second->footprint;
+                S->tiles_in_use -= p.second->tiles;
                 p.second->status = st;
                 p.second->done = true;
                 p.second->t_done = now_ns();
@@ -463,7 +485,9 @@ mhs_status mhs_server_create(const mhs_server_options *opt_in, void *cuda_stream
         return set_error(MHS_EINVAL, "contraction must be 0, 1 or 2");
     if (opt.hbm_budget_bytes < 0) return set_error(MHS_EINVAL, "hbm_budget_bytes must be >= 0");
     if (opt.layout < 0 || opt.layout > 2) return set_error(MHS_EINVAL, "layout must be 0, 1 or 2");
-    for (int i = 0; i < 2; ++i)
+    if (opt.sparsity < 0 || opt.sparsity > 2)
+        return set_error(MHS_EINVAL, "sparsity must be 0, 1 or 2");
+    for (int i = 0; i < 1; ++i)
         if (opt.reserved[i]) return set_error(MHS_EINVAL, "reserved options must be zero");
     auto *S = new mhs_server();
     S->opt = opt;
@@ -501,7 +525,9 @@ mhs_status mhs_server_create(const mhs_server_options *opt_in, void *cuda_stream
     const int64_t o_ctr = o_tile + up(8 * (ns + 1), 256);
     const int64_t o_kerr = o_ctr + up(sizeof(BatchCounters), 256);
     const int64_t o_done = o_kerr + 256;
-    const int64_t total = o_done + up(4 * ns, 256);
+    const int64_t o_list = o_done + up(4 * ns, 256);
+    const int64_t list_cap = S->contraction == kFp8 ? kServerListCap : 1;
+    const int64_t total = o_list + up(8 * list_cap, 256);
     if (cudaMallocFromPoolAsync(reinterpret_cast<void **>(&S->ctl), (size_t)total, S->pool,
                                 S->stream) != cudaSuccess)
         return bail(set_error(MHS_ENOMEM, "server control allocation failed"));
@@ -522,7 +548,9 @@ mhs_status mhs_server_create(const mhs_server_options *opt_in, void *cuda_stream
     p.count = S->slots_n;
     p.row_off = reinterpret_cast<int32_t *>(S->ctl + o_row);
     p.tile_off = reinterpret_cast<int64_t *>(S->ctl + o_tile);
-    cudaError_t e = cudaMemsetAsync(S->ctl, 0, (size_t)total, S->stream);
+    p.tile_list = reinterpret_cast<int64_t *>(S->ctl + o_list);
+    p.list_cap = (int32_t)list_cap;
+    cudaError_t e = cudaMemsetAsync(S->ctl, 0, (size_t)o_list, S->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(S->dplan, &p, sizeof(p), cudaMemcpyHostToDevice, S->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
@@ -566,6 +594,10 @@ mhs_status mhs_submit(mhs_server *S, int32_t n, int32_t m, const int32_t *edge_p
     r->vtx.assign(edge_vtx, edge_vtx + nnz);
     r->dem.assign(demand, demand + m);
     r->footprint = plan_layout(n, m, nnz, S->contraction == kFp8).bytes;
+    r->tiles = std::max(tc_tiles(m), tc_tiles(n));
+    if (S->contraction == kFp8 && r->tiles > kServerListCap)
+        return set_error(MHS_ENOMEM, "instance needs %lld tiles, over the server's %lld",
+                         (long long)r->tiles, (long long)kServerListCap);
     if (r->footprint > S->opt.hbm_budget_bytes)
         return set_error(MHS_ENOMEM, "instance needs %lld bytes, over the server budget %lld",
                          (long long)r->footprint, (long long)S->opt.hbm_budget_bytes);

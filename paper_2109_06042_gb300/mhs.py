@@ -33,12 +33,13 @@ class MhsError(RuntimeError):
 
 
 LAYOUTS = {"auto": 0, "input": 1, "sorted": 2}
+SPARSITY = {"auto": 0, "skip": 1, "dense": 2}
 
 
 class Options(ctypes.Structure):
     _fields_ = [("contraction", ctypes.c_int32), ("max_rounds", ctypes.c_int32),
                 ("use_graphs", ctypes.c_int32), ("layout", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("sparsity", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class RoundStats(ctypes.Structure):
@@ -53,7 +54,8 @@ class RoundStats(ctypes.Structure):
 class ServerOptions(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("max_slots", ctypes.c_int32),
                 ("queue_capacity", ctypes.c_int32), ("contraction", ctypes.c_int32),
-                ("layout", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("layout", ctypes.c_int32), ("sparsity", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 1)]
 
 
 class ServerStats(ctypes.Structure):
@@ -94,6 +96,7 @@ _SIGS = {
     "mhs_trace_at": (_i32, [_vp, _i32, _P32, _i32, _P32]),
     "mhs_export": (_i32, [_vp, _i32, _P32, _i32, _P32, _i64, _P32, _P32, _P32, _P64]),
     "mhs_set_timing": (_i32, [_vp, _i32]),
+    "mhs_work_stats": (_i32, [_vp, _P64, _P64]),
     "mhs_last_timing": (_i32, [_vp, ctypes.POINTER(ctypes.c_float)]),
     "mhs_kernelize_noalloc": (_i32, [_i32, _i32, _vp, _vp, _vp, _i32, _vp, _vp, _P32, _vp,
                                      ctypes.c_char_p, ctypes.c_size_t]),
@@ -143,6 +146,12 @@ def _p32(a):
 
 
 _DEFAULT_LAYOUT = ["auto"]
+_DEFAULT_SPARSITY = ["auto"]
+
+
+def set_default_sparsity(sparsity: str):
+    """Sparsity policy used by the helpers below when none is given ('auto', 'skip', 'dense')."""
+    _DEFAULT_SPARSITY[0] = sparsity
 
 
 def set_default_layout(layout: str):
@@ -150,7 +159,8 @@ def set_default_layout(layout: str):
     _DEFAULT_LAYOUT[0] = layout
 
 
-def make_options(contraction="auto", max_rounds=0, use_graphs=True, layout=None) -> Options:
+def make_options(contraction="auto", max_rounds=0, use_graphs=True, layout=None,
+                 sparsity=None) -> Options:
     o = Options()
     _check(lib().mhs_default_options(ctypes.byref(o)))
     o.contraction = CONTRACTIONS[contraction] if isinstance(contraction, str) else int(contraction)
@@ -158,6 +168,8 @@ def make_options(contraction="auto", max_rounds=0, use_graphs=True, layout=None)
     o.use_graphs = int(bool(use_graphs))
     lay = _DEFAULT_LAYOUT[0] if layout is None else layout
     o.layout = LAYOUTS[lay] if isinstance(lay, str) else int(lay)
+    sp = _DEFAULT_SPARSITY[0] if sparsity is None else sparsity
+    o.sparsity = SPARSITY[sp] if isinstance(sp, str) else int(sp)
     return o
 
 
@@ -179,7 +191,7 @@ class Instance:
     # ---- loading ----
     @classmethod
     def load(cls, inst, contraction="auto", max_rounds=0, use_graphs=True, stream=None,
-             layout=None):
+             layout=None, sparsity=None):
         """mhs_load from host arrays of an ``instances.Instance``-like object."""
         ptr = np.ascontiguousarray(inst.edge_ptr, dtype=np.int32)
         vtx = np.ascontiguousarray(inst.edge_vtx, dtype=np.int32)
@@ -188,7 +200,7 @@ class Instance:
             vtx = np.zeros(1, np.int32)
         if dem.size == 0:
             dem = np.zeros(1, np.int32)
-        opt = make_options(contraction, max_rounds, use_graphs, layout)
+        opt = make_options(contraction, max_rounds, use_graphs, layout, sparsity)
         h = ctypes.c_void_p()
         _check(lib().mhs_load(int(inst.n), int(inst.m), _p32(ptr), _p32(vtx), _p32(dem),
                               int(inst.k), ctypes.byref(opt), _stream_ptr(stream),
@@ -197,9 +209,9 @@ class Instance:
 
     @classmethod
     def load_device(cls, n, m, edge_ptr, edge_vtx, demand, k, contraction="auto", max_rounds=0,
-                    use_graphs=True, stream=None):
+                    use_graphs=True, stream=None, layout=None, sparsity=None):
         """mhs_load_device from CUDA tensors (int32, contiguous)."""
-        opt = make_options(contraction, max_rounds, use_graphs)
+        opt = make_options(contraction, max_rounds, use_graphs, layout, sparsity)
         h = ctypes.c_void_p()
         _check(lib().mhs_load_device(int(n), int(m), ctypes.c_void_p(edge_ptr.data_ptr()),
                                      ctypes.c_void_p(edge_vtx.data_ptr()),
@@ -228,8 +240,8 @@ class Instance:
 
     @classmethod
     def load_batch_arrays(cls, count, n, m, ptr, vtx, dem, k, contraction="auto", max_rounds=0,
-                          use_graphs=True, stream=None):
-        opt = make_options(contraction, max_rounds, use_graphs)
+                          use_graphs=True, stream=None, layout=None, sparsity=None):
+        opt = make_options(contraction, max_rounds, use_graphs, layout, sparsity)
         h = ctypes.c_void_p()
         _check(lib().mhs_load_batch(int(count), _p32(n), _p32(m), ptr.ctypes.data_as(_P64),
                                     _p32(vtx), _p32(dem), k.ctypes.data_as(_P64),
@@ -238,13 +250,13 @@ class Instance:
 
     @classmethod
     def load_batch_device(cls, n, m, k, edge_ptr, edge_vtx, demand, contraction="auto",
-                          max_rounds=0, use_graphs=True, stream=None):
+                          max_rounds=0, use_graphs=True, stream=None, layout=None, sparsity=None):
         """mhs_load_batch_device: n, m, k host numpy arrays; edge_ptr (int64),
         edge_vtx, demand (int32) CUDA tensors over the concatenated instances."""
         n = np.ascontiguousarray(n, dtype=np.int32)
         m = np.ascontiguousarray(m, dtype=np.int32)
         k = np.ascontiguousarray(k, dtype=np.int64)
-        opt = make_options(contraction, max_rounds, use_graphs)
+        opt = make_options(contraction, max_rounds, use_graphs, layout, sparsity)
         h = ctypes.c_void_p()
         _check(lib().mhs_load_batch_device(int(n.size), _p32(n), _p32(m),
                                            ctypes.c_void_p(edge_ptr.data_ptr()),
@@ -272,6 +284,13 @@ class Instance:
         a = (ctypes.c_float * 4)()
         _check(lib().mhs_last_timing(self._h, a))
         return {"dp_ms": a[0], "md_ms": a[1], "other_ms": a[2], "total_ms": a[3]}
+
+    def work_stats(self):
+        """(K blocks of 128x256x128 MACs issued, tiles contracted) since load."""
+        kb = ctypes.c_int64()
+        tl = ctypes.c_int64()
+        _check(lib().mhs_work_stats(self._h, ctypes.byref(kb), ctypes.byref(tl)))
+        return int(kb.value), int(tl.value)
 
     @property
     def count(self) -> int:
@@ -343,9 +362,11 @@ class Instance:
             pass
 
 
-def kernelize(inst, contraction="auto", max_rounds=0, use_graphs=True, layout=None) -> dict:
+def kernelize(inst, contraction="auto", max_rounds=0, use_graphs=True, layout=None,
+              sparsity=None) -> dict:
     """Load, reduce to the fixpoint and return the result of one host instance."""
-    with Instance.load(inst, contraction, max_rounds, use_graphs, layout=layout) as h:
+    with Instance.load(inst, contraction, max_rounds, use_graphs, layout=layout,
+                       sparsity=sparsity) as h:
         h.kernelize()
         return h.result()
 
@@ -354,7 +375,7 @@ class Server:
     """Continuous-batching server (mhs_server_*): submit host instances, poll results."""
 
     def __init__(self, hbm_budget_bytes=0, max_slots=256, queue_capacity=65536,
-                 contraction="auto", stream=None, layout=None):
+                 contraction="auto", stream=None, layout=None, sparsity=None):
         o = ServerOptions()
         _check(lib().mhs_server_default_options(ctypes.byref(o)))
         o.hbm_budget_bytes = int(hbm_budget_bytes)
@@ -363,6 +384,8 @@ class Server:
         o.contraction = CONTRACTIONS[contraction] if isinstance(contraction, str) else int(contraction)
         lay = _DEFAULT_LAYOUT[0] if layout is None else layout
         o.layout = LAYOUTS[lay] if isinstance(lay, str) else int(lay)
+        sp = _DEFAULT_SPARSITY[0] if sparsity is None else sparsity
+        o.sparsity = SPARSITY[sp] if isinstance(sp, str) else int(sp)
         h = ctypes.c_void_p()
         _check(lib().mhs_server_create(ctypes.byref(o), _stream_ptr(stream), ctypes.byref(h)))
         self._h = h

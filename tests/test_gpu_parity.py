@@ -324,3 +324,38 @@ def test_layouts_and_tie_breaks(mhs, mode, layout):
         inst = I.config_interval(seed, n=3000, m=6000)
         _same(mhs.kernelize(inst, contraction=mode, layout=layout), O.reduce(inst),
               f"{layout} interval {seed}")
+
+
+@pytest.mark.parametrize("sparsity", ["skip", "dense"])
+def test_zero_tiles_with_loose_hyperedge(mhs, sparsity):
+    """A hyperedge with f > |e| supersedes hyperedges it shares no vertex
+    with (count 0): tiles with no shared K block must still be tested in DP
+    then.  e_0 = {0} with f = 3 pushes 3 - 1 = 2 units of demand to every
+    other hyperedge, so every hyperedge with f <= 2 goes."""
+    rng = np.random.default_rng(5)
+    n, m = 1200, 2500
+    edges = [[0]] + [sorted(rng.choice(np.arange(300, n), size=int(rng.integers(2, 9)),
+                                       replace=False).tolist()) for _ in range(m - 1)]
+    dem = [3] + [int(rng.integers(1, 4)) for _ in range(m - 1)]
+    inst = I.from_edges(n, edges, dem)
+    ref = O.reduce(inst)
+    for mode in MODES:
+        _same(mhs.kernelize(inst, contraction=mode, sparsity=sparsity), ref, f"{mode} {sparsity}")
+    # and a feasible instance whose blocks are mostly disjoint (interval layout)
+    inst = I.config_interval(4, n=6000, m=12000)
+    _same(mhs.kernelize(inst, sparsity=sparsity), O.reduce(inst), f"interval {sparsity}")
+
+
+def test_skip_and_dense_agree_and_skip_does_less(mhs):
+    inst = I.config_interval(1, n=8000, m=16000)
+    with mhs.Instance.load(inst, contraction="fp8", sparsity="dense") as h:
+        h.kernelize()
+        dense = h.result()
+        kb_dense, t_dense = h.work_stats()
+    with mhs.Instance.load(inst, contraction="fp8", sparsity="skip") as h:
+        h.kernelize()
+        skip = h.result()
+        kb_skip, t_skip = h.work_stats()
+    for key in ("vertices", "edges", "demands", "rounds"):
+        assert np.array_equal(np.asarray(dense[key]), np.asarray(skip[key]))
+    assert 0 < kb_skip < kb_dense and 0 < t_skip <= t_dense
