@@ -306,7 +306,8 @@ typedef struct {
     int32_t contraction;      /* mhs_contraction */
     int32_t layout;           /* mhs_layout */
     int32_t sparsity;         /* mhs_sparsity */
-    int32_t reserved[1];      /* must be zero */
+    int32_t small_items;      /* requests with n + m <= this go to the small-request lane
+                                 (0: 8192; < 0: a single lane for all requests) */
 } mhs_server_options;
 
 typedef struct {
@@ -317,8 +318,11 @@ typedef struct {
 
 mhs_status mhs_server_default_options(mhs_server_options *opt);
 
-/* Start a server on the current device; all its GPU work runs on cuda_stream
- * (NULL: a stream of its own).  opt may be NULL (defaults). */
+/* Start a server on the current device.  Requests are split by size into
+ * two lanes, each with its own slot table, worker thread and stream: small
+ * requests (n + m <= small_items) are batched on a high-priority stream the
+ * server creates; large ones run a few at a time on cuda_stream (NULL: a
+ * stream of its own).  opt may be NULL (defaults). */
 mhs_status mhs_server_create(const mhs_server_options *opt, void *cuda_stream, mhs_server **out);
 
 /*

@@ -14,6 +14,12 @@
 //      wakes the pollers.
 // Requests that arrive while others are on the GPU join at the next round
 // boundary, so work of different sizes overlaps in the same launches.
+// Requests are split by size into two lanes, each with its own slot table,
+// captured round graph, worker thread and stream: small instances are
+// batched by the hundreds on a high-priority stream, large ones (which fill
+// the GPU on their own) run a few at a time on the other, so a small
+// request never waits for the rounds of a large one.  The HBM budget, the
+// queue limit and the tickets are shared.
 // The result of an instance does not depend on what else is in flight:
 // instances share no state, and every per-instance quantity lives in the
 // instance's own arena.
@@ -122,16 +128,14 @@ struct Slot {
 
 }  // namespace
 
-struct mhs_server {
-    mhs_server_options opt{};
-    int contraction = kFp8;
-    int device = 0, sms = 0;
+struct Lane {
+    int id = 0;
+    mhs_server *S = nullptr;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
-    cudaMemPool_t pool = nullptr;
     int32_t slots_n = 0;
-    // device slot table and round bookkeeping
-    uint8_t *ctl = nullptr;  // one allocation: states, plan, offsets, counters, done list
+    // device slot table and round bookkeeping (one allocation)
+    uint8_t *ctl = nullptr;
     InstState *dstate = nullptr;
     Plan *dplan = nullptr;
     BatchCounters *dctr = nullptr;
@@ -141,34 +145,46 @@ struct mhs_server {
     uint8_t *hmaps = nullptr;       // pinned: 2 tensor maps per slot, staged for upload
     InstState *hstates = nullptr;   // pinned: states of the slots retired in a round
     cudaGraphExec_t graph = nullptr;
-    std::vector<Slot> slots;   // owned by the worker thread
-    int32_t active_count = 0;  // busy slots (guarded by mu)
-    int64_t in_use_release = 0;
-    int64_t tiles_in_use = 0, tiles_release = 0;  // tile-list entries reserved by busy slots
-    int64_t in_use = 0, peak = 0;
-    // queues
+    int64_t list_cap = 0;
+    std::vector<Slot> slots;                         // owned by the lane's worker
+    std::deque<std::shared_ptr<Request>> pending;    // guarded by S->mu
+    int32_t active_count = 0;                        // guarded by S->mu
+    int64_t tiles_in_use = 0;                        // guarded by S->mu
+    int64_t in_use_release = 0, tiles_release = 0;   // worker-local
+    std::condition_variable cv_work;
+    std::thread worker;
+    int64_t rounds = 0;
+};
+
+struct mhs_server {
+    mhs_server_options opt{};
+    int contraction = kFp8;
+    int device = 0, sms = 0;
+    cudaMemPool_t pool = nullptr;
+    int64_t small_items = 0;  // n + m at most for the small-request lane
+    Lane lanes[2];
+    // shared state
     std::mutex mu;
-    std::condition_variable cv_work, cv_done;
-    std::deque<std::shared_ptr<Request>> pending;
+    std::condition_variable cv_done;
     std::unordered_map<uint64_t, std::shared_ptr<Request>> table;
     uint64_t next_ticket = 1;
     bool stop = false, paused = false;
     mhs_status fatal = MHS_OK;
-    std::thread worker;
-    // stats
-    int64_t submitted = 0, admitted = 0, completed = 0, rounds = 0;
+    int64_t in_use = 0, peak = 0;
+    int64_t submitted = 0, admitted = 0, completed = 0;
 };
 
 namespace {
 
 // Upload and initialise one request into slot `si` (worker thread only).
-mhs_status admit(mhs_server *S, int si, std::shared_ptr<Request> req) {
+mhs_status admit(Lane &Ln, int si, std::shared_ptr<Request> req) {
+    mhs_server *S = Ln.S;
     const bool dense = S->contraction == kFp8;
     const int64_t nnz = req->ptr.empty() ? 0 : req->ptr.back();
     Layout L = plan_layout(req->n, req->m, nnz, dense);
     uint8_t *a = nullptr;
     cudaError_t e = cudaMallocFromPoolAsync(reinterpret_cast<void **>(&a), (size_t)L.bytes, S->pool,
-                                            S->stream);
+                                            Ln.stream);
     if (e != cudaSuccess) return set_error(MHS_ENOMEM, "server: arena allocation failed");
     InstState s;
     std::memset(&s, 0, sizeof(s));
@@ -196,7 +212,7 @@ mhs_status admit(mhs_server *S, int si, std::shared_ptr<Request> req) {
     const int64_t atrows = up(req->n > 0 ? req->n : 1, kRowAlign);
     s.A_rows = (int32_t)arows;
     s.At_rows = (int32_t)atrows;
-    uint8_t *maps = S->hmaps + (size_t)si * 2 * tmap_bytes();
+    uint8_t *maps = Ln.hmaps + (size_t)si * 2 * tmap_bytes();
     if (dense) {
         s.occ[0] = reinterpret_cast<uint32_t *>(a + L.occ0);
         s.occ[1] = reinterpret_cast<uint32_t *>(a + L.occ1);
@@ -210,7 +226,7 @@ mhs_status admit(mhs_server *S, int si, std::shared_ptr<Request> req) {
         s.tmap_At = a + L.tmaps + tmap_bytes();
         if (!make_operand_tmap(maps, s.A, s.A_pitch, s.A_rows) ||
             !make_operand_tmap(maps + tmap_bytes(), s.At, s.At_pitch, s.At_rows)) {
-            cudaFreeAsync(a, S->stream);
+            cudaFreeAsync(a, Ln.stream);
             return set_error(MHS_ECUDA, "server: tensor map encoding failed");
         }
     } else {
@@ -221,32 +237,32 @@ mhs_status admit(mhs_server *S, int si, std::shared_ptr<Request> req) {
     }
     // pageable sources: each copy has staged its source when it returns
     e = cudaMemcpyAsync(a + L.eptr, req->ptr.data(), 4 * req->ptr.size(), cudaMemcpyHostToDevice,
-                        S->stream);
+                        Ln.stream);
     if (e == cudaSuccess && nnz > 0)
         e = cudaMemcpyAsync(a + L.evtx, req->vtx.data(), 4 * (size_t)nnz, cudaMemcpyHostToDevice,
-                            S->stream);
+                            Ln.stream);
     if (e == cudaSuccess && req->m > 0)
         e = cudaMemcpyAsync(a + L.f, req->dem.data(), 4 * (size_t)req->m, cudaMemcpyHostToDevice,
-                            S->stream);
+                            Ln.stream);
     if (e == cudaSuccess && dense)
         e = cudaMemcpyAsync(a + L.tmaps, maps, 2 * tmap_bytes(), cudaMemcpyHostToDevice,
-                            S->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(a + L.dense, 0, (size_t)L.dense_bytes, S->stream);
+                            Ln.stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(a + L.dense, 0, (size_t)L.dense_bytes, Ln.stream);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(S->dstate + si, &s, sizeof(s), cudaMemcpyHostToDevice, S->stream);
-    if (e == cudaSuccess) e = launch_build(S->dstate + si, 1, 0, nnz, req->m, req->n, S->stream);
+        e = cudaMemcpyAsync(Ln.dstate + si, &s, sizeof(s), cudaMemcpyHostToDevice, Ln.stream);
+    if (e == cudaSuccess) e = launch_build(Ln.dstate + si, 1, 0, nnz, req->m, req->n, Ln.stream);
     if (e != cudaSuccess) {
-        cudaFreeAsync(a, S->stream);
+        cudaFreeAsync(a, Ln.stream);
         return set_error(MHS_ECUDA, "server: admission failed: %s", cudaGetErrorString(e));
     }
-    Slot &sl = S->slots[si];
+    Slot &sl = Ln.slots[si];
     sl.busy = true;
     sl.req = std::move(req);
     sl.arena = a;
     sl.bytes = L.bytes;
     sl.tiles = sl.req->tiles;
     std::lock_guard<std::mutex> lk(S->mu);
-    ++S->active_count;
+    ++Ln.active_count;
     return MHS_OK;
 }
 
@@ -261,40 +277,44 @@ void fail_all_locked(mhs_server *S, mhs_status st) {
             r.t_done = t;
         }
     }
-    S->pending.clear();
+    for (auto &ln : S->lanes) {
+        ln.pending.clear();
+        ln.active_count = 0;
+    }
 }
 
 // Copy the results of the slots that finished in the last round to their
 // requests and release the slots: two synchronisations for the whole set.
-void retire(mhs_server *S, const std::vector<int> &fin) {
+void retire(Lane &Ln, const std::vector<int> &fin) {
     if (fin.empty()) return;
+    mhs_server *S = Ln.S;
     cudaError_t e = cudaSuccess;
     for (size_t i = 0; i < fin.size() && e == cudaSuccess; ++i)
-        e = cudaMemcpyAsync(S->hstates + i, S->dstate + fin[i], sizeof(InstState),
-                            cudaMemcpyDeviceToHost, S->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
+        e = cudaMemcpyAsync(Ln.hstates + i, Ln.dstate + fin[i], sizeof(InstState),
+                            cudaMemcpyDeviceToHost, Ln.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(Ln.stream);
     for (size_t i = 0; i < fin.size() && e == cudaSuccess; ++i) {
-        const InstState &s = S->hstates[i];
-        Request &r = *S->slots[fin[i]].req;
+        const InstState &s = Ln.hstates[i];
+        Request &r = *Ln.slots[fin[i]].req;
         r.vout.resize(s.n);
         r.eout.resize(s.m);
         if (s.n > 0)
             e = cudaMemcpyAsync(r.vout.data(), s.v_c2o, 4 * (size_t)s.n, cudaMemcpyDeviceToHost,
-                                S->stream);
+                                Ln.stream);
         if (e == cudaSuccess && s.m > 0)
             e = cudaMemcpyAsync(r.eout.data(), s.e_c2o, 4 * (size_t)s.m, cudaMemcpyDeviceToHost,
-                                S->stream);
+                                Ln.stream);
     }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(Ln.stream);
     InstState z;
     std::memset(&z, 0, sizeof(z));
     const int64_t t = now_ns();
     std::vector<std::shared_ptr<Request>> done;
     for (size_t i = 0; i < fin.size(); ++i) {
-        Slot &sl = S->slots[fin[i]];
+        Slot &sl = Ln.slots[fin[i]];
         Request &r = *sl.req;
         if (e == cudaSuccess) {
-            const InstState &s = S->hstates[i];
+            const InstState &s = Ln.hstates[i];
             std::sort(r.vout.begin(), r.vout.end());  // layout order -> input ids ascending
             std::sort(r.eout.begin(), r.eout.end());
             r.dout.resize(s.m);
@@ -304,11 +324,11 @@ void retire(mhs_server *S, const std::vector<int> &fin) {
         } else {
             r.status = MHS_ECUDA;
         }
-        cudaMemcpyAsync(S->dstate + fin[i], &z, sizeof(z), cudaMemcpyHostToDevice, S->stream);
-        cudaFreeAsync(sl.arena, S->stream);
+        cudaMemcpyAsync(Ln.dstate + fin[i], &z, sizeof(z), cudaMemcpyHostToDevice, Ln.stream);
+        cudaFreeAsync(sl.arena, Ln.stream);
         done.push_back(sl.req);
-        S->in_use_release += sl.bytes;
-        S->tiles_release += sl.tiles;
+        Ln.in_use_release += sl.bytes;
+        Ln.tiles_release += sl.tiles;
         sl = Slot();
     }
     {
@@ -320,56 +340,60 @@ void retire(mhs_server *S, const std::vector<int> &fin) {
             rp->vtx.clear();
             rp->dem.clear();
             ++S->completed;
-            --S->active_count;
+            --Ln.active_count;
         }
-        S->in_use -= S->in_use_release;
-        S->in_use_release = 0;
-        S->tiles_in_use -= S->tiles_release;
-        S->tiles_release = 0;
+        S->in_use -= Ln.in_use_release;
+        Ln.tiles_in_use -= Ln.tiles_release;
+        Ln.in_use_release = 0;
+        Ln.tiles_release = 0;
     }
     S->cv_done.notify_all();
+    // admission may have waited for this memory
+    for (auto &ln : S->lanes) ln.cv_work.notify_one();
 }
 
-void worker_loop(mhs_server *S) {
+void worker_loop(Lane *L) {
+    Lane &Ln = *L;
+    mhs_server *S = Ln.S;
     cudaSetDevice(S->device);
     for (;;) {
         // ---- admission at the round boundary ----
         std::vector<std::pair<int, std::shared_ptr<Request>>> to_admit;
         {
             std::unique_lock<std::mutex> lk(S->mu);
-            bool any_busy = false;
-            for (auto &sl : S->slots) any_busy |= sl.busy;
-            if (!any_busy)
-                S->cv_work.wait(lk, [&] { return S->stop || (!S->paused && !S->pending.empty()); });
+            if (Ln.active_count == 0)
+                Ln.cv_work.wait_for(lk, std::chrono::milliseconds(50), [&] {
+                    return S->stop || (!S->paused && !Ln.pending.empty());
+                });
             if (S->stop) break;
             if (!S->paused) {
                 int si = 0;
-                while (!S->pending.empty()) {
-                    auto &front = S->pending.front();
+                while (!Ln.pending.empty()) {
+                    auto &front = Ln.pending.front();
                     if (S->in_use + front->footprint > S->opt.hbm_budget_bytes) break;
-                    if (S->tiles_in_use + front->tiles > kServerListCap) break;
-                    while (si < S->slots_n && (S->slots[si].busy ||
+                    if (Ln.tiles_in_use + front->tiles > Ln.list_cap) break;
+                    while (si < Ln.slots_n && (Ln.slots[si].busy ||
                                                std::any_of(to_admit.begin(), to_admit.end(),
                                                            [si](auto &p) { return p.first == si; })))
                         ++si;
-                    if (si >= S->slots_n) break;
+                    if (si >= Ln.slots_n) break;
                     S->in_use += front->footprint;
-                    S->tiles_in_use += front->tiles;
+                    Ln.tiles_in_use += front->tiles;
                     S->peak = std::max(S->peak, S->in_use);
                     front->t_admit = now_ns();
                     to_admit.emplace_back(si, front);
-                    S->pending.pop_front();
+                    Ln.pending.pop_front();
                     ++S->admitted;
                     ++si;
                 }
             }
         }
         for (auto &p : to_admit) {
-            mhs_status st = admit(S, p.first, p.second);
+            mhs_status st = admit(Ln, p.first, p.second);
             if (st != MHS_OK) {
                 std::lock_guard<std::mutex> lk(S->mu);
                 S->in_use -= p.second->footprint;
-                S->tiles_in_use -= p.second->tiles;
+                Ln.tiles_in_use -= p.second->tiles;
                 p.second->status = st;
                 p.second->done = true;
                 p.second->t_done = now_ns();
@@ -377,55 +401,112 @@ void worker_loop(mhs_server *S) {
             }
         }
         bool any_busy = false;
-        for (auto &sl : S->slots) any_busy |= sl.busy;
+        for (auto &sl : Ln.slots) any_busy |= sl.busy;
         if (!any_busy) continue;
-        // ---- one round for every busy slot ----
-        cudaError_t e = cudaGraphLaunch(S->graph, S->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
-        if (e != cudaSuccess || *S->hkerr) {
+        // ---- one round for every busy slot of this lane ----
+        cudaError_t e = cudaGraphLaunch(Ln.graph, Ln.stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(Ln.stream);
+        if (e != cudaSuccess || *Ln.hkerr) {
             std::lock_guard<std::mutex> lk(S->mu);
             S->fatal = e != cudaSuccess ? MHS_ECUDA : MHS_EDEVICE;
             fail_all_locked(S, S->fatal);
-            S->active_count = 0;
+            S->stop = true;
             S->cv_done.notify_all();
+            for (auto &ln : S->lanes) ln.cv_work.notify_all();
             break;
         }
-        ++S->rounds;
-        const int nd = S->hctr->n_done;
+        ++Ln.rounds;
+        const int nd = Ln.hctr->n_done;
         std::vector<int> fin;
-        for (int i = 0; i < nd && i < S->slots_n; ++i) {
-            const int si = S->hdone[i];
-            if (si >= 0 && si < S->slots_n && S->slots[si].busy) fin.push_back(si);
+        for (int i = 0; i < nd && i < Ln.slots_n; ++i) {
+            const int si = Ln.hdone[i];
+            if (si >= 0 && si < Ln.slots_n && Ln.slots[si].busy) fin.push_back(si);
         }
-        retire(S, fin);
+        retire(Ln, fin);
     }
 }
 
-mhs_status capture_graph(mhs_server *S) {
+mhs_status capture_graph(Lane &Ln) {
+    mhs_server *S = Ln.S;
     cudaGraph_t g;
-    cudaError_t e = cudaStreamBeginCapture(S->stream, cudaStreamCaptureModeThreadLocal);
+    cudaError_t e = cudaStreamBeginCapture(Ln.stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return set_error(MHS_ECUDA, "server capture: %s", cudaGetErrorString(e));
-    cudaError_t e1 = launch_round_phase(S->dstate, S->dplan, S->dctr, S->slots_n, 0, S->contraction,
-                                        S->sms, S->dkerr, S->stream, nullptr, nullptr, nullptr);
+    cudaError_t e1 = launch_round_phase(Ln.dstate, Ln.dplan, Ln.dctr, Ln.slots_n, 0, S->contraction,
+                                        S->sms, Ln.dkerr, Ln.stream, nullptr, nullptr, nullptr);
     if (e1 == cudaSuccess)
-        e1 = launch_round_phase(S->dstate, S->dplan, S->dctr, S->slots_n, 1, S->contraction,
-                                S->sms, S->dkerr, S->stream, nullptr, nullptr, S->ddone);
+        e1 = launch_round_phase(Ln.dstate, Ln.dplan, Ln.dctr, Ln.slots_n, 1, S->contraction,
+                                S->sms, Ln.dkerr, Ln.stream, nullptr, nullptr, Ln.ddone);
     if (e1 == cudaSuccess)
-        e1 = cudaMemcpyAsync(S->hctr, S->dctr, sizeof(BatchCounters), cudaMemcpyDeviceToHost,
-                             S->stream);
+        e1 = cudaMemcpyAsync(Ln.hctr, Ln.dctr, sizeof(BatchCounters), cudaMemcpyDeviceToHost,
+                             Ln.stream);
     if (e1 == cudaSuccess)
-        e1 = cudaMemcpyAsync(S->hdone, S->ddone, 4 * (size_t)S->slots_n, cudaMemcpyDeviceToHost,
-                             S->stream);
+        e1 = cudaMemcpyAsync(Ln.hdone, Ln.ddone, 4 * (size_t)Ln.slots_n, cudaMemcpyDeviceToHost,
+                             Ln.stream);
     if (e1 == cudaSuccess)
-        e1 = cudaMemcpyAsync(S->hkerr, S->dkerr, 4, cudaMemcpyDeviceToHost, S->stream);
-    cudaError_t e2 = cudaStreamEndCapture(S->stream, &g);
+        e1 = cudaMemcpyAsync(Ln.hkerr, Ln.dkerr, 4, cudaMemcpyDeviceToHost, Ln.stream);
+    cudaError_t e2 = cudaStreamEndCapture(Ln.stream, &g);
     if (e1 != cudaSuccess || e2 != cudaSuccess)
         return set_error(MHS_ECUDA, "server capture failed: %s",
                          cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
-    e = cudaGraphInstantiate(&S->graph, g, 0);
+    e = cudaGraphInstantiate(&Ln.graph, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return set_error(MHS_ECUDA, "server graph: %s", cudaGetErrorString(e));
     return MHS_OK;
+}
+
+// Device and pinned memory, and the round graph, of one lane.
+mhs_status setup_lane(mhs_server *S, Lane &Ln, int id, int32_t slots, int64_t list_cap,
+                      cudaStream_t user_stream, int priority) {
+    Ln.id = id;
+    Ln.S = S;
+    Ln.slots_n = slots;
+    Ln.slots.resize(slots);
+    Ln.list_cap = list_cap;
+    if (user_stream) {
+        Ln.stream = user_stream;
+    } else {
+        if (cudaStreamCreateWithPriority(&Ln.stream, cudaStreamNonBlocking, priority) != cudaSuccess)
+            return set_error(MHS_ECUDA, "stream creation failed");
+        Ln.own_stream = true;
+    }
+    const int64_t ns = slots;
+    const int64_t o_state = 0;
+    const int64_t o_plan = up(sizeof(InstState) * ns, 256);
+    const int64_t o_row = o_plan + up(sizeof(Plan), 256);
+    const int64_t o_tile = o_row + up(4 * (ns + 1), 256);
+    const int64_t o_ctr = o_tile + up(8 * (ns + 1), 256);
+    const int64_t o_kerr = o_ctr + up(sizeof(BatchCounters), 256);
+    const int64_t o_done = o_kerr + 256;
+    const int64_t o_list = o_done + up(4 * ns, 256);
+    const int64_t total = o_list + up(8 * std::max<int64_t>(list_cap, 1), 256);
+    if (cudaMallocFromPoolAsync(reinterpret_cast<void **>(&Ln.ctl), (size_t)total, S->pool,
+                                Ln.stream) != cudaSuccess)
+        return set_error(MHS_ENOMEM, "server control allocation failed");
+    Ln.dstate = reinterpret_cast<InstState *>(Ln.ctl + o_state);
+    Ln.dplan = reinterpret_cast<Plan *>(Ln.ctl + o_plan);
+    Ln.dctr = reinterpret_cast<BatchCounters *>(Ln.ctl + o_ctr);
+    Ln.dkerr = reinterpret_cast<int32_t *>(Ln.ctl + o_kerr);
+    Ln.ddone = reinterpret_cast<int32_t *>(Ln.ctl + o_done);
+    if (cudaMallocHost(&Ln.hctr, sizeof(BatchCounters)) != cudaSuccess ||
+        cudaMallocHost(&Ln.hkerr, 4) != cudaSuccess ||
+        cudaMallocHost(&Ln.hdone, 4 * (size_t)ns) != cudaSuccess ||
+        cudaMallocHost(&Ln.hmaps, 2 * tmap_bytes() * (size_t)ns) != cudaSuccess ||
+        cudaMallocHost(&Ln.hstates, sizeof(InstState) * (size_t)ns) != cudaSuccess)
+        return set_error(MHS_ENOMEM, "pinned allocation failed");
+    *Ln.hkerr = 0;
+    Plan p;
+    std::memset(&p, 0, sizeof(p));
+    p.count = slots;
+    p.row_off = reinterpret_cast<int32_t *>(Ln.ctl + o_row);
+    p.tile_off = reinterpret_cast<int64_t *>(Ln.ctl + o_tile);
+    p.tile_list = reinterpret_cast<int64_t *>(Ln.ctl + o_list);
+    p.list_cap = (int32_t)std::min<int64_t>(list_cap, INT32_MAX);
+    cudaError_t e = cudaMemsetAsync(Ln.ctl, 0, (size_t)o_list, Ln.stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(Ln.dplan, &p, sizeof(p), cudaMemcpyHostToDevice, Ln.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(Ln.stream);
+    if (e != cudaSuccess) return set_error(MHS_ECUDA, "server setup: %s", cudaGetErrorString(e));
+    return capture_graph(Ln);
 }
 
 void destroy_server(mhs_server *S) {
@@ -434,26 +515,28 @@ void destroy_server(mhs_server *S) {
         std::lock_guard<std::mutex> lk(S->mu);
         S->stop = true;
     }
-    S->cv_work.notify_all();
-    if (S->worker.joinable()) S->worker.join();
+    for (auto &ln : S->lanes) ln.cv_work.notify_all();
+    for (auto &ln : S->lanes)
+        if (ln.worker.joinable()) ln.worker.join();
     {
         std::lock_guard<std::mutex> lk(S->mu);
         fail_all_locked(S, MHS_ECUDA);
     }
     S->cv_done.notify_all();
-    if (S->stream) cudaStreamSynchronize(S->stream);
-    for (auto &sl : S->slots)
-        if (sl.arena) cudaFreeAsync(sl.arena, S->stream);
-    if (S->graph) cudaGraphExecDestroy(S->graph);
-    if (S->ctl) cudaFreeAsync(S->ctl, S->stream);
-    if (S->stream) cudaStreamSynchronize(S->stream);
-    if (S->hctr) cudaFreeHost(S->hctr);
-    if (S->hkerr) cudaFreeHost(S->hkerr);
-    if (S->hdone) cudaFreeHost(S->hdone);
-    if (S->hmaps) cudaFreeHost(S->hmaps);
-    if (S->hstates) cudaFreeHost(S->hstates);
-    if (S->own_stream && S->stream) cudaStreamDestroy(S->stream);
-    S->cv_done.notify_all();
+    for (auto &ln : S->lanes) {
+        if (ln.stream) cudaStreamSynchronize(ln.stream);
+        for (auto &sl : ln.slots)
+            if (sl.arena) cudaFreeAsync(sl.arena, ln.stream);
+        if (ln.graph) cudaGraphExecDestroy(ln.graph);
+        if (ln.ctl) cudaFreeAsync(ln.ctl, ln.stream);
+        if (ln.stream) cudaStreamSynchronize(ln.stream);
+        if (ln.hctr) cudaFreeHost(ln.hctr);
+        if (ln.hkerr) cudaFreeHost(ln.hkerr);
+        if (ln.hdone) cudaFreeHost(ln.hdone);
+        if (ln.hmaps) cudaFreeHost(ln.hmaps);
+        if (ln.hstates) cudaFreeHost(ln.hstates);
+        if (ln.own_stream && ln.stream) cudaStreamDestroy(ln.stream);
+    }
     delete S;
 }
 
@@ -468,6 +551,7 @@ mhs_status mhs_server_default_options(mhs_server_options *opt) {
     opt->max_slots = 256;
     opt->queue_capacity = 65536;
     opt->contraction = MHS_CONTRACT_AUTO;
+    opt->small_items = 0;
     return MHS_OK;
 }
 
@@ -487,13 +571,11 @@ mhs_status mhs_server_create(const mhs_server_options *opt_in, void *cuda_stream
     if (opt.layout < 0 || opt.layout > 2) return set_error(MHS_EINVAL, "layout must be 0, 1 or 2");
     if (opt.sparsity < 0 || opt.sparsity > 2)
         return set_error(MHS_EINVAL, "sparsity must be 0, 1 or 2");
-    for (int i = 0; i < 1; ++i)
-        if (opt.reserved[i]) return set_error(MHS_EINVAL, "reserved options must be zero");
     auto *S = new mhs_server();
     S->opt = opt;
     S->contraction = opt.contraction == MHS_CONTRACT_POPCOUNT ? kPopcount : kFp8;
-    S->slots_n = opt.max_slots;
-    S->slots.resize(opt.max_slots);
+    // < 0: one lane for every request; 0: default split
+    S->small_items = opt.small_items < 0 ? INT64_MAX : (opt.small_items == 0 ? 8192 : opt.small_items);
     auto bail = [&](mhs_status st) {
         destroy_server(S);
         return st;
@@ -505,59 +587,21 @@ mhs_status mhs_server_create(const mhs_server_options *opt_in, void *cuda_stream
         cudaMemGetInfo(&fr, &tot);
         S->opt.hbm_budget_bytes = (int64_t)(fr / 4 * 3);
     }
-    if (cuda_stream) {
-        S->stream = static_cast<cudaStream_t>(cuda_stream);
-    } else {
-        if (cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking) != cudaSuccess)
-            return bail(set_error(MHS_ECUDA, "stream creation failed"));
-        S->own_stream = true;
-    }
     if (pool_for(S->device, &S->pool) != cudaSuccess)
         return bail(set_error(MHS_ECUDA, "memory pool unavailable"));
     if (S->contraction == kFp8 && prepare_tc_contract() != cudaSuccess)
         return bail(set_error(MHS_ECUDA, "tcgen05 kernel setup failed"));
-    // slot table, plan, counters and done list in one allocation
-    const int64_t ns = S->slots_n;
-    const int64_t o_state = 0;
-    const int64_t o_plan = up(sizeof(InstState) * ns, 256);
-    const int64_t o_row = o_plan + up(sizeof(Plan), 256);
-    const int64_t o_tile = o_row + up(4 * (ns + 1), 256);
-    const int64_t o_ctr = o_tile + up(8 * (ns + 1), 256);
-    const int64_t o_kerr = o_ctr + up(sizeof(BatchCounters), 256);
-    const int64_t o_done = o_kerr + 256;
-    const int64_t o_list = o_done + up(4 * ns, 256);
-    const int64_t list_cap = S->contraction == kFp8 ? kServerListCap : 1;
-    const int64_t total = o_list + up(8 * list_cap, 256);
-    if (cudaMallocFromPoolAsync(reinterpret_cast<void **>(&S->ctl), (size_t)total, S->pool,
-                                S->stream) != cudaSuccess)
-        return bail(set_error(MHS_ENOMEM, "server control allocation failed"));
-    S->dstate = reinterpret_cast<InstState *>(S->ctl + o_state);
-    S->dplan = reinterpret_cast<Plan *>(S->ctl + o_plan);
-    S->dctr = reinterpret_cast<BatchCounters *>(S->ctl + o_ctr);
-    S->dkerr = reinterpret_cast<int32_t *>(S->ctl + o_kerr);
-    S->ddone = reinterpret_cast<int32_t *>(S->ctl + o_done);
-    if (cudaMallocHost(&S->hctr, sizeof(BatchCounters)) != cudaSuccess ||
-        cudaMallocHost(&S->hkerr, 4) != cudaSuccess ||
-        cudaMallocHost(&S->hdone, 4 * (size_t)ns) != cudaSuccess ||
-        cudaMallocHost(&S->hmaps, 2 * tmap_bytes() * (size_t)ns) != cudaSuccess ||
-        cudaMallocHost(&S->hstates, sizeof(InstState) * (size_t)ns) != cudaSuccess)
-        return bail(set_error(MHS_ENOMEM, "pinned allocation failed"));
-    *S->hkerr = 0;
-    Plan p;
-    std::memset(&p, 0, sizeof(p));
-    p.count = S->slots_n;
-    p.row_off = reinterpret_cast<int32_t *>(S->ctl + o_row);
-    p.tile_off = reinterpret_cast<int64_t *>(S->ctl + o_tile);
-    p.tile_list = reinterpret_cast<int64_t *>(S->ctl + o_list);
-    p.list_cap = (int32_t)list_cap;
-    cudaError_t e = cudaMemsetAsync(S->ctl, 0, (size_t)o_list, S->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(S->dplan, &p, sizeof(p), cudaMemcpyHostToDevice, S->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
-    if (e != cudaSuccess) return bail(set_error(MHS_ECUDA, "server setup: %s", cudaGetErrorString(e)));
-    mhs_status st = capture_graph(S);
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);  // hi is the most urgent
+    const bool dense = S->contraction == kFp8;
+    // lane 0: small requests, many slots, high priority; lane 1: large ones, a few at a time
+    mhs_status st = setup_lane(S, S->lanes[0], 0, opt.max_slots, dense ? kServerListCap : 1,
+                               nullptr, hi);
     if (st) return bail(st);
-    S->worker = std::thread(worker_loop, S);
+    st = setup_lane(S, S->lanes[1], 1, std::min(opt.max_slots, 4), dense ? kServerListCap : 1,
+                    static_cast<cudaStream_t>(cuda_stream), lo);
+    if (st) return bail(st);
+    for (auto &ln : S->lanes) ln.worker = std::thread(worker_loop, &ln);
     *out = S;
     return MHS_OK;
 }
@@ -594,26 +638,29 @@ mhs_status mhs_submit(mhs_server *S, int32_t n, int32_t m, const int32_t *edge_p
     r->vtx.assign(edge_vtx, edge_vtx + nnz);
     r->dem.assign(demand, demand + m);
     r->footprint = plan_layout(n, m, nnz, S->contraction == kFp8).bytes;
-    r->tiles = std::max(tc_tiles(m), tc_tiles(n));
+    // tile-list entries only matter for the tcgen05 contraction
+    r->tiles = S->contraction == kFp8 ? std::max(tc_tiles(m), tc_tiles(n)) : 0;
     if (S->contraction == kFp8 && r->tiles > kServerListCap)
         return set_error(MHS_ENOMEM, "instance needs %lld tiles, over the server's %lld",
                          (long long)r->tiles, (long long)kServerListCap);
     if (r->footprint > S->opt.hbm_budget_bytes)
         return set_error(MHS_ENOMEM, "instance needs %lld bytes, over the server budget %lld",
                          (long long)r->footprint, (long long)S->opt.hbm_budget_bytes);
+    Lane &ln = S->lanes[(int64_t)n + m <= S->small_items ? 0 : 1];
     {
         std::lock_guard<std::mutex> lk(S->mu);
         if (S->fatal) return set_error(S->fatal, "server stopped after a device error");
-        if ((int64_t)S->pending.size() >= S->opt.queue_capacity)
+        const int64_t queued = (int64_t)S->lanes[0].pending.size() + S->lanes[1].pending.size();
+        if (queued >= S->opt.queue_capacity)
             return set_error(MHS_EBUSY, "request queue full (%d)", S->opt.queue_capacity);
         r->ticket = S->next_ticket++;
         r->t_submit = now_ns();
-        S->pending.push_back(r);
+        ln.pending.push_back(r);
         S->table[r->ticket] = r;
         ++S->submitted;
         *ticket = r->ticket;
     }
-    S->cv_work.notify_one();
+    ln.cv_work.notify_one();
     return MHS_OK;
 }
 
@@ -664,7 +711,7 @@ mhs_status mhs_server_pause(mhs_server *S, int32_t paused) {
         std::lock_guard<std::mutex> lk(S->mu);
         S->paused = paused != 0;
     }
-    S->cv_work.notify_all();
+    for (auto &ln : S->lanes) ln.cv_work.notify_all();
     return MHS_OK;
 }
 
@@ -675,9 +722,9 @@ mhs_status mhs_server_get_stats(mhs_server *S, mhs_server_stats *out) {
     out->submitted = S->submitted;
     out->admitted = S->admitted;
     out->completed = S->completed;
-    out->rounds = S->rounds;
-    out->pending = (int32_t)S->pending.size();
-    out->active = S->active_count;
+    out->rounds = S->lanes[0].rounds + S->lanes[1].rounds;
+    out->pending = (int32_t)(S->lanes[0].pending.size() + S->lanes[1].pending.size());
+    out->active = S->lanes[0].active_count + S->lanes[1].active_count;
     out->bytes_in_use = S->in_use;
     out->peak_bytes = S->peak;
     out->budget_bytes = S->opt.hbm_budget_bytes;

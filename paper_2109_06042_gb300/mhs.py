@@ -55,7 +55,7 @@ class ServerOptions(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("max_slots", ctypes.c_int32),
                 ("queue_capacity", ctypes.c_int32), ("contraction", ctypes.c_int32),
                 ("layout", ctypes.c_int32), ("sparsity", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 1)]
+                ("small_items", ctypes.c_int32)]
 
 
 class ServerStats(ctypes.Structure):
@@ -375,7 +375,7 @@ class Server:
     """Continuous-batching server (mhs_server_*): submit host instances, poll results."""
 
     def __init__(self, hbm_budget_bytes=0, max_slots=256, queue_capacity=65536,
-                 contraction="auto", stream=None, layout=None, sparsity=None):
+                 contraction="auto", stream=None, layout=None, sparsity=None, small_items=0):
         o = ServerOptions()
         _check(lib().mhs_server_default_options(ctypes.byref(o)))
         o.hbm_budget_bytes = int(hbm_budget_bytes)
@@ -386,6 +386,7 @@ class Server:
         o.layout = LAYOUTS[lay] if isinstance(lay, str) else int(lay)
         sp = _DEFAULT_SPARSITY[0] if sparsity is None else sparsity
         o.sparsity = SPARSITY[sp] if isinstance(sp, str) else int(sp)
+        o.small_items = int(small_items)
         h = ctypes.c_void_p()
         _check(lib().mhs_server_create(ctypes.byref(o), _stream_ptr(stream), ctypes.byref(h)))
         self._h = h

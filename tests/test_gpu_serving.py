@@ -5,6 +5,8 @@ instance reduced alone (bit-exact), whatever else is in flight; admission
 respects the HBM budget; queue limits, early polls, oversize requests and
 shutdown with work pending behave as the C ABI documents.
 """
+import time
+
 import numpy as np
 import pytest
 
@@ -31,18 +33,33 @@ def _mix():
     return insts
 
 
+def _poll_all(srv, tickets, seconds=120.0):
+    """Poll every ticket against one overall deadline (fails instead of stalling)."""
+    deadline = time.monotonic() + seconds
+    out = []
+    for t in tickets:
+        left = max(0.0, deadline - time.monotonic())
+        r = srv.poll(t, timeout_us=int(left * 1e6))
+        assert r is not None, f"ticket {t} not finished within {seconds} s"
+        out.append(r)
+    return out
+
+
 def _same(a, b, ctx):
     for key in ("vertices", "edges", "demands"):
         assert a[key].tolist() == b[key].tolist(), (key, ctx)
     assert a["k"] == b["k"] and a["rounds"] == b["rounds"], ctx
 
 
-@pytest.mark.parametrize("mode", ["fp8", "popcount"])
-def test_served_equals_alone_and_oracle(mhs, mode):
+@pytest.mark.parametrize("mode,small_items", [("fp8", 0), ("popcount", 0), ("fp8", -1),
+                                              ("fp8", 1)])
+def test_served_equals_alone_and_oracle(mhs, mode, small_items):
+    """Both lanes (default split), a single lane (-1), and everything in the
+    large-request lane (1)."""
     insts = _mix()
-    with mhs.Server(max_slots=16, contraction=mode) as srv:
+    with mhs.Server(max_slots=16, contraction=mode, small_items=small_items) as srv:
         tickets = [srv.submit(i) for i in insts]
-        results = [srv.poll(t, timeout_us=60_000_000) for t in tickets]
+        results = _poll_all(srv, tickets)
         st = srv.stats()
     assert st["completed"] == len(insts) and st["pending"] == 0 and st["active"] == 0
     for idx, (inst, res) in enumerate(zip(insts, results)):
@@ -60,7 +77,7 @@ def test_admission_by_footprint(mhs):
     budget = 2 * (3 * big + 16 * (max(i.m for i in insts) + max(i.n for i in insts)) + (1 << 20))
     with mhs.Server(hbm_budget_bytes=budget, max_slots=64) as srv:
         tickets = [srv.submit(i) for i in insts]
-        results = [srv.poll(t, timeout_us=60_000_000) for t in tickets]
+        results = _poll_all(srv, tickets)
         st = srv.stats()
     assert st["peak_bytes"] <= budget
     for inst, res in zip(insts, results):
@@ -79,8 +96,8 @@ def test_queue_full_and_early_poll(mhs):
         assert srv.poll(tickets[0], timeout_us=20_000) is None      # paused: still waiting
         assert srv.stats()["pending"] == 3
         srv.pause(False)
-        for t, inst in zip(tickets, insts):
-            _same(srv.poll(t, timeout_us=60_000_000), O.reduce(inst), inst.name)
+        for r, inst in zip(_poll_all(srv, tickets), insts):
+            _same(r, O.reduce(inst), inst.name)
         with pytest.raises(mhs.MhsError):
             srv.poll(tickets[0])                                     # already consumed
 
@@ -90,7 +107,7 @@ def test_oversize_request_rejected(mhs):
         with pytest.raises(mhs.MhsError) as ei:
             srv.submit(I.config_powerlaw(0, n=3000, m=6000))
         assert ei.value.status == mhs.MHS_ENOMEM
-        res = srv.poll(srv.submit(I.config_uniform(0, n=40, m=60)), timeout_us=60_000_000)
+        res = _poll_all(srv, [srv.submit(I.config_uniform(0, n=40, m=60))])[0]
         _same(res, O.reduce(I.config_uniform(0, n=40, m=60)), "small fits")
 
 
