@@ -390,9 +390,10 @@ def run_ours(args, rank, world, dist):
                 "kernel": "k_pop_contract", "peak_source": "derived: 16 POPC/clk/SM nominal",
                 "launches_per_step": 2 * rounds, "avg_launch_ms": round(per_launch, 4)}
 
-    cpu = None
+    cpu = seq = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(insts, desc, args.cpu_seconds)
+        seq = cpu_sequential(insts, desc, args.cpu_seconds)
 
     # load kernels incl. the result-mask kernel, plus per round: 10 + the loop-condition kernel
     load_kernels = 5 if batch else 3
@@ -411,6 +412,7 @@ def run_ours(args, rank, world, dist):
         "pair_tests_per_s": round(world * pairs * args.steps / (ms / 1e3), 1),
         "roofline": roof,
         "cpu_baseline": cpu,
+        "cpu_sequential": seq,
         "e2e": e2e,
         "gpu_launches": args.steps * (load_kernels + 11 * rounds),
         "clocks": clk,
@@ -528,6 +530,32 @@ def cpu_baseline(insts, desc, seconds):
               f"single-threaded C oracle with exact pair pruning, {dt:.2f} s")
     return {"value": round(done / dt, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": sample}
+
+
+def cpu_sequential(insts, desc, seconds):
+    """The paper's sequential design (Section 4.2, Algorithms 4-6) with
+    OpenMP on every host core, on a bounded sample of the workload."""
+    from oracle import kernelcpu as KC
+    KC.build()
+    cores = os.cpu_count() or 1
+    sized = [i for i in insts if KC.matrix_bytes(i.n, i.m) <= KC.DEFAULT_MAX_BYTES]
+    if not sized:
+        return {"value": None, "unit": UNIT, "cores": cores,
+                "kind": "paper sequential algorithm (Algorithms 4-6)",
+                "sample": f"not run: dense count matrices of {desc} exceed "
+                          f"{KC.DEFAULT_MAX_BYTES >> 30} GiB"}
+    done = 0
+    t0 = time.perf_counter()
+    for i in sized:
+        KC.reduce(i, threads=cores)
+        done += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": round(done / dt, 6), "unit": UNIT, "cores": cores,
+            "kind": "paper sequential algorithm (Algorithms 4-6)",
+            "sample": f"{done} of {len(insts)} instance(s) of the workload ({desc}), "
+                      f"dense I^E/I^V count matrices, OpenMP over {cores} threads, {dt:.2f} s"}
 
 
 def run_reference(args, rank, world):
