@@ -37,6 +37,20 @@
  *   MD: a dominator of v_j (E(v_j) non-empty) lies in every hyperedge of
  *       E(v_j), in particular in the first one.
  * prune == 0 scans all pairs; the tests check that both agree.
+ *
+ * Two further rules of Section 3.1, for the variants of the experiments:
+ *   SE (superedge rule): e_j goes if some distinct e_i is a subset of e_j
+ *       with f(e_i) >= f(e_j).  The "MD+SE" variant runs Algorithm 3 with
+ *       this test in place of "e_i supersedes e_j" (same simultaneous
+ *       deletions and lowest-index tie-break).  The pruning above stays
+ *       exact: a non-empty e_i inside e_j meets e_j, and an empty e_i has
+ *       f(e_i) > |e_i|.
+ *   FE (full-edge rule): while some alive e_j has |e_j| = f(e_j), take the
+ *       lowest such j, delete e_j and each alive v in e_j (v goes into the
+ *       solution, k drops by one), lower f of every other alive hyperedge
+ *       holding v by one and delete those whose demand reaches 0.
+ *   KernelGPU-FE (Section 5.1): alternate Algorithm 3 to its fixpoint and
+ *       exhaustive FE until FE changes nothing.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -46,7 +60,10 @@ typedef struct {
     int32_t n, m;
     const int32_t *eptr, *evtx, *f;
     int32_t *vptr, *vedg; /* vertex -> hyperedges, ascending */
+    int32_t rule;         /* 0: DP (supersedes), 1: SE (subset, f_i >= f_j) */
 } hyper_t;
+
+enum { RULE_DP = 0, RULE_SE = 1 };
 
 static int build_incidence(hyper_t *h) {
     int32_t n = h->n, m = h->m;
@@ -87,8 +104,18 @@ static int32_t diff_size(const hyper_t *h, const uint8_t *alive_v, int32_t i, in
     return d;
 }
 
-/* e_i supersedes e_j (Definition in Section 3.1). */
+/* e_i supersedes e_j (Definition in Section 3.1); under rule SE: e_i is a
+   subset of e_j and f(e_i) >= f(e_j) (rule SE, Section 3.1). */
 static int supersedes(const hyper_t *h, const uint8_t *alive_v, int32_t i, int32_t j) {
+    if (h->rule == RULE_SE) {
+#ifdef ORACLE_MUTANT_SE_IGNORE_DEMAND
+        return diff_size(h, alive_v, i, j) == 0;
+#elif defined(ORACLE_MUTANT_SE_DEMAND_REVERSED)
+        return diff_size(h, alive_v, i, j) == 0 && h->f[i] <= h->f[j];
+#else
+        return diff_size(h, alive_v, i, j) == 0 && h->f[i] >= h->f[j];
+#endif
+    }
 #ifdef ORACLE_MUTANT_DP_TRANSPOSED
     return h->f[i] - diff_size(h, alive_v, j, i) >= h->f[j];
 #elif defined(ORACLE_MUTANT_DP_DROP_FI)
@@ -267,14 +294,14 @@ static int32_t md_pass(const hyper_t *h, const uint8_t *alive_v, const uint8_t *
  * (at most trace_cap rounds are recorded).  Returns 0, or -1 on allocation
  * failure.
  */
-int mhs_oracle_reduce(int32_t n, int32_t m, const int32_t *edge_ptr, const int32_t *edge_vtx,
-                      const int32_t *demand, int32_t max_rounds, int32_t prune,
-                      uint8_t *alive_v, uint8_t *alive_e, int32_t *rounds_out,
-                      int32_t *changed_out, int32_t *trace, int32_t trace_cap) {
-    hyper_t h = {n, m, edge_ptr, edge_vtx, demand, NULL, NULL};
-    if (build_incidence(&h)) return -1;
+static int algorithm3(hyper_t *hp, int32_t max_rounds, int32_t prune, uint8_t *alive_v,
+                      uint8_t *alive_e, int32_t *rounds_out, int32_t *changed_out,
+                      int32_t *trace, int32_t trace_cap) {
+    hyper_t h = *hp;
+    const int32_t n = h.n, m = h.m;
     uint8_t *del_e = (uint8_t *)malloc((size_t)(m > 0 ? m : 1));
     uint8_t *del_v = (uint8_t *)malloc((size_t)(n > 0 ? n : 1));
+    if (!del_e || !del_v) { free(del_e); free(del_v); return -1; }
     int32_t rounds = 0, changed = 0;
     int32_t alive_m = 0, alive_n = 0;
     for (int32_t e = 0; e < m; ++e) alive_m += alive_e[e] != 0;
@@ -308,15 +335,111 @@ int mhs_oracle_reduce(int32_t n, int32_t m, const int32_t *edge_ptr, const int32
     *changed_out = changed;
     free(del_e);
     free(del_v);
-    free_incidence(&h);
     return 0;
+}
+
+int mhs_oracle_reduce(int32_t n, int32_t m, const int32_t *edge_ptr, const int32_t *edge_vtx,
+                      const int32_t *demand, int32_t max_rounds, int32_t prune,
+                      uint8_t *alive_v, uint8_t *alive_e, int32_t *rounds_out,
+                      int32_t *changed_out, int32_t *trace, int32_t trace_cap) {
+    hyper_t h = {n, m, edge_ptr, edge_vtx, demand, NULL, NULL, RULE_DP};
+    if (build_incidence(&h)) return -1;
+    int rc = algorithm3(&h, max_rounds, prune, alive_v, alive_e, rounds_out, changed_out, trace,
+                        trace_cap);
+    free_incidence(&h);
+    return rc;
+}
+
+/*
+ * Exhaustive FE (rule FE, Section 3.1), one full hyperedge at a time in
+ * increasing index order, on the state (alive_v, alive_e, f).  f is the
+ * current demand per hyperedge (updated), forced[v] is set for every vertex
+ * the rule puts into the solution, *k is lowered by their number.  Returns
+ * the number of hyperedges and vertices deleted.
+ */
+static int32_t fe_exhaustive(const hyper_t *h, uint8_t *alive_v, uint8_t *alive_e, int32_t *f,
+                             uint8_t *forced, int64_t *k) {
+    int32_t deleted = 0;
+    for (;;) {
+        int32_t j = -1;
+        for (int32_t e = 0; e < h->m && j < 0; ++e)
+            if (alive_e[e] && alive_size(h, alive_v, e) == f[e]) j = e;
+        if (j < 0) return deleted;
+        alive_e[j] = 0;
+        ++deleted;
+        for (int32_t p = h->eptr[j]; p < h->eptr[j + 1]; ++p) {
+            const int32_t v = h->evtx[p];
+            if (!alive_v[v]) continue;
+            alive_v[v] = 0;
+            forced[v] = 1;
+#ifndef ORACLE_MUTANT_FE_K_UNCHANGED
+            *k -= 1;
+#endif
+            ++deleted;
+            for (int32_t q = h->vptr[v]; q < h->vptr[v + 1]; ++q) {
+                const int32_t i = h->vedg[q];
+                if (!alive_e[i]) continue;
+#ifndef ORACLE_MUTANT_FE_SKIP_DECREMENT
+                f[i] -= 1;
+#endif
+#ifndef ORACLE_MUTANT_FE_KEEP_ZERO_DEMAND
+                if (f[i] == 0) { alive_e[i] = 0; ++deleted; }
+#endif
+            }
+        }
+    }
+}
+
+/*
+ * The reduction variants of the experiments (Section 5.1), from the input
+ * state (everything alive):
+ *   rule 0 / 1: Algorithm 3 with DP or SE as the hyperedge pass;
+ *   full_edges != 0: alternate that to its fixpoint with exhaustive FE
+ *   until FE changes nothing (KernelGPU-FE).
+ * Outputs: alive masks, current demands f_out[m] (input demands unless FE
+ * lowered them), forced_v[n] (vertices FE put into the solution), *k_out,
+ * *rounds_out (Algorithm 3 rounds over all alternations, each run counting
+ * its final round that changes nothing), *fe_passes_out (FE applications,
+ * counting the last one that changes nothing; 0 without FE).  max_rounds
+ * bounds Algorithm 3 when full_edges == 0 and is ignored otherwise.
+ */
+int mhs_oracle_reduce_ext(int32_t n, int32_t m, const int32_t *edge_ptr, const int32_t *edge_vtx,
+                          const int32_t *demand, int64_t k, int32_t rule, int32_t full_edges,
+                          int32_t max_rounds, int32_t prune, uint8_t *alive_v, uint8_t *alive_e,
+                          int32_t *f_out, uint8_t *forced_v, int64_t *k_out,
+                          int32_t *rounds_out, int32_t *fe_passes_out, int32_t *changed_out) {
+    for (int32_t e = 0; e < m; ++e) f_out[e] = demand[e];
+    for (int32_t v = 0; v < n; ++v) forced_v[v] = 0;
+    hyper_t h = {n, m, edge_ptr, edge_vtx, f_out, NULL, NULL, rule};
+    if (build_incidence(&h)) return -1;
+    int32_t rounds = 0, passes = 0, changed = 0;
+    int rc = 0;
+    for (;;) {
+        int32_t r = 0;
+        rc = algorithm3(&h, full_edges ? 0 : max_rounds, prune, alive_v, alive_e, &r, &changed,
+                        NULL, 0);
+        rounds += r;
+        if (rc || !full_edges) break;
+        ++passes;
+        if (fe_exhaustive(&h, alive_v, alive_e, f_out, forced_v, &k) == 0) break;
+#ifdef ORACLE_MUTANT_FE_NO_ALTERNATION
+        ++passes;
+        break;
+#endif
+    }
+    *k_out = k;
+    *rounds_out = rounds;
+    *fe_passes_out = passes;
+    *changed_out = changed;
+    free_incidence(&h);
+    return rc;
 }
 
 /* One Algorithm 1 pass: del_e[j] = 1 for deleted hyperedges. Returns count or -1. */
 int mhs_oracle_dp_pass(int32_t n, int32_t m, const int32_t *edge_ptr, const int32_t *edge_vtx,
                        const int32_t *demand, int32_t prune, const uint8_t *alive_v,
                        const uint8_t *alive_e, uint8_t *del_e) {
-    hyper_t h = {n, m, edge_ptr, edge_vtx, demand, NULL, NULL};
+    hyper_t h = {n, m, edge_ptr, edge_vtx, demand, NULL, NULL, RULE_DP};
     if (build_incidence(&h)) return -1;
     int32_t c = dp_pass(&h, alive_v, alive_e, prune, del_e);
     free_incidence(&h);
@@ -327,7 +450,7 @@ int mhs_oracle_dp_pass(int32_t n, int32_t m, const int32_t *edge_ptr, const int3
 int mhs_oracle_md_pass(int32_t n, int32_t m, const int32_t *edge_ptr, const int32_t *edge_vtx,
                        const int32_t *demand, int32_t prune, const uint8_t *alive_v,
                        const uint8_t *alive_e, uint8_t *del_v, int32_t *cnt, int32_t *maxf) {
-    hyper_t h = {n, m, edge_ptr, edge_vtx, demand, NULL, NULL};
+    hyper_t h = {n, m, edge_ptr, edge_vtx, demand, NULL, NULL, RULE_DP};
     if (build_incidence(&h)) return -1;
     int32_t c = md_pass(&h, alive_v, alive_e, prune, del_v, cnt, maxf);
     free_incidence(&h);
@@ -337,13 +460,13 @@ int mhs_oracle_md_pass(int32_t n, int32_t m, const int32_t *edge_ptr, const int3
 /* Pairwise relations on a state, for invariant tests. */
 int mhs_oracle_supersedes(int32_t n, int32_t m, const int32_t *edge_ptr, const int32_t *edge_vtx,
                           const int32_t *demand, const uint8_t *alive_v, int32_t i, int32_t j) {
-    hyper_t h = {n, m, edge_ptr, edge_vtx, demand, NULL, NULL};
+    hyper_t h = {n, m, edge_ptr, edge_vtx, demand, NULL, NULL, RULE_DP};
     return supersedes(&h, alive_v, i, j);
 }
 
 int mhs_oracle_dominates(int32_t n, int32_t m, const int32_t *edge_ptr, const int32_t *edge_vtx,
                          const uint8_t *alive_e, int32_t i, int32_t j) {
-    hyper_t h = {n, m, edge_ptr, edge_vtx, NULL, NULL, NULL};
+    hyper_t h = {n, m, edge_ptr, edge_vtx, NULL, NULL, NULL, RULE_DP};
     if (build_incidence(&h)) return -1;
     int r = dominates(&h, alive_e, i, j);
     free_incidence(&h);

@@ -35,6 +35,12 @@ MUTANTS = (
     "MD_STRICT_GT",
     "MD_KEEP_ISOLATED",
     "SEQUENTIAL_MD_BEFORE_DP",
+    "SE_IGNORE_DEMAND",
+    "SE_DEMAND_REVERSED",
+    "FE_K_UNCHANGED",
+    "FE_SKIP_DECREMENT",
+    "FE_KEEP_ZERO_DEMAND",
+    "FE_NO_ALTERNATION",
 )
 
 
@@ -73,6 +79,10 @@ def _load(mutant: str | None = None):
     lib.mhs_oracle_dp_pass.restype = ctypes.c_int
     lib.mhs_oracle_md_pass.argtypes = [i32, i32, i32p, i32p, i32p, i32, u8p, u8p, u8p, i32p, i32p]
     lib.mhs_oracle_md_pass.restype = ctypes.c_int
+    i64, i64p = ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)
+    lib.mhs_oracle_reduce_ext.argtypes = [i32, i32, i32p, i32p, i32p, i64, i32, i32, i32, i32,
+                                          u8p, u8p, i32p, u8p, i64p, i32p, i32p, i32p]
+    lib.mhs_oracle_reduce_ext.restype = ctypes.c_int
     lib.mhs_oracle_supersedes.argtypes = [i32, i32, i32p, i32p, i32p, u8p, i32, i32]
     lib.mhs_oracle_supersedes.restype = ctypes.c_int
     lib.mhs_oracle_dominates.argtypes = [i32, i32, i32p, i32p, u8p, i32, i32]
@@ -154,6 +164,48 @@ def reduce(inst, prune: bool = True, max_rounds: int = 0, mutant: str | None = N
         "k": int(inst.k),
         "rounds": rounds,
         "changed": changed,
+    }
+
+
+RULES = {"dp": 0, "se": 1}
+
+
+def reduce_variant(inst, rule: str = "dp", full_edges: bool = False, prune: bool = True,
+                   max_rounds: int = 0, mutant: str | None = None) -> dict:
+    """The reduction variants of the experiments (Section 5.1): Algorithm 3
+    with DP ("dp") or the superedge rule SE ("se") as its hyperedge pass,
+    and with ``full_edges`` alternated with exhaustive FE (KernelGPU-FE).
+
+    Returns the dict of ``reduce`` with the CURRENT demands of the surviving
+    hyperedges (FE lowers them), the current k, ``forced`` (input ids of the
+    vertices FE put into the solution, ascending) and ``fe_passes``.
+    """
+    lib = _load(mutant)
+    arr = _Arrays(inst)
+    av = _alive(arr.n, None)
+    ae = _alive(arr.m, None)
+    fo = np.zeros(max(arr.m, 1), dtype=np.int32)
+    forced = np.zeros(max(arr.n, 1), dtype=np.uint8)
+    k_out = ctypes.c_int64(0)
+    rounds, passes, changed = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
+    rc = lib.mhs_oracle_reduce_ext(*arr.args(), int(inst.k), RULES[rule], int(bool(full_edges)),
+                                   int(max_rounds), int(bool(prune)), _p(av, ctypes.c_uint8),
+                                   _p(ae, ctypes.c_uint8), _p(fo, ctypes.c_int32),
+                                   _p(forced, ctypes.c_uint8), ctypes.byref(k_out),
+                                   ctypes.byref(rounds), ctypes.byref(passes),
+                                   ctypes.byref(changed))
+    if rc != 0:
+        raise MemoryError("oracle allocation failed")
+    edges = np.nonzero(ae[:arr.m])[0].astype(np.int32)
+    return {
+        "vertices": np.nonzero(av[:arr.n])[0].astype(np.int32),
+        "edges": edges,
+        "demands": fo[:arr.m][edges].astype(np.int32),
+        "k": int(k_out.value),
+        "rounds": int(rounds.value),
+        "fe_passes": int(passes.value),
+        "forced": np.nonzero(forced[:arr.n])[0].astype(np.int32),
+        "changed": bool(changed.value),
     }
 
 

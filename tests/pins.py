@@ -13,6 +13,9 @@ set tests:
   items resolved to the lowest index (the tie-breaks of Algorithms 1 and 2).
 * ``min_mhs_size``      brute force over all vertex subsets of the ILP model
   of Eq. (7) (Section 5.1), for n <= 16.
+* ``matrix_kernelize_fe``  the same with rule FE applied to all full
+  hyperedges at once between fixpoints (KernelGPU-FE, Section 5.1),
+  where the oracle applies FE one hyperedge at a time as the rule states.
 * ``matching_number``   the matching number of the incidence graph, which
   bounds the rounds by nu + 1 (proof of the parallel kernelization theorem,
   Section 4.1).
@@ -32,16 +35,17 @@ def dense_incidence(inst) -> np.ndarray:
     return A
 
 
-def matrix_kernelize(inst, max_rounds: int = 0):
-    """Algorithm 3 with Algorithms 1 and 2 in their matrix form.
+def matrix_rounds(A, f, alive_v, alive_e, max_rounds: int = 0, rule: str = "dp"):
+    """Algorithm 3 with Algorithms 1 and 2 in their matrix form, from the
+    state (alive_v, alive_e) with demands f; updates the masks in place.
 
-    Returns (alive_v, alive_e, rounds, trace) with trace rows
+    rule "dp": D_ij = [f_i - (I^E_ii - I^E_ij) >= f_j] (Algorithm 1);
+    rule "se": D_ij = [I^E_ij = I^E_ii and f_i >= f_j] (rule SE: e_i is a
+    subset of e_j exactly when their intersection is all of e_i).
+    Returns (rounds, trace) with trace rows
     [edges deleted by DP, vertices deleted by MD, alive edges, alive vertices].
     """
-    A = dense_incidence(inst)
-    f = np.asarray(inst.demand, dtype=np.int64)
-    alive_e = np.ones(inst.m, dtype=bool)
-    alive_v = np.ones(inst.n, dtype=bool)
+    f = np.asarray(f, dtype=np.int64)
     trace = []
     rounds = 0
     while True:
@@ -52,7 +56,10 @@ def matrix_kernelize(inst, max_rounds: int = 0):
         IE = Ac @ Ac.T                                   # Eq. (1)
         s = np.diag(IE)
         fe = f[E]
-        D = (fe[:, None] - (s[:, None] - IE)) >= fe[None, :]   # D_ij
+        if rule == "se":
+            D = (IE == s[:, None]) & (fe[:, None] >= fe[None, :])
+        else:
+            D = (fe[:, None] - (s[:, None] - IE)) >= fe[None, :]   # D_ij
         np.fill_diagonal(D, False)
         idx = np.arange(E.size)
         i_lt_j = idx[:, None] < idx[None, :]
@@ -79,7 +86,62 @@ def matrix_kernelize(inst, max_rounds: int = 0):
         trace.append([de, dv, int(alive_e.sum()), int(alive_v.sum())])
         if de + dv == 0 or (max_rounds > 0 and rounds >= max_rounds):
             break
-    return alive_v, alive_e, rounds, np.array(trace, dtype=np.int64)
+    return rounds, np.array(trace, dtype=np.int64)
+
+
+def matrix_kernelize(inst, max_rounds: int = 0, rule: str = "dp"):
+    """Algorithm 3 with Algorithms 1 and 2 in their matrix form.
+
+    Returns (alive_v, alive_e, rounds, trace) with trace rows
+    [edges deleted by DP, vertices deleted by MD, alive edges, alive vertices].
+    """
+    A = dense_incidence(inst)
+    alive_e = np.ones(inst.m, dtype=bool)
+    alive_v = np.ones(inst.n, dtype=bool)
+    rounds, trace = matrix_rounds(A, inst.demand, alive_v, alive_e, max_rounds, rule)
+    return alive_v, alive_e, rounds, trace
+
+
+def full_edges_at_once(A, f, alive_v, alive_e):
+    """Exhaustive FE (Section 3.1) as ONE simultaneous step: S = all alive
+    vertices of all full hyperedges (|e| = f(e)); every other alive
+    hyperedge loses |e & S| demand and goes at demand <= 0.  Updates f and
+    the masks in place; returns the bool mask S."""
+    Ac = A * alive_v[None, :]
+    size = Ac.sum(axis=1)
+    full = alive_e & (size == f)
+    S = alive_v & (Ac[full].sum(axis=0) > 0)
+    lost = Ac[:, S].sum(axis=1)
+    rest = alive_e & ~full
+    f[rest] -= lost[rest]
+    alive_e[full] = False
+    alive_e[rest & (f <= 0)] = False
+    alive_v[S] = False
+    return S
+
+
+def matrix_kernelize_fe(inst, rule: str = "dp"):
+    """KernelGPU-FE (Section 5.1): Algorithm 3 in matrix form to its fixpoint,
+    then FE at once, until FE finds no full hyperedge.  Returns a dict like
+    the oracle's reduce_variant."""
+    A = dense_incidence(inst)
+    f = np.asarray(inst.demand, dtype=np.int64).copy()
+    alive_e = np.ones(inst.m, dtype=bool)
+    alive_v = np.ones(inst.n, dtype=bool)
+    forced = np.zeros(inst.n, dtype=bool)
+    rounds = passes = 0
+    while True:
+        r, _ = matrix_rounds(A, f, alive_v, alive_e, 0, rule)
+        rounds += r
+        passes += 1
+        S = full_edges_at_once(A, f, alive_v, alive_e)
+        if not S.any():  # f >= 1, so a full hyperedge has a vertex
+            break
+        forced |= S
+    E = np.nonzero(alive_e)[0]
+    return {"vertices": np.nonzero(alive_v)[0].tolist(), "edges": E.tolist(),
+            "demands": f[E].tolist(), "k": int(inst.k) - int(forced.sum()),
+            "forced": np.nonzero(forced)[0].tolist(), "rounds": rounds, "fe_passes": passes}
 
 
 def fone_kernelize(inst):
