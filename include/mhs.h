@@ -17,9 +17,21 @@
  *   Algorithm 3: repeat (Algorithm 1, then Algorithm 2 on its output) until
  *       a round deletes nothing.
  *
+ * Two variants of the experiments (Section 5.1) are options:
+ *   MHS_RULE_SE ("MD+SE"): the hyperedge pass tests the superedge rule SE
+ *       of Section 3.1 instead of DP: e_j goes if some e_i lies within e_j
+ *       with f(e_i) >= f(e_j), i.e. D_ij = [I^E_ij = I^E_ii and f_i >= f_j],
+ *       with the same simultaneous deletions and tie-break.
+ *   full_edges (KernelGPU-FE): whenever Algorithm 3 reaches its fixpoint,
+ *       the full-edge rule FE of Section 3.1 runs: every hyperedge with
+ *       |e| = f(e) goes and its vertices go into the solution (k drops by
+ *       one per vertex, see mhs_forced_at); every other hyperedge loses one
+ *       unit of demand per such vertex and goes at demand 0.  If FE changed
+ *       anything, more rounds follow; the result is a fixpoint of both.
+ *
  * Problem input (Problem 1.1, Section 1): hypergraph H = (V, E) with
  * V = {0..n-1}, hyperedges e_0..e_{m-1} in CSR form, demands f(e) >= 1 and
- * the budget k.  DP and MD never change f or k; k is passed through.
+ * the budget k.  DP, SE and MD never change f or k; only FE lowers them.
  *
  * Conventions
  *  - Every function returns an mhs_status; mhs_last_error() gives a message
@@ -81,13 +93,21 @@ typedef enum {
     MHS_SPARSITY_DENSE = 2  /* every tile of the upper triangle, every K block */
 } mhs_sparsity;
 
+/* The hyperedge rule of each round's first pass. */
+typedef enum {
+    MHS_RULE_DP = 0,  /* demand pushing, Algorithm 1 (default) */
+    MHS_RULE_SE = 1   /* superedge rule SE (the "MD+SE" variant) */
+} mhs_edge_rule;
+
 typedef struct {
     int32_t contraction; /* mhs_contraction */
     int32_t max_rounds;  /* mhs_kernelize stops after this many rounds; 0 = fixpoint */
     int32_t use_graphs;  /* 1: replay captured CUDA graphs (the whole fixpoint in one launch) */
     int32_t layout;      /* mhs_layout */
     int32_t sparsity;    /* mhs_sparsity */
-    int32_t reserved[3]; /* must be zero */
+    int32_t edge_rule;   /* mhs_edge_rule */
+    int32_t full_edges;  /* 1: alternate with rule FE (KernelGPU-FE); needs max_rounds = 0 */
+    int32_t reserved[1]; /* must be zero */
 } mhs_options;
 
 typedef struct {
@@ -137,7 +157,7 @@ mhs_status mhs_load_device(int32_t n, int32_t m, const int32_t *edge_ptr,
 /*
  * Load a batch of independent instances from HOST arrays, reduced together
  * (each round contracts all unfinished instances in the same launches).
- *   count                 number of instances, >= 1
+ *   count                 number of instances, 1 .. 65535
  *   n[b], m[b]            sizes of instance b
  *   edge_ptr              int64[sum m + 1]: CSR over the concatenated
  *                         hyperedges of all instances (instance b owns
@@ -169,8 +189,9 @@ int32_t mhs_count(const mhs_instance *inst);
 /*
  * One iteration of Algorithm 3 (one DP pass, then one MD pass on its
  * output) for every unfinished instance.  An instance whose last round
- * deleted nothing is finished and is not run again.  stats may be NULL.
- * Synchronises the instance's stream once.
+ * deleted nothing is finished and is not run again (with full_edges: FE runs
+ * right after such a round, and the instance goes on if FE changed it).
+ * stats may be NULL.  Synchronises the instance's stream once.
  */
 mhs_status mhs_reduce_round(mhs_instance *inst, mhs_round_stats *stats);
 
@@ -183,9 +204,10 @@ mhs_status mhs_kernelize(mhs_instance *inst, mhs_round_stats *stats);
  * non-NULL).
  *   vtx_out[vtx_cap]      surviving vertex ids (input ids), ascending
  *   edge_out[edge_cap]    surviving hyperedge ids (input ids), ascending
- *   demand_out[edge_cap]  f of each surviving hyperedge (unchanged input)
+ *   demand_out[edge_cap]  current f of each surviving hyperedge (the input's
+ *                         unless rule FE lowered it)
  *   n_out, m_out          number of surviving vertices / hyperedges
- *   k_out                 k (unchanged)
+ *   k_out                 current k (the input's minus the vertices FE took)
  *   rounds_out            rounds executed for this instance
  * MHS_EINVAL if a capacity is too small (counts are still returned).
  */
@@ -193,6 +215,16 @@ mhs_status mhs_result_at(const mhs_instance *inst, int32_t index, int32_t *vtx_o
                          int32_t vtx_cap, int32_t *n_out, int32_t *edge_out,
                          int32_t *demand_out, int32_t edge_cap, int32_t *m_out,
                          int64_t *k_out, int32_t *rounds_out);
+
+/*
+ * The vertices rule FE put into the solution for instance `index` (input
+ * ids, ascending, HOST buffer vtx_out[cap], may be NULL), their number in
+ * *count_out and the FE applications run (counting the last, empty one) in
+ * *fe_passes_out (either may be NULL).  Without full_edges the list is
+ * empty.  MHS_EINVAL if cap is too small (the count is still returned).
+ */
+mhs_status mhs_forced_at(const mhs_instance *inst, int32_t index, int32_t *vtx_out, int32_t cap,
+                         int32_t *count_out, int32_t *fe_passes_out);
 
 /* mhs_result_at for index 0. */
 mhs_status mhs_result(const mhs_instance *inst, int32_t *vtx_out, int32_t vtx_cap,
@@ -308,6 +340,8 @@ typedef struct {
     int32_t sparsity;         /* mhs_sparsity */
     int32_t small_items;      /* requests with n + m <= this go to the small-request lane
                                  (0: 8192; < 0: a single lane for all requests) */
+    int32_t edge_rule;        /* mhs_edge_rule, for every request */
+    int32_t full_edges;       /* 1: KernelGPU-FE for every request (see mhs_options) */
 } mhs_server_options;
 
 typedef struct {
@@ -347,6 +381,16 @@ mhs_status mhs_poll(mhs_server *srv, uint64_t ticket, int64_t timeout_us, int32_
                     int32_t vtx_cap, int32_t *n_out, int32_t *edge_out, int32_t *demand_out,
                     int32_t edge_cap, int32_t *m_out, int64_t *k_out, int32_t *rounds_out,
                     int64_t *times_ns);
+
+/*
+ * The vertices rule FE put into the solution of finished request `ticket`
+ * whose result is still held (after a counts-only mhs_poll): input ids
+ * ascending into vtx_out[cap] (may be NULL), their number in *count_out.
+ * MHS_EAGAIN if the request is not finished, MHS_EINVAL for an unknown or
+ * released ticket or a too small cap.
+ */
+mhs_status mhs_server_forced(mhs_server *srv, uint64_t ticket, int32_t *vtx_out, int32_t cap,
+                             int32_t *count_out);
 
 /* Stop (paused != 0) or resume admitting queued requests; running ones finish. */
 mhs_status mhs_server_pause(mhs_server *srv, int32_t paused);

@@ -457,6 +457,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int32_t R = ti.R;
             const int32_t j0 = ti.bj * kTcN;
             const int32_t i = ti.bi * kTcM + 32 * q + lane;
+            // DP stages f and f - s per hyperedge, SE stages f and s
+            const bool se = phase == 0 && s.edge_rule != 0;
             // stage the column data of this tile
             epi_bar();
             for (int c = et; c < kTcN; c += kEpiThreads) {
@@ -466,7 +468,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (j < R) {
                     if (phase == 0) {
                         a = (float)s.e_f[j];
-                        bb = (float)(s.e_f[j] - s.e_s[j]);
+                        bb = (float)(se ? s.e_s[j] : s.e_f[j] - s.e_s[j]);
                         o = s.e_c2o[j];
                     } else {
                         a = (float)s.v_deg[j];
@@ -476,12 +478,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                 ctl->colAB[c] = make_float2(a, bb);
                 ctl->colO[c] = o;
             }
-            float ri_f = 0.f, ri_a = 0.f;  // DP: f_i, f_i - s_i ; MD: d_i
+            float ri_f = 0.f, ri_a = 0.f;  // DP: f_i, f_i - s_i ; SE: f_i, s_i ; MD: d_i
             int32_t ri_o = 0;              // input index of row i
             if (i < R) {
                 if (phase == 0) {
                     ri_f = (float)s.e_f[i];
-                    ri_a = (float)(s.e_f[i] - s.e_s[i]);
+                    ri_a = (float)(se ? s.e_s[i] : s.e_f[i] - s.e_s[i]);
                     ri_o = s.e_c2o[i];
                 } else {
                     ri_f = (float)s.v_deg[i];
@@ -501,9 +503,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                 kit_init(kit, s, phase, ti);
                 nonzero = kit_next(kit) >= 0;
             }
-            // A count of 0 changes nothing unless some hyperedge has f > |e| (DP):
-            // in DP, x = 0 supersedes only from such a hyperedge; in MD it only
-            // adds dominators of a vertex in no hyperedge, deleted anyway.
+            // A count of 0 changes nothing unless some hyperedge has f > |e| (DP)
+            // or is empty (SE): only from such a hyperedge does x = 0 delete; in
+            // MD it only adds dominators of a vertex in no hyperedge, deleted anyway.
             const bool zero_matters = phase == 0 && s.has_loose;
             {
                 const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + acc * kAccCols;
@@ -540,8 +542,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                             const float x = v[c];
                             const float2 ab = cab[c];
                             if (phase == 0) {
-                                const bool dij = x + ri_a >= ab.x;  // f_i - (s_i - x) >= f_j
-                                const bool dji = x + ab.y >= ri_f;  // f_j - (s_j - x) >= f_i
+                                // DP: f_i - (s_i - x) >= f_j ; SE: x = s_i and f_i >= f_j
+                                const bool dij = se ? (x == ri_a && ri_f >= ab.x)
+                                                    : x + ri_a >= ab.x;
+                                const bool dji = se ? (x == ab.y && ab.x >= ri_f)
+                                                    : x + ab.y >= ri_f;
                                 cm |= (uint32_t)dij << c;
                                 rf |= dji;
                                 mut |= dij && dji;
@@ -570,10 +575,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                             const float2 ab = cab[c];
                             const bool i_first = ri_o < ctl->colO[cc];  // input-index tie-break
                             if (phase == 0) {
-                                // Algorithm 1: D_ij = [f_i - (s_i - x) >= f_j]; e_j goes iff
-                                // D_ij and (not D_ji or i before j)
-                                const bool dij = x + ri_a >= ab.x;
-                                const bool dji = x + ab.y >= ri_f;
+                                // Algorithm 1: D_ij = [f_i - (s_i - x) >= f_j] (rule SE:
+                                // [x = s_i and f_i >= f_j]); e_j goes iff D_ij and
+                                // (not D_ji or i before j)
+                                const bool dij = se ? (x == ri_a && ri_f >= ab.x)
+                                                    : x + ri_a >= ab.x;
+                                const bool dji = se ? (x == ab.y && ab.x >= ri_f)
+                                                    : x + ab.y >= ri_f;
                                 colmask |= (uint32_t)(valid && dij && (!dji || i_first)) << c;
                                 rowflag |= valid && dji && (!dij || !i_first);
                             } else {

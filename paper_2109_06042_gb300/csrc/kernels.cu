@@ -2,8 +2,9 @@
 // contraction with the fused DP / MD epilogue.
 //
 // Round structure (Algorithm 3, Section 4.1), all on the device:
-//   plan(phase 0) -> encode_edges -> contract(DP) -> compact_edges
+//   plan(phase 0) -> encode_edges -> contract(DP or SE) -> compact_edges
 //   plan(phase 1) -> encode_vertices -> contract(MD) -> compact_vertices
+//   [rule FE at a fixpoint, fe.cu]
 // The contraction of either kind (this file: popcount; contract_tc.cu:
 // tcgen05 FP8) computes the pair counts of Eq. (1) / Eq. (2) tile by tile
 // and never writes them out: the epilogue turns each count into the
@@ -149,11 +150,14 @@ __global__ void k_init(InstState *st, int count, int32_t max_rounds) {
     } else {
         for (int32_t e = threadIdx.x; e < s.m0; e += blockDim.x) { s.e_o2c[e] = e; s.e_c2o[e] = e; }
     }
+    if (s.forced)
+        for (int32_t v = threadIdx.x; v < s.n0; v += blockDim.x) s.forced[v] = 0;
     zero_occupancy(s, 0, s.m0);
     if (threadIdx.x == 0) {
         s.n = s.n0; s.m = s.m0; s.m_dp = s.m0; s.n_next = s.n0;
         s.rounds = 0; s.active = s.status == 0; s.max_rounds = max_rounds; s.changed = 0;
         s.dp_deleted = 0; s.md_deleted = 0; s.has_loose = 0;
+        s.fe_stage = 0; s.fe_passes = 0;
     }
 }
 
@@ -335,7 +339,9 @@ __global__ void k_scatter(InstState *st, const Plan *plan) {
         }
         if (kSet && kPhase == 0) {
             s.e_s[ce] = fresh_cnt;  // one thread owns the row
-            if (kDense && s.e_f[ce] > fresh_cnt) s.has_loose = 1;  // f > |e|
+            // a count of 0 decides a pair only from a hyperedge with f > |e|
+            // (DP) or an empty one (SE)
+            if (kDense && (s.edge_rule ? fresh_cnt == 0 : s.e_f[ce] > fresh_cnt)) s.has_loose = 1;
         }
     }
 }
@@ -416,12 +422,16 @@ __global__ void k_compact_vertices(InstState *st, int count, BatchCounters *ctr,
             s.m = s.m_dp;
             s.n = carry;
             s.rounds += 1;
-            if (!s.changed || (s.max_rounds > 0 && s.rounds >= s.max_rounds)) {
+            if (!s.changed && s.full_edges && s.max_rounds == 0) {
+                s.fe_stage = 1;  // fixpoint: rule FE decides (fe.cu) whether it goes on
+            } else if (!s.changed || (s.max_rounds > 0 && s.rounds >= s.max_rounds)) {
                 s.active = 0;
                 if (done_list && ctr) done_list[atomicAdd(&ctr->n_done, 1)] = b;
             }
         }
         __syncthreads();
+        if (s.fe_stage)  // FE marks the vertices it takes here
+            for (int32_t r = threadIdx.x; r < s.n; r += blockDim.x) s.v_del[r] = 0;
         // hyperedge rows of the next round's DP pass
         if (s.active) {
             for (int32_t r = threadIdx.x; r < s.m; r += blockDim.x) {
@@ -520,6 +530,8 @@ __global__ void __launch_bounds__(256) k_pop_contract(InstState *st, const Plan 
         if (phase == 0) {
             // Algorithm 1: D_ij = [f_i - (s_i - x) >= f_j]; delete j iff
             // D_ij and (not D_ji or i < j), i < j comparing input indices.
+            // Rule SE instead: D_ij = [x = s_i and f_i >= f_j] (e_i within e_j).
+            const bool se = s.edge_rule != 0;
 #pragma unroll
             for (int a = 0; a < 4; ++a) {
                 const int32_t i = i0 + ty + 16 * a;
@@ -531,8 +543,8 @@ __global__ void __launch_bounds__(256) k_pop_contract(InstState *st, const Plan 
                     if (j <= i || j >= R) continue;
                     const int32_t x = acc[a][c];
                     const int32_t fj = s.e_f[j], sj = s.e_s[j];
-                    const bool dij = fi - (si - x) >= fj;
-                    const bool dji = fj - (sj - x) >= fi;
+                    const bool dij = se ? (x == si && fi >= fj) : fi - (si - x) >= fj;
+                    const bool dji = se ? (x == sj && fj >= fi) : fj - (sj - x) >= fi;
                     const bool i_first = oi < s.e_c2o[j];  // tie-break by input index
                     if (dij && (!dji || i_first)) s.e_del[j] = 1;   // same-value stores
                     if (dji && (!dij || !i_first)) s.e_del[i] = 1;

@@ -45,6 +45,11 @@ cudaError_t launch_round_phase(InstState *st, Plan *plan, BatchCounters *ctr, in
 // rounds ran (hitting the cap raises kErrRoundCap).
 cudaError_t launch_loop_cond(cudaGraphConditionalHandle h, BatchCounters *ctr, int32_t *kerr,
                              int32_t round_cap, cudaStream_t s);
+// Rule FE for every instance that reached its DP/MD fixpoint in this round
+// (after phase 1; fe.cu).  An instance FE changed runs more rounds; one it
+// did not change is finished and goes to done_list.
+cudaError_t launch_full_edges(InstState *st, int count, BatchCounters *ctr, int32_t *done_list,
+                              int sms, cudaStream_t s);
 cudaError_t launch_alive_masks(const InstState *st, uint8_t *alive_v, uint8_t *alive_e,
                                cudaStream_t s);
 cudaError_t launch_alive_masks_batch(const InstState *st, int count, uint8_t *alive_v,

@@ -162,8 +162,13 @@ mhs_status check_options(const mhs_options *opt, mhs_options *out) {
         return fail(MHS_EINVAL, "options.layout must be 0 (auto), 1 (input) or 2 (sorted)");
     if (out->sparsity < 0 || out->sparsity > 2)
         return fail(MHS_EINVAL, "options.sparsity must be 0 (auto), 1 (skip) or 2 (dense)");
-    for (int i = 0; i < 3; ++i)
-        if (out->reserved[i] != 0) return fail(MHS_EINVAL, "options.reserved must be zero");
+    if (out->edge_rule < 0 || out->edge_rule > 1)
+        return fail(MHS_EINVAL, "options.edge_rule must be 0 (DP) or 1 (SE)");
+    if (out->full_edges < 0 || out->full_edges > 1)
+        return fail(MHS_EINVAL, "options.full_edges must be 0 or 1");
+    if (out->full_edges && out->max_rounds)
+        return fail(MHS_EINVAL, "options.full_edges needs max_rounds = 0");
+    if (out->reserved[0] != 0) return fail(MHS_EINVAL, "options.reserved must be zero");
     return MHS_OK;
 }
 
@@ -197,7 +202,7 @@ mhs_status validate_host(int32_t n, int32_t m, const int64_t *eptr64, const int3
 struct Layout {  // byte offsets inside the arena for one instance
     int64_t occ0, occ1;
     int64_t eptr, evtx, f;
-    int64_t v_o2c, v_c2o, e_o2c, e_c2o, e_f, e_s, v_deg, v_maxf, v_cnt, e_del, v_del;
+    int64_t v_o2c, v_c2o, e_o2c, e_c2o, e_f, e_s, v_deg, v_maxf, v_cnt, e_del, v_del, forced;
     int64_t A, At, Ab, Atb;
 };
 
@@ -251,9 +256,11 @@ mhs_status create(int32_t count, const int32_t *n, const int32_t *m, const int64
         h->max_nnz = std::max(h->max_nnz, z);
         h->max_m = std::max(h->max_m, m0);
         h->max_n = std::max(h->max_n, n0);
-        // every changing round deletes an item, so n + m + 1 rounds always suffice
-        h->round_cap = (int32_t)std::min<int64_t>(std::max<int64_t>(h->round_cap, n0 + m0 + 2),
-                                                  INT32_MAX);
+        // every changing round deletes an item, so n + m + 1 rounds always
+        // suffice; with FE, every fixpoint but the last is followed by an FE
+        // pass that deletes an item, so 2 (n + m) + 2 do
+        h->round_cap = (int32_t)std::min<int64_t>(
+            std::max<int64_t>(h->round_cap, 2 * (n0 + m0) + 4), INT32_MAX);
         L.eptr = off_eptr + 4 * c_m1;
         L.evtx = off_evtx + 4 * c_z;
         L.f = off_f + 4 * c_m;
@@ -271,6 +278,7 @@ mhs_status create(int32_t count, const int32_t *n, const int32_t *m, const int64
         L.v_cnt = ar.take(4 * (n0 + 1));
         L.e_del = ar.take(m0);
         L.v_del = ar.take(n0);
+        L.forced = opt.full_edges ? ar.take(n0) : -1;
         if (dense) {
             const int64_t arows = round_up(std::max<int64_t>(m0, 1), kRowAlign);
             const int64_t atrows = round_up(std::max<int64_t>(n0, 1), kRowAlign);
@@ -351,6 +359,9 @@ mhs_status create(int32_t count, const int32_t *n, const int32_t *m, const int64
         s.k = k[b];
         s.layout_sorted = opt.layout != MHS_LAYOUT_INPUT;
         s.no_skip = opt.sparsity == MHS_SPARSITY_DENSE;
+        s.edge_rule = opt.edge_rule;
+        s.full_edges = opt.full_edges;
+        s.forced = L.forced >= 0 ? base + L.forced : nullptr;
         s.eptr = reinterpret_cast<int32_t *>(base + L.eptr);
         s.evtx = reinterpret_cast<int32_t *>(base + L.evtx);
         s.f = reinterpret_cast<int32_t *>(base + L.f);
@@ -461,6 +472,8 @@ cudaError_t enqueue_round(mhs_instance *h, bool with_events) {
     e = launch_round_phase(h->dstate, h->dplan, h->dctr, h->count, 1, h->contraction, h->sms,
                            h->dkerr, h->stream, with_events ? h->ev[2] : nullptr,
                            with_events ? h->ev[3] : nullptr);
+    if (e == cudaSuccess && h->opt.full_edges)
+        e = launch_full_edges(h->dstate, h->count, h->dctr, nullptr, h->sms, h->stream);
     if (e != cudaSuccess) return e;
     e = cudaMemcpyAsync(h->hctr, h->dctr, sizeof(BatchCounters), cudaMemcpyDeviceToHost,
                         h->stream);
@@ -522,6 +535,8 @@ mhs_status build_loop_graph(mhs_instance *h) {
     if (e1 == cudaSuccess)
         e1 = launch_round_phase(h->dstate, h->dplan, h->dctr, h->count, 1, h->contraction, h->sms,
                                 h->dkerr, h->stream, nullptr, nullptr);
+    if (e1 == cudaSuccess && h->opt.full_edges)
+        e1 = launch_full_edges(h->dstate, h->count, h->dctr, nullptr, h->sms, h->stream);
     if (e1 == cudaSuccess)
         e1 = launch_loop_cond(cond, h->dctr, h->dkerr, h->round_cap, h->stream);
     cudaGraph_t captured = nullptr;
@@ -729,7 +744,8 @@ mhs_status mhs_load_batch(int32_t count, const int32_t *n, const int32_t *m,
                           mhs_instance **out) {
     if (!out) return fail(MHS_EINVAL, "out is NULL");
     *out = nullptr;
-    if (count < 1 || count > (1 << 20)) return fail(MHS_EINVAL, "count must be in [1, 2^20]");
+    // kernels index the instances of a batch by blockIdx.y
+    if (count < 1 || count > 65535) return fail(MHS_EINVAL, "count must be in [1, 65535]");
     if (!n || !m || !edge_ptr || !k) return fail(MHS_EINVAL, "NULL input array");
     std::vector<int64_t> eoff(count + 1, 0), nnz(count);
     for (int b = 0; b < count; ++b) {
@@ -800,7 +816,8 @@ mhs_status mhs_load_batch_device(int32_t count, const int32_t *n, const int32_t 
                                  const mhs_options *opt, void *cuda_stream, mhs_instance **out) {
     if (!out) return fail(MHS_EINVAL, "out is NULL");
     *out = nullptr;
-    if (count < 1 || count > (1 << 20)) return fail(MHS_EINVAL, "count must be in [1, 2^20]");
+    // kernels index the instances of a batch by blockIdx.y
+    if (count < 1 || count > 65535) return fail(MHS_EINVAL, "count must be in [1, 65535]");
     if (!n || !m || !edge_ptr || !k) return fail(MHS_EINVAL, "NULL input array");
     std::vector<int64_t> eoff(count + 1, 0);
     for (int b = 0; b < count; ++b) {
@@ -947,6 +964,32 @@ mhs_status mhs_result_at(const mhs_instance *inst, int32_t index, int32_t *vtx_o
     if (eo) std::sort(eo, eo + s.m);
     if (demand_out)
         for (int32_t i = 0; i < s.m; ++i) demand_out[i] = f[eo[i]];
+    return MHS_OK;
+}
+
+mhs_status mhs_forced_at(const mhs_instance *inst, int32_t index, int32_t *vtx_out, int32_t cap,
+                         int32_t *count_out, int32_t *fe_passes_out) {
+    if (!inst) return fail(MHS_EINVAL, "instance is NULL");
+    if (index < 0 || index >= inst->count) return fail(MHS_EINVAL, "index out of range");
+    InstState s;
+    cudaStream_t cs = inst->stream;
+    CUDA_TRY(cudaMemcpyAsync(&s, inst->dstate + index, sizeof(s), cudaMemcpyDeviceToHost, cs));
+    CUDA_TRY(cudaStreamSynchronize(cs));
+    if (fe_passes_out) *fe_passes_out = s.fe_passes;
+    std::vector<uint8_t> flags;
+    if (s.forced && s.n0 > 0) {
+        flags.resize(s.n0);
+        CUDA_TRY(cudaMemcpyAsync(flags.data(), s.forced, (size_t)s.n0, cudaMemcpyDeviceToHost, cs));
+        CUDA_TRY(cudaStreamSynchronize(cs));
+    }
+    int32_t c = 0;
+    for (uint8_t x : flags) c += x != 0;
+    if (count_out) *count_out = c;
+    if (!vtx_out) return MHS_OK;
+    if (cap < c) return fail(MHS_EINVAL, "output capacity too small (need %d vertices)", c);
+    int32_t w = 0;
+    for (int32_t v = 0; v < (int32_t)flags.size(); ++v)
+        if (flags[v]) vtx_out[w++] = v;
     return MHS_OK;
 }
 

@@ -43,9 +43,16 @@ struct InstState {
     int64_t nnz0;
     const int32_t *eptr;   // [m0+1] (int32 offsets into evtx)
     const int32_t *evtx;   // [nnz0] vertex ids
-    const int32_t *f;      // [m0] demands
+    int32_t *f;            // [m0] current demands (the input's, until FE lowers them)
 
-    int64_t k;
+    int64_t k;             // current budget (FE lowers it)
+
+    // ---- reduction variant ----
+    int32_t edge_rule;     // hyperedge pass: 0 = DP (Algorithm 1), 1 = SE (superedge rule)
+    int32_t full_edges;    // 1: alternate the DP/SE + MD fixpoint with rule FE
+    int32_t fe_stage;      // 1: this round reached the fixpoint; FE runs before the next
+    int32_t fe_passes;     // FE applications so far (counting the last, empty one)
+    uint8_t *forced;       // [n0] 1 = vertex put into the solution by FE (input ids)
 
     // ---- round state ----
     int32_t n, m;          // current alive vertices / hyperedges
@@ -88,7 +95,8 @@ struct InstState {
     // phase p (0: A, 1: At); occ_words[p] words per row block
     uint32_t *occ[2];
     int32_t occ_words[2];
-    int32_t has_loose;     // DP: some hyperedge has f > |e| (zero counts then matter)
+    int32_t has_loose;     // zero counts matter in this hyperedge pass: DP, some
+                           // hyperedge has f > |e|; SE, some hyperedge is empty
     int32_t no_skip;       // 1: contract every tile and K block (dense formulation)
     // offsets of this instance's ids in the concatenated ids of its batch
     int64_t v_base, e_base;

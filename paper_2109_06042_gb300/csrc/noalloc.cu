@@ -131,7 +131,7 @@ extern "C" mhs_status mhs_kernelize_noalloc(int32_t n, int32_t m, const int32_t 
     st.nnz0 = nnz;
     st.eptr = edge_ptr;  // inputs are read in place
     st.evtx = edge_vtx;
-    st.f = demand;
+    st.f = const_cast<int32_t *>(demand);  // read only: rule FE is off here
     st.v_o2c = reinterpret_cast<int32_t *>(base + o_vo2c);
     st.v_c2o = reinterpret_cast<int32_t *>(base + o_vc2o);
     st.e_o2c = reinterpret_cast<int32_t *>(base + o_eo2c);

@@ -66,17 +66,17 @@ struct Request {
     int64_t t_submit = 0, t_admit = 0, t_done = 0;
     bool done = false;
     mhs_status status = MHS_OK;
-    std::vector<int32_t> vout, eout, dout;
+    std::vector<int32_t> vout, eout, dout, forced;
     int32_t rounds = 0;
 };
 
 // Device layout of one admitted instance inside its arena.
 struct Layout {
     int64_t eptr, evtx, f, v_o2c, v_c2o, e_o2c, e_c2o, e_f, e_s, v_deg, v_maxf, v_cnt, e_del,
-        v_del, occ0, occ1, tmaps, dense, dense_bytes, bytes;
+        v_del, forced, occ0, occ1, tmaps, dense, dense_bytes, bytes;
 };
 
-Layout plan_layout(int32_t n, int32_t m, int64_t nnz, bool dense) {
+Layout plan_layout(int32_t n, int32_t m, int64_t nnz, bool dense, bool fe) {
     Layout L;
     int64_t b = 0;
     auto take = [&b](int64_t x) {
@@ -98,6 +98,7 @@ Layout plan_layout(int32_t n, int32_t m, int64_t nnz, bool dense) {
     L.v_cnt = take(4 * ((int64_t)n + 1));
     L.e_del = take(m);
     L.v_del = take(n);
+    L.forced = fe ? take(n) : -1;
     {
         const int64_t arows = up(m > 0 ? m : 1, kRowAlign), atrows = up(n > 0 ? n : 1, kRowAlign);
         L.occ0 = take(dense ? 4 * (arows / kTcM) * occ_words(n) : 0);
@@ -181,7 +182,8 @@ mhs_status admit(Lane &Ln, int si, std::shared_ptr<Request> req) {
     mhs_server *S = Ln.S;
     const bool dense = S->contraction == kFp8;
     const int64_t nnz = req->ptr.empty() ? 0 : req->ptr.back();
-    Layout L = plan_layout(req->n, req->m, nnz, dense);
+    const bool fe = S->opt.full_edges != 0;
+    Layout L = plan_layout(req->n, req->m, nnz, dense, fe);
     uint8_t *a = nullptr;
     cudaError_t e = cudaMallocFromPoolAsync(reinterpret_cast<void **>(&a), (size_t)L.bytes, S->pool,
                                             Ln.stream);
@@ -194,6 +196,9 @@ mhs_status admit(Lane &Ln, int si, std::shared_ptr<Request> req) {
     s.k = req->k;
     s.layout_sorted = S->opt.layout != MHS_LAYOUT_INPUT;
     s.no_skip = S->opt.sparsity == MHS_SPARSITY_DENSE;
+    s.edge_rule = S->opt.edge_rule;
+    s.full_edges = S->opt.full_edges;
+    s.forced = fe ? a + L.forced : nullptr;
     s.eptr = reinterpret_cast<int32_t *>(a + L.eptr);
     s.evtx = reinterpret_cast<int32_t *>(a + L.evtx);
     s.f = reinterpret_cast<int32_t *>(a + L.f);
@@ -293,6 +298,7 @@ void retire(Lane &Ln, const std::vector<int> &fin) {
         e = cudaMemcpyAsync(Ln.hstates + i, Ln.dstate + fin[i], sizeof(InstState),
                             cudaMemcpyDeviceToHost, Ln.stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(Ln.stream);
+    std::vector<std::vector<uint8_t>> taken(S->opt.full_edges ? fin.size() : 0);
     for (size_t i = 0; i < fin.size() && e == cudaSuccess; ++i) {
         const InstState &s = Ln.hstates[i];
         Request &r = *Ln.slots[fin[i]].req;
@@ -304,6 +310,15 @@ void retire(Lane &Ln, const std::vector<int> &fin) {
         if (e == cudaSuccess && s.m > 0)
             e = cudaMemcpyAsync(r.eout.data(), s.e_c2o, 4 * (size_t)s.m, cudaMemcpyDeviceToHost,
                                 Ln.stream);
+        if (S->opt.full_edges) {  // FE lowered demands and took vertices
+            if (e == cudaSuccess && s.m0 > 0)
+                e = cudaMemcpyAsync(r.dem.data(), s.f, 4 * (size_t)s.m0, cudaMemcpyDeviceToHost,
+                                    Ln.stream);
+            taken[i].resize(s.n0);
+            if (e == cudaSuccess && s.n0 > 0 && s.forced)
+                e = cudaMemcpyAsync(taken[i].data(), s.forced, (size_t)s.n0,
+                                    cudaMemcpyDeviceToHost, Ln.stream);
+        }
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(Ln.stream);
     InstState z;
@@ -320,6 +335,10 @@ void retire(Lane &Ln, const std::vector<int> &fin) {
             r.dout.resize(s.m);
             for (int32_t q = 0; q < s.m; ++q) r.dout[q] = r.dem[r.eout[q]];
             r.rounds = s.rounds;
+            r.k = s.k;
+            if (!taken.empty())
+                for (int32_t v = 0; v < (int32_t)taken[i].size(); ++v)
+                    if (taken[i][v]) r.forced.push_back(v);
             r.status = s.status ? MHS_EDEVICE : MHS_OK;
         } else {
             r.status = MHS_ECUDA;
@@ -436,6 +455,8 @@ mhs_status capture_graph(Lane &Ln) {
     if (e1 == cudaSuccess)
         e1 = launch_round_phase(Ln.dstate, Ln.dplan, Ln.dctr, Ln.slots_n, 1, S->contraction,
                                 S->sms, Ln.dkerr, Ln.stream, nullptr, nullptr, Ln.ddone);
+    if (e1 == cudaSuccess && S->opt.full_edges)
+        e1 = launch_full_edges(Ln.dstate, Ln.slots_n, Ln.dctr, Ln.ddone, S->sms, Ln.stream);
     if (e1 == cudaSuccess)
         e1 = cudaMemcpyAsync(Ln.hctr, Ln.dctr, sizeof(BatchCounters), cudaMemcpyDeviceToHost,
                              Ln.stream);
@@ -571,6 +592,10 @@ mhs_status mhs_server_create(const mhs_server_options *opt_in, void *cuda_stream
     if (opt.layout < 0 || opt.layout > 2) return set_error(MHS_EINVAL, "layout must be 0, 1 or 2");
     if (opt.sparsity < 0 || opt.sparsity > 2)
         return set_error(MHS_EINVAL, "sparsity must be 0, 1 or 2");
+    if (opt.edge_rule < 0 || opt.edge_rule > 1)
+        return set_error(MHS_EINVAL, "edge_rule must be 0 (DP) or 1 (SE)");
+    if (opt.full_edges < 0 || opt.full_edges > 1)
+        return set_error(MHS_EINVAL, "full_edges must be 0 or 1");
     auto *S = new mhs_server();
     S->opt = opt;
     S->contraction = opt.contraction == MHS_CONTRACT_POPCOUNT ? kPopcount : kFp8;
@@ -637,7 +662,7 @@ mhs_status mhs_submit(mhs_server *S, int32_t n, int32_t m, const int32_t *edge_p
     r->ptr.assign(edge_ptr, edge_ptr + m + 1);
     r->vtx.assign(edge_vtx, edge_vtx + nnz);
     r->dem.assign(demand, demand + m);
-    r->footprint = plan_layout(n, m, nnz, S->contraction == kFp8).bytes;
+    r->footprint = plan_layout(n, m, nnz, S->contraction == kFp8, S->opt.full_edges != 0).bytes;
     // tile-list entries only matter for the tcgen05 contraction
     r->tiles = S->contraction == kFp8 ? std::max(tc_tiles(m), tc_tiles(n)) : 0;
     if (S->contraction == kFp8 && r->tiles > kServerListCap)
@@ -702,6 +727,25 @@ mhs_status mhs_poll(mhs_server *S, uint64_t ticket, int64_t timeout_us, int32_t 
     if (edge_out) std::copy(r->eout.begin(), r->eout.end(), edge_out);
     if (demand_out) std::copy(r->dout.begin(), r->dout.end(), demand_out);
     S->table.erase(it);
+    return MHS_OK;
+}
+
+mhs_status mhs_server_forced(mhs_server *S, uint64_t ticket, int32_t *vtx_out, int32_t cap,
+                             int32_t *count_out) {
+    if (!S) return set_error(MHS_EINVAL, "server is NULL");
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->table.find(ticket);
+    if (it == S->table.end())
+        return set_error(MHS_EINVAL, "unknown or released ticket %llu", (unsigned long long)ticket);
+    const Request &r = *it->second;
+    if (!r.done) return set_error(MHS_EAGAIN, "request %llu not finished", (unsigned long long)ticket);
+    if (r.status != MHS_OK)
+        return set_error(r.status, "request %llu failed on the device", (unsigned long long)ticket);
+    const int32_t c = (int32_t)r.forced.size();
+    if (count_out) *count_out = c;
+    if (!vtx_out) return MHS_OK;
+    if (cap < c) return set_error(MHS_EINVAL, "output capacity too small (need %d vertices)", c);
+    std::copy(r.forced.begin(), r.forced.end(), vtx_out);
     return MHS_OK;
 }
 

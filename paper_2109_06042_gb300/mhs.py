@@ -34,12 +34,14 @@ class MhsError(RuntimeError):
 
 LAYOUTS = {"auto": 0, "input": 1, "sorted": 2}
 SPARSITY = {"auto": 0, "skip": 1, "dense": 2}
+RULES = {"dp": 0, "se": 1}
 
 
 class Options(ctypes.Structure):
     _fields_ = [("contraction", ctypes.c_int32), ("max_rounds", ctypes.c_int32),
                 ("use_graphs", ctypes.c_int32), ("layout", ctypes.c_int32),
-                ("sparsity", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("sparsity", ctypes.c_int32), ("edge_rule", ctypes.c_int32),
+                ("full_edges", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
 
 
 class RoundStats(ctypes.Structure):
@@ -55,7 +57,8 @@ class ServerOptions(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("max_slots", ctypes.c_int32),
                 ("queue_capacity", ctypes.c_int32), ("contraction", ctypes.c_int32),
                 ("layout", ctypes.c_int32), ("sparsity", ctypes.c_int32),
-                ("small_items", ctypes.c_int32)]
+                ("small_items", ctypes.c_int32), ("edge_rule", ctypes.c_int32),
+                ("full_edges", ctypes.c_int32)]
 
 
 class ServerStats(ctypes.Structure):
@@ -91,6 +94,7 @@ _SIGS = {
     "mhs_kernelize": (_i32, [_vp, ctypes.POINTER(RoundStats)]),
     "mhs_result_at": (_i32, [_vp, _i32, _P32, _i32, _P32, _P32, _P32, _i32, _P32, _P64, _P32]),
     "mhs_result": (_i32, [_vp, _P32, _i32, _P32, _P32, _P32, _i32, _P32, _P64, _P32]),
+    "mhs_forced_at": (_i32, [_vp, _i32, _P32, _i32, _P32, _P32]),
     "mhs_result_device": (_i32, [_vp, _i32, _vp, _vp]),
     "mhs_result_batch_device": (_i32, [_vp, _vp, _vp]),
     "mhs_trace_at": (_i32, [_vp, _i32, _P32, _i32, _P32]),
@@ -106,6 +110,7 @@ _SIGS = {
                           ctypes.POINTER(ctypes.c_uint64)]),
     "mhs_poll": (_i32, [_vp, ctypes.c_uint64, _i64, _P32, _i32, _P32, _P32, _P32, _i32, _P32,
                         _P64, _P32, _P64]),
+    "mhs_server_forced": (_i32, [_vp, ctypes.c_uint64, _P32, _i32, _P32]),
     "mhs_server_pause": (_i32, [_vp, _i32]),
     "mhs_server_get_stats": (_i32, [_vp, ctypes.POINTER(ServerStats)]),
     "mhs_server_destroy": (None, [_vp]),
@@ -160,7 +165,7 @@ def set_default_layout(layout: str):
 
 
 def make_options(contraction="auto", max_rounds=0, use_graphs=True, layout=None,
-                 sparsity=None) -> Options:
+                 sparsity=None, rule="dp", full_edges=False) -> Options:
     o = Options()
     _check(lib().mhs_default_options(ctypes.byref(o)))
     o.contraction = CONTRACTIONS[contraction] if isinstance(contraction, str) else int(contraction)
@@ -170,6 +175,8 @@ def make_options(contraction="auto", max_rounds=0, use_graphs=True, layout=None,
     o.layout = LAYOUTS[lay] if isinstance(lay, str) else int(lay)
     sp = _DEFAULT_SPARSITY[0] if sparsity is None else sparsity
     o.sparsity = SPARSITY[sp] if isinstance(sp, str) else int(sp)
+    o.edge_rule = RULES[rule] if isinstance(rule, str) else int(rule)
+    o.full_edges = int(bool(full_edges))
     return o
 
 
@@ -191,7 +198,7 @@ class Instance:
     # ---- loading ----
     @classmethod
     def load(cls, inst, contraction="auto", max_rounds=0, use_graphs=True, stream=None,
-             layout=None, sparsity=None):
+             layout=None, sparsity=None, rule="dp", full_edges=False):
         """mhs_load from host arrays of an ``instances.Instance``-like object."""
         ptr = np.ascontiguousarray(inst.edge_ptr, dtype=np.int32)
         vtx = np.ascontiguousarray(inst.edge_vtx, dtype=np.int32)
@@ -200,7 +207,7 @@ class Instance:
             vtx = np.zeros(1, np.int32)
         if dem.size == 0:
             dem = np.zeros(1, np.int32)
-        opt = make_options(contraction, max_rounds, use_graphs, layout, sparsity)
+        opt = make_options(contraction, max_rounds, use_graphs, layout, sparsity, rule, full_edges)
         h = ctypes.c_void_p()
         _check(lib().mhs_load(int(inst.n), int(inst.m), _p32(ptr), _p32(vtx), _p32(dem),
                               int(inst.k), ctypes.byref(opt), _stream_ptr(stream),
@@ -209,9 +216,10 @@ class Instance:
 
     @classmethod
     def load_device(cls, n, m, edge_ptr, edge_vtx, demand, k, contraction="auto", max_rounds=0,
-                    use_graphs=True, stream=None, layout=None, sparsity=None):
+                    use_graphs=True, stream=None, layout=None, sparsity=None, rule="dp",
+                    full_edges=False):
         """mhs_load_device from CUDA tensors (int32, contiguous)."""
-        opt = make_options(contraction, max_rounds, use_graphs, layout, sparsity)
+        opt = make_options(contraction, max_rounds, use_graphs, layout, sparsity, rule, full_edges)
         h = ctypes.c_void_p()
         _check(lib().mhs_load_device(int(n), int(m), ctypes.c_void_p(edge_ptr.data_ptr()),
                                      ctypes.c_void_p(edge_vtx.data_ptr()),
@@ -220,7 +228,8 @@ class Instance:
         return cls(h)
 
     @classmethod
-    def load_batch(cls, insts, contraction="auto", max_rounds=0, use_graphs=True, stream=None):
+    def load_batch(cls, insts, contraction="auto", max_rounds=0, use_graphs=True, stream=None,
+                   rule="dp", full_edges=False):
         """mhs_load_batch from a list of host instances."""
         count = len(insts)
         n = np.array([i.n for i in insts], dtype=np.int32)
@@ -236,12 +245,13 @@ class Instance:
         vtx = np.concatenate([np.asarray(i.edge_vtx, np.int32) for i in insts] + [np.zeros(1, np.int32)])
         dem = np.concatenate([np.asarray(i.demand, np.int32) for i in insts] + [np.zeros(1, np.int32)])
         return cls.load_batch_arrays(count, n, m, ptr, vtx, dem, k, contraction, max_rounds,
-                                     use_graphs, stream)
+                                     use_graphs, stream, rule=rule, full_edges=full_edges)
 
     @classmethod
     def load_batch_arrays(cls, count, n, m, ptr, vtx, dem, k, contraction="auto", max_rounds=0,
-                          use_graphs=True, stream=None, layout=None, sparsity=None):
-        opt = make_options(contraction, max_rounds, use_graphs, layout, sparsity)
+                          use_graphs=True, stream=None, layout=None, sparsity=None, rule="dp",
+                          full_edges=False):
+        opt = make_options(contraction, max_rounds, use_graphs, layout, sparsity, rule, full_edges)
         h = ctypes.c_void_p()
         _check(lib().mhs_load_batch(int(count), _p32(n), _p32(m), ptr.ctypes.data_as(_P64),
                                     _p32(vtx), _p32(dem), k.ctypes.data_as(_P64),
@@ -250,13 +260,14 @@ class Instance:
 
     @classmethod
     def load_batch_device(cls, n, m, k, edge_ptr, edge_vtx, demand, contraction="auto",
-                          max_rounds=0, use_graphs=True, stream=None, layout=None, sparsity=None):
+                          max_rounds=0, use_graphs=True, stream=None, layout=None, sparsity=None,
+                          rule="dp", full_edges=False):
         """mhs_load_batch_device: n, m, k host numpy arrays; edge_ptr (int64),
         edge_vtx, demand (int32) CUDA tensors over the concatenated instances."""
         n = np.ascontiguousarray(n, dtype=np.int32)
         m = np.ascontiguousarray(m, dtype=np.int32)
         k = np.ascontiguousarray(k, dtype=np.int64)
-        opt = make_options(contraction, max_rounds, use_graphs, layout, sparsity)
+        opt = make_options(contraction, max_rounds, use_graphs, layout, sparsity, rule, full_edges)
         h = ctypes.c_void_p()
         _check(lib().mhs_load_batch_device(int(n.size), _p32(n), _p32(m),
                                            ctypes.c_void_p(edge_ptr.data_ptr()),
@@ -313,6 +324,16 @@ class Instance:
         return {"vertices": vtx[:n.value], "edges": edg[:m.value], "demands": dem[:m.value],
                 "k": int(k.value), "rounds": int(r.value)}
 
+    def forced(self, index: int = 0):
+        """(input ids rule FE put into the solution, ascending; FE passes run)."""
+        c = ctypes.c_int32()
+        p = ctypes.c_int32()
+        _check(lib().mhs_forced_at(self._h, int(index), None, 0, ctypes.byref(c), ctypes.byref(p)))
+        out = np.zeros(max(c.value, 1), np.int32)
+        _check(lib().mhs_forced_at(self._h, int(index), _p32(out), out.size, ctypes.byref(c),
+                                   ctypes.byref(p)))
+        return out[:c.value], int(p.value)
+
     def result_device(self, alive_v, alive_e, index: int = 0):
         """Write uint8 alive masks (CUDA tensors) over the input ids."""
         _check(lib().mhs_result_device(self._h, int(index), ctypes.c_void_p(alive_v.data_ptr()),
@@ -363,19 +384,24 @@ class Instance:
 
 
 def kernelize(inst, contraction="auto", max_rounds=0, use_graphs=True, layout=None,
-              sparsity=None) -> dict:
-    """Load, reduce to the fixpoint and return the result of one host instance."""
+              sparsity=None, rule="dp", full_edges=False) -> dict:
+    """Load, reduce to the fixpoint and return the result of one host instance
+    (with ``full_edges`` also 'forced' and 'fe_passes')."""
     with Instance.load(inst, contraction, max_rounds, use_graphs, layout=layout,
-                       sparsity=sparsity) as h:
+                       sparsity=sparsity, rule=rule, full_edges=full_edges) as h:
         h.kernelize()
-        return h.result()
+        res = h.result()
+        if full_edges:
+            res["forced"], res["fe_passes"] = h.forced()
+        return res
 
 
 class Server:
     """Continuous-batching server (mhs_server_*): submit host instances, poll results."""
 
     def __init__(self, hbm_budget_bytes=0, max_slots=256, queue_capacity=65536,
-                 contraction="auto", stream=None, layout=None, sparsity=None, small_items=0):
+                 contraction="auto", stream=None, layout=None, sparsity=None, small_items=0,
+                 rule="dp", full_edges=False):
         o = ServerOptions()
         _check(lib().mhs_server_default_options(ctypes.byref(o)))
         o.hbm_budget_bytes = int(hbm_budget_bytes)
@@ -387,6 +413,9 @@ class Server:
         sp = _DEFAULT_SPARSITY[0] if sparsity is None else sparsity
         o.sparsity = SPARSITY[sp] if isinstance(sp, str) else int(sp)
         o.small_items = int(small_items)
+        o.edge_rule = RULES[rule] if isinstance(rule, str) else int(rule)
+        o.full_edges = int(bool(full_edges))
+        self._fe = bool(full_edges)
         h = ctypes.c_void_p()
         _check(lib().mhs_server_create(ctypes.byref(o), _stream_ptr(stream), ctypes.byref(h)))
         self._h = h
@@ -418,14 +447,26 @@ class Server:
         if st == MHS_EAGAIN:
             return None
         _check(st)
+        forced = None
+        if self._fe:  # before the copying poll releases the result
+            c = ctypes.c_int32()
+            _check(lib().mhs_server_forced(self._h, ctypes.c_uint64(ticket), None, 0,
+                                           ctypes.byref(c)))
+            fb = np.zeros(max(c.value, 1), np.int32)
+            _check(lib().mhs_server_forced(self._h, ctypes.c_uint64(ticket), _p32(fb), fb.size,
+                                           ctypes.byref(c)))
+            forced = fb[:c.value]
         vtx = np.zeros(max(n.value, 1), np.int32)
         edg = np.zeros(max(m.value, 1), np.int32)
         dem = np.zeros(max(m.value, 1), np.int32)
         _check(lib().mhs_poll(self._h, ctypes.c_uint64(ticket), 0, _p32(vtx), vtx.size,
                               ctypes.byref(n), _p32(edg), _p32(dem), edg.size, ctypes.byref(m),
                               ctypes.byref(k), ctypes.byref(r), tm))
-        return {"vertices": vtx[:n.value], "edges": edg[:m.value], "demands": dem[:m.value],
-                "k": int(k.value), "rounds": int(r.value), "times_ns": [int(x) for x in tm]}
+        res = {"vertices": vtx[:n.value], "edges": edg[:m.value], "demands": dem[:m.value],
+               "k": int(k.value), "rounds": int(r.value), "times_ns": [int(x) for x in tm]}
+        if forced is not None:
+            res["forced"] = forced
+        return res
 
     def pause(self, paused=True):
         _check(lib().mhs_server_pause(self._h, int(bool(paused))))
