@@ -57,6 +57,10 @@ def parse():
     p.add_argument("--contraction", choices=["fp8", "popcount"], default="fp8")
     p.add_argument("--sparsity", choices=["skip", "dense"], default="skip",
                    help="tcgen05 block-sparse skipping (exact) or the dense formulation")
+    p.add_argument("--rule", choices=["dp", "se"], default="dp",
+                   help="hyperedge rule of each round: DP (Algorithm 1) or SE (MD+SE variant)")
+    p.add_argument("--full-edges", action="store_true",
+                   help="alternate with rule FE at every fixpoint (KernelGPU-FE variant)")
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--batch-count", type=int, default=4096)
     p.add_argument("--cpu-seconds", type=float, default=15.0,
@@ -236,6 +240,7 @@ def run_ours(args, rank, world, dist):
     batch = args.workload == "batch"
 
     mhs.set_default_sparsity(args.sparsity)
+    mhs.set_default_variant(args.rule, args.full_edges)
 
     def load():
         if batch:
@@ -392,11 +397,14 @@ def run_ours(args, rank, world, dist):
 
     cpu = seq = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(insts, desc, args.cpu_seconds)
-        seq = cpu_sequential(insts, desc, args.cpu_seconds)
+        cpu = cpu_baseline(insts, desc, args.cpu_seconds, args)
+        seq = cpu_sequential(insts, desc, args.cpu_seconds) if variant_name(args) == "DP+MD" \
+            else None
 
-    # load kernels incl. the result-mask kernel, plus per round: 10 + the loop-condition kernel
+    # load kernels incl. the result-mask kernel, plus per round: 10 + the loop-condition
+    # kernel (+ the 3 kernels of rule FE with --full-edges)
     load_kernels = 5 if batch else 3
+    per_round = 11 + (3 if args.full_edges else 0)
     line = {
         "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
@@ -404,7 +412,7 @@ def run_ours(args, rank, world, dist):
         "dtype": "e4m3" if args.contraction == "fp8" else "u32-popcount",
         "data": DATA,
         "config": {"workload": desc, "contraction": args.contraction, "rounds": rounds,
-                   "sparsity": args.sparsity,
+                   "sparsity": args.sparsity, "rules": variant_name(args),
                    "instances_per_step": D.count,
                    "l2": "inputs larger than L2: dense operands "
                          f"{sum(i.m * i.n for i in insts) / 1e9:.2f} GB per product",
@@ -414,7 +422,7 @@ def run_ours(args, rank, world, dist):
         "cpu_baseline": cpu,
         "cpu_sequential": seq,
         "e2e": e2e,
-        "gpu_launches": args.steps * (load_kernels + 11 * rounds),
+        "gpu_launches": args.steps * (load_kernels + per_round * rounds),
         "clocks": clk,
     }
     if loop is not None:
@@ -431,6 +439,7 @@ def run_stream(args, rank, world):
     B.build()
     from paper_2109_06042_gb300 import instances as I
     from paper_2109_06042_gb300 import mhs
+    mhs.set_default_variant(args.rule, args.full_edges)
     rng = np.random.Generator(np.random.PCG64(777 + rank))
     pool = [I.config_stream_one(50_000 + rank * 100_000 + i) for i in range(args.pool)]
     order = rng.integers(0, len(pool), size=args.requests)
@@ -514,14 +523,18 @@ def run_stream(args, rank, world):
     }
 
 
-def cpu_baseline(insts, desc, seconds):
+def variant_name(args):
+    return ("SE+MD" if args.rule == "se" else "DP+MD") + ("+FE" if args.full_edges else "")
+
+
+def cpu_baseline(insts, desc, seconds, args):
     """The oracle, as it stands, on a bounded sample of the workload."""
     from oracle import oracle as O
     O.build()
     done = 0
     t0 = time.perf_counter()
     for i in insts:
-        O.reduce(i)
+        O.reduce_variant(i, args.rule, args.full_edges)
         done += 1
         if time.perf_counter() - t0 > seconds:
             break
@@ -570,7 +583,7 @@ def run_reference(args, rank, world):
     def one_step():
         done, t0 = 0, time.perf_counter()
         for i in insts:
-            O.reduce(i)
+            O.reduce_variant(i, args.rule, args.full_edges)
             done += 1
             if time.perf_counter() - t0 > per_step:
                 break
@@ -590,7 +603,7 @@ def run_reference(args, rank, world):
         "ms_per_step": round(1e3 * total_t / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": DATA,
         "config": {"workload": desc, "contraction": "explicit pairwise set tests (oracle)",
-                   "parallelism": "host CPU, single thread"},
+                   "rules": variant_name(args), "parallelism": "host CPU, single thread"},
         "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"{total_done} kernelizations over {args.steps} steps, each "
                                    f"step at most ~{per_step:.1f} s of the workload ({desc})"},

@@ -152,6 +152,14 @@ def _p32(a):
 
 _DEFAULT_LAYOUT = ["auto"]
 _DEFAULT_SPARSITY = ["auto"]
+_DEFAULT_VARIANT = ["dp", False]
+
+
+def set_default_variant(rule: str = "dp", full_edges: bool = False):
+    """Reduction variant used by the helpers below when none is given: the
+    hyperedge rule ('dp' or 'se') and whether rule FE alternates with it."""
+    _DEFAULT_VARIANT[0] = rule
+    _DEFAULT_VARIANT[1] = bool(full_edges)
 
 
 def set_default_sparsity(sparsity: str):
@@ -165,7 +173,7 @@ def set_default_layout(layout: str):
 
 
 def make_options(contraction="auto", max_rounds=0, use_graphs=True, layout=None,
-                 sparsity=None, rule="dp", full_edges=False) -> Options:
+                 sparsity=None, rule=None, full_edges=None) -> Options:
     o = Options()
     _check(lib().mhs_default_options(ctypes.byref(o)))
     o.contraction = CONTRACTIONS[contraction] if isinstance(contraction, str) else int(contraction)
@@ -175,6 +183,8 @@ def make_options(contraction="auto", max_rounds=0, use_graphs=True, layout=None,
     o.layout = LAYOUTS[lay] if isinstance(lay, str) else int(lay)
     sp = _DEFAULT_SPARSITY[0] if sparsity is None else sparsity
     o.sparsity = SPARSITY[sp] if isinstance(sp, str) else int(sp)
+    rule = _DEFAULT_VARIANT[0] if rule is None else rule
+    full_edges = _DEFAULT_VARIANT[1] if full_edges is None else full_edges
     o.edge_rule = RULES[rule] if isinstance(rule, str) else int(rule)
     o.full_edges = int(bool(full_edges))
     return o
@@ -198,7 +208,7 @@ class Instance:
     # ---- loading ----
     @classmethod
     def load(cls, inst, contraction="auto", max_rounds=0, use_graphs=True, stream=None,
-             layout=None, sparsity=None, rule="dp", full_edges=False):
+             layout=None, sparsity=None, rule=None, full_edges=None):
         """mhs_load from host arrays of an ``instances.Instance``-like object."""
         ptr = np.ascontiguousarray(inst.edge_ptr, dtype=np.int32)
         vtx = np.ascontiguousarray(inst.edge_vtx, dtype=np.int32)
@@ -216,8 +226,8 @@ class Instance:
 
     @classmethod
     def load_device(cls, n, m, edge_ptr, edge_vtx, demand, k, contraction="auto", max_rounds=0,
-                    use_graphs=True, stream=None, layout=None, sparsity=None, rule="dp",
-                    full_edges=False):
+                    use_graphs=True, stream=None, layout=None, sparsity=None, rule=None,
+                    full_edges=None):
         """mhs_load_device from CUDA tensors (int32, contiguous)."""
         opt = make_options(contraction, max_rounds, use_graphs, layout, sparsity, rule, full_edges)
         h = ctypes.c_void_p()
@@ -229,7 +239,7 @@ class Instance:
 
     @classmethod
     def load_batch(cls, insts, contraction="auto", max_rounds=0, use_graphs=True, stream=None,
-                   rule="dp", full_edges=False):
+                   rule=None, full_edges=None):
         """mhs_load_batch from a list of host instances."""
         count = len(insts)
         n = np.array([i.n for i in insts], dtype=np.int32)
@@ -249,8 +259,8 @@ class Instance:
 
     @classmethod
     def load_batch_arrays(cls, count, n, m, ptr, vtx, dem, k, contraction="auto", max_rounds=0,
-                          use_graphs=True, stream=None, layout=None, sparsity=None, rule="dp",
-                          full_edges=False):
+                          use_graphs=True, stream=None, layout=None, sparsity=None, rule=None,
+                          full_edges=None):
         opt = make_options(contraction, max_rounds, use_graphs, layout, sparsity, rule, full_edges)
         h = ctypes.c_void_p()
         _check(lib().mhs_load_batch(int(count), _p32(n), _p32(m), ptr.ctypes.data_as(_P64),
@@ -261,7 +271,7 @@ class Instance:
     @classmethod
     def load_batch_device(cls, n, m, k, edge_ptr, edge_vtx, demand, contraction="auto",
                           max_rounds=0, use_graphs=True, stream=None, layout=None, sparsity=None,
-                          rule="dp", full_edges=False):
+                          rule=None, full_edges=None):
         """mhs_load_batch_device: n, m, k host numpy arrays; edge_ptr (int64),
         edge_vtx, demand (int32) CUDA tensors over the concatenated instances."""
         n = np.ascontiguousarray(n, dtype=np.int32)
@@ -384,14 +394,14 @@ class Instance:
 
 
 def kernelize(inst, contraction="auto", max_rounds=0, use_graphs=True, layout=None,
-              sparsity=None, rule="dp", full_edges=False) -> dict:
+              sparsity=None, rule=None, full_edges=None) -> dict:
     """Load, reduce to the fixpoint and return the result of one host instance
     (with ``full_edges`` also 'forced' and 'fe_passes')."""
     with Instance.load(inst, contraction, max_rounds, use_graphs, layout=layout,
                        sparsity=sparsity, rule=rule, full_edges=full_edges) as h:
         h.kernelize()
         res = h.result()
-        if full_edges:
+        if (_DEFAULT_VARIANT[1] if full_edges is None else full_edges):
             res["forced"], res["fe_passes"] = h.forced()
         return res
 
@@ -401,7 +411,7 @@ class Server:
 
     def __init__(self, hbm_budget_bytes=0, max_slots=256, queue_capacity=65536,
                  contraction="auto", stream=None, layout=None, sparsity=None, small_items=0,
-                 rule="dp", full_edges=False):
+                 rule=None, full_edges=None):
         o = ServerOptions()
         _check(lib().mhs_server_default_options(ctypes.byref(o)))
         o.hbm_budget_bytes = int(hbm_budget_bytes)
@@ -413,6 +423,8 @@ class Server:
         sp = _DEFAULT_SPARSITY[0] if sparsity is None else sparsity
         o.sparsity = SPARSITY[sp] if isinstance(sp, str) else int(sp)
         o.small_items = int(small_items)
+        rule = _DEFAULT_VARIANT[0] if rule is None else rule
+        full_edges = _DEFAULT_VARIANT[1] if full_edges is None else full_edges
         o.edge_rule = RULES[rule] if isinstance(rule, str) else int(rule)
         o.full_edges = int(bool(full_edges))
         self._fe = bool(full_edges)
