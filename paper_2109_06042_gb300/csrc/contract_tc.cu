@@ -24,6 +24,7 @@
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 
+#include <cstdlib>
 #include <cstring>
 
 #include "bounded_wait.cuh"
@@ -43,7 +44,7 @@ constexpr int kTmemCols = 2 * kAccCols;         // 512
 constexpr int kEpiWarps = 8;                    // two per TMEM lane quarter
 constexpr int kThreads = 64 + 32 * kEpiWarps;   // producer + MMA + epilogue
 constexpr int kEpiThreads = 32 * kEpiWarps;
-constexpr int kGroupRows = 8;                   // row blocks per L2 group
+constexpr int kGroupRows = 16;                  // default row blocks per L2 group
 constexpr uint64_t kWaitNs = 4000000000ull;     // 4 s bound on any wait
 
 // ------------------------------------------------------------- PTX glue --
@@ -131,21 +132,22 @@ __device__ __forceinline__ int64_t tc_prefix(int64_t bi, int64_t cb) {
     return bi * cb - (bi / 2) * ((bi - 1) / 2 > 0 ? (bi - 1) / 2 : 0);
 }
 
-// Order: groups of kGroupRows row blocks; inside a group, column block by
-// column block, and inside a column block the group's row blocks.  About
-// 152 concurrent tiles then share ~8 row blocks and ~19 column blocks,
+// Order: groups of G row blocks; inside a group, column block by column
+// block, and inside a column block the group's row blocks.  With G = 16,
+// about 152 concurrent tiles share 16 row blocks and ~10 column blocks,
 // which keeps their K slices in L2.
-__device__ void tc_tile_coords(int64_t t, int32_t R, int32_t *bi_out, int32_t *bj_out) {
+__device__ void tc_tile_coords(int64_t t, int32_t R, int32_t G, int32_t *bi_out,
+                               int32_t *bj_out) {
     const int32_t rb = tc_row_blocks(R), cb = tc_col_blocks(R);
-    const int32_t ng = (rb + kGroupRows - 1) / kGroupRows;
+    const int32_t ng = (rb + G - 1) / G;
     int32_t lo = 0, hi = ng;  // find group g: prefix(g*G) <= t < prefix((g+1)*G)
     while (hi - lo > 1) {
         int32_t mid = (lo + hi) >> 1;
-        if (tc_prefix((int64_t)mid * kGroupRows, cb) <= t) lo = mid; else hi = mid;
+        if (tc_prefix((int64_t)mid * G, cb) <= t) lo = mid; else hi = mid;
     }
     const int32_t g = lo;
-    const int32_t r0 = g * kGroupRows;
-    const int32_t gsz = min(kGroupRows, rb - r0);
+    const int32_t r0 = g * G;
+    const int32_t gsz = min(G, rb - r0);
     int64_t p = t - tc_prefix(r0, cb);
     int32_t bj = r0 / 2;  // first column block of the group
     for (;;) {
@@ -168,16 +170,14 @@ struct TileInfo {
     int32_t bi, bj, R, nk;
 };
 
-// The t-th entry of this phase's tile list.
-__device__ __forceinline__ bool next_tile(const InstState *st, const Plan *plan, int phase,
-                                          int64_t t, TileInfo *ti) {
-    if (t >= plan->list_count) return false;
-    unpack_tile(plan->tile_list[t], &ti->b, &ti->bi, &ti->bj);
+// Sizes of the tile a packed tile-list entry names.
+__device__ __forceinline__ void tile_info(const InstState *st, int phase, int64_t entry,
+                                          TileInfo *ti) {
+    unpack_tile(entry, &ti->b, &ti->bi, &ti->bj);
     const InstState &s = st[ti->b];
     ti->R = phase == 0 ? s.m : s.n;
     const int32_t K = phase == 0 ? s.n : s.m_dp;
     ti->nk = ((K > 0 ? K : 1) + kTcK - 1) / kTcK;
-    return true;
 }
 
 // K blocks of a tile where both operands hold a nonzero: the occupancy
@@ -228,6 +228,7 @@ __device__ __forceinline__ int32_t kit_next(KIter &k) {
 __global__ void k_tile_list(InstState *st, Plan *plan, int phase) {
     const int lane = threadIdx.x & 31;
     const int64_t total = plan->total_tiles;
+    const int32_t G = plan->group_rows > 0 ? plan->group_rows : kGroupRows;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane); base < total;
          base += nw * 32) {
@@ -246,7 +247,7 @@ __global__ void k_tile_list(InstState *st, Plan *plan, int phase) {
             ti.R = phase == 0 ? s.m : s.n;
             const int32_t K = phase == 0 ? s.n : s.m_dp;
             ti.nk = ((K > 0 ? K : 1) + kTcK - 1) / kTcK;
-            tc_tile_coords(t - plan->tile_off[lo], ti.R, &ti.bi, &ti.bj);
+            tc_tile_coords(t - plan->tile_off[lo], ti.R, G, &ti.bi, &ti.bj);
             if ((phase == 0 && s.has_loose) || s.no_skip) {
                 keep = true;
             } else {
@@ -264,11 +265,21 @@ __global__ void k_tile_list(InstState *st, Plan *plan, int phase) {
     }
 }
 
+// Tiles are handed out dynamically: the producer thread takes the next
+// tile-list entry with an atomic and publishes it in a shared ring that the
+// MMA thread and the epilogue warps read in the same order.  CTAs that draw
+// cheap tiles take more of them, so the tiles in flight at any time stay a
+// narrow window of the (L2-grouped) list.
+constexpr int kRing = 8;
+
 struct __align__(8) SharedCtl {
     uint64_t full[kStages];
     uint64_t empty[kStages];
     uint64_t tmem_full[2];
     uint64_t tmem_empty[2];
+    uint64_t ring_full[kRing];   // entry published (producer arrives)
+    uint64_t ring_empty[kRing];  // entry read by the MMA thread and the epilogue (2 arrivals)
+    int64_t ring[kRing];         // packed tile entry, -1 = no more tiles
     uint64_t drain;
     uint32_t tmem_base;
     int abort;
@@ -295,6 +306,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int a = 0; a < 2; ++a) {
             mbar_init(smem_u32(&ctl->tmem_full[a]), 1);
             mbar_init(smem_u32(&ctl->tmem_empty[a]), kEpiThreads);
+        }
+        for (int r = 0; r < kRing; ++r) {
+            mbar_init(smem_u32(&ctl->ring_full[r]), 1);
+            mbar_init(smem_u32(&ctl->ring_empty[r]), 2);
         }
         mbar_init(smem_u32(&ctl->drain), 1);
         ctl->abort = 0;
@@ -323,21 +338,42 @@ __global__ void __launch_bounds__(kThreads, 1)
             int64_t issued = 0;
             bool aborted = false;
             const void *fenced = nullptr;
+            // Publish ring entry k: wait until both readers are done with the
+            // slot's previous entry, take the next list entry, and release it.
+            // Returns the entry (-1: the list is exhausted), or -2 on abort.
+            auto publish = [&](int k) -> int64_t {
+                const int slot = k % kRing;
+                if (!mbar_wait(smem_u32(&ctl->ring_empty[slot]), ((k / kRing) & 1) ^ 1, abort,
+                               kWaitNs))
+                    return -2;
+                const int32_t t = atomicAdd(const_cast<int32_t *>(&plan->list_next), 1);
+                const int64_t e = t < plan->list_count ? plan->tile_list[t] : -1;
+                ctl->ring[slot] = e;
+                mbar_arrive(smem_u32(&ctl->ring_full[slot]));
+                return e;
+            };
             // The next tile (list entry and first shared K block) is fetched
             // while the current one is issued, so a tile start does not wait
             // on global-memory latency.
             TileInfo ti, nx;
             KIter kit, nkit;
             int32_t kb = -1, nkb = -1;
-            int64_t t = blockIdx.x;
-            bool have = next_tile(st, plan, phase, t, &ti);
-            if (have) {
+            int it = 0;
+            int64_t cur = publish(0);
+            aborted = cur == -2;
+            if (cur >= 0) {
+                tile_info(st, phase, cur, &ti);
                 kit_init(kit, st[ti.b], phase, ti);
                 kb = kit_next(kit);
             }
-            while (have && !aborted) {
-                const bool have_nx = next_tile(st, plan, phase, t + gridDim.x, &nx);
-                if (have_nx) {
+            while (cur >= 0 && !aborted) {
+                const int64_t nxt = publish(it + 1);
+                if (nxt == -2) {
+                    aborted = true;
+                    break;
+                }
+                if (nxt >= 0) {
+                    tile_info(st, phase, nxt, &nx);
                     kit_init(nkit, st[nx.b], phase, nx);
                     nkb = kit_next(nkit);
                 }
@@ -364,11 +400,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                     ++issued;
                     if (++stage == kStages) { stage = 0; phase_bit ^= 1; }
                 }
-                have = have_nx;
+                cur = nxt;
                 ti = nx;
                 kit = nkit;
                 kb = nkb;
-                t += gridDim.x;
+                ++it;
             }
             if (aborted) {  // let the loads still in flight land before exiting
                 for (int64_t k = issued > kStages ? issued - kStages : 0; k < issued; ++k)
@@ -384,18 +420,33 @@ __global__ void __launch_bounds__(kThreads, 1)
             int it = 0;
             bool aborted = false;
             unsigned long long n_kblocks = 0, n_tiles = 0;
+            // ring entry k (false on abort)
+            auto take = [&](int k, int64_t *e) -> bool {
+                const int slot = k % kRing;
+                if (!mbar_wait(smem_u32(&ctl->ring_full[slot]), (k / kRing) & 1, abort, kWaitNs))
+                    return false;
+                *e = *reinterpret_cast<volatile int64_t *>(&ctl->ring[slot]);
+                return true;
+            };
             TileInfo ti, nx;
             KIter kit, nkit;
             int32_t kb = -1, nkb = -1;
-            int64_t t = blockIdx.x;
-            bool have = next_tile(st, plan, phase, t, &ti);
-            if (have) {
+            int64_t cur = -1;
+            aborted = !take(0, &cur);
+            if (cur >= 0) {
+                tile_info(st, phase, cur, &ti);
                 kit_init(kit, st[ti.b], phase, ti);
                 kb = kit_next(kit);
             }
-            while (have && !aborted) {
-                const bool have_nx = next_tile(st, plan, phase, t + gridDim.x, &nx);
-                if (have_nx) {  // prefetch the next tile's first K block
+            while (cur >= 0 && !aborted) {
+                mbar_arrive(smem_u32(&ctl->ring_empty[it % kRing]));  // done with entry `it`
+                int64_t nxt = -1;
+                if (!take(it + 1, &nxt)) {  // published before tile `it` was loaded
+                    aborted = true;
+                    break;
+                }
+                if (nxt >= 0) {  // prefetch the next tile's first K block
+                    tile_info(st, phase, nxt, &nx);
                     kit_init(nkit, st[nx.b], phase, nx);
                     nkb = kit_next(nkit);
                 }
@@ -427,11 +478,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (++stage == kStages) { stage = 0; phase_bit ^= 1; }
                 }
                 if (!aborted) mma_commit(smem_u32(&ctl->tmem_full[acc]));
-                have = have_nx;
+                cur = nxt;
                 ti = nx;
                 kit = nkit;
                 kb = nkb;
-                t += gridDim.x;
                 ++it;
             }
             if (aborted) {  // wait for the MMAs already issued before freeing TMEM
@@ -448,9 +498,17 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int q = warp & 3;             // TMEM lane quarter
         const int half = (warp - 2) >> 2;   // which 128 columns of the tile
         const int et = threadIdx.x - 64;
-        int it = 0;
         TileInfo ti;
-        for (int64_t t = blockIdx.x; next_tile(st, plan, phase, t, &ti); t += gridDim.x, ++it) {
+        for (int it = 0;; ++it) {
+            const int slot = it % kRing;
+            if (!epi_bar_and(mbar_wait(smem_u32(&ctl->ring_full[slot]), (it / kRing) & 1, abort,
+                                       kWaitNs))) {
+                *abort = 1;
+                break;
+            }
+            const int64_t entry = *reinterpret_cast<volatile int64_t *>(&ctl->ring[slot]);
+            if (entry < 0) break;
+            tile_info(st, phase, entry, &ti);
             InstState &s = st[ti.b];
             const int acc = it & 1;
             const uint32_t acc_phase = (it >> 1) & 1;
@@ -460,7 +518,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             // DP stages f and f - s per hyperedge, SE stages f and s
             const bool se = phase == 0 && s.edge_rule != 0;
             // stage the column data of this tile
-            epi_bar();
+            epi_bar();  // every epilogue thread has read the entry
+            if (et == 0) mbar_arrive(smem_u32(&ctl->ring_empty[slot]));
             for (int c = et; c < kTcN; c += kEpiThreads) {
                 const int32_t j = j0 + c;
                 float a = 0.f, bb = 0.f;
@@ -684,6 +743,15 @@ cudaError_t launch_tc_contract(InstState *st, Plan *plan, BatchCounters *ctr, in
                                int32_t *kerr, cudaStream_t s) {
     k_tc_contract<<<sms, kThreads, kSmemBytes, s>>>(st, plan, ctr, phase, kerr);
     return cudaGetLastError();
+}
+
+int32_t tile_group_rows() {
+    static int32_t g = [] {
+        const char *e = std::getenv("MHS_TILE_GROUP_ROWS");
+        const int v = e ? std::atoi(e) : 0;
+        return (int32_t)(v >= 1 && v <= 4096 ? v : kGroupRows);
+    }();
+    return g;
 }
 
 cudaError_t launch_tc_tile_list(InstState *st, Plan *plan, int phase, int sms, cudaStream_t s) {

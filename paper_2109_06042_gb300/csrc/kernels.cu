@@ -262,6 +262,7 @@ __global__ void k_plan(InstState *st, Plan *plan, int phase, int tc, BatchCounte
         plan->tile_off[count] = tcarry;
         plan->total_rows = rcarry;
         plan->list_count = 0;
+        plan->list_next = 0;
         plan->total_tiles = tcarry;
         plan->any_active = act_any;
         if (phase == 0 && ctr) {

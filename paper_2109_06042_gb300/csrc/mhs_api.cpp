@@ -408,6 +408,7 @@ mhs_status create(int32_t count, const int32_t *n, const int32_t *m, const int64
     p.tile_off = reinterpret_cast<int64_t *>(base + off_tileoff);
     p.tile_list = reinterpret_cast<int64_t *>(base + off_list);
     p.list_cap = (int32_t)std::min<int64_t>(list_cap, INT32_MAX);
+    p.group_rows = tile_group_rows();
     ce = cudaMemcpyAsync(h->dplan, &p, sizeof(p), cudaMemcpyHostToDevice, h->stream);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(h->dkerr, 0, 4, h->stream);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(h->dctr, 0, sizeof(BatchCounters), h->stream);

@@ -112,10 +112,12 @@ struct Plan {
     int32_t list_count;     // entries in tile_list this phase
     int32_t list_cap;
     int32_t total_rows;     // current hyperedges to scatter this phase
-    int32_t pad_;
+    int32_t group_rows;     // tcgen05 tile order: row blocks per L2 group (0: default)
     int64_t total_tiles;    // contraction tiles this phase
     int32_t *row_off;       // [count+1] prefix of current hyperedges of active instances
     int64_t *tile_off;      // [count+1] prefix of tiles
+    int32_t list_next;      // tcgen05: next tile_list entry to hand out (dynamic schedule)
+    int32_t pad_;
 };
 
 // Number of pair tiles of an R x R upper triangle.

@@ -522,6 +522,7 @@ mhs_status setup_lane(mhs_server *S, Lane &Ln, int id, int32_t slots, int64_t li
     p.tile_off = reinterpret_cast<int64_t *>(Ln.ctl + o_tile);
     p.tile_list = reinterpret_cast<int64_t *>(Ln.ctl + o_list);
     p.list_cap = (int32_t)std::min<int64_t>(list_cap, INT32_MAX);
+    p.group_rows = tile_group_rows();
     cudaError_t e = cudaMemsetAsync(Ln.ctl, 0, (size_t)o_list, Ln.stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(Ln.dplan, &p, sizeof(p), cudaMemcpyHostToDevice, Ln.stream);
