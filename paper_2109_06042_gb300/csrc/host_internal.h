@@ -17,4 +17,12 @@ mhs_status set_error(mhs_status st, const char *fmt, ...);
 // kept for reuse, so load/free loops do not reach the driver).
 cudaError_t pool_for(int dev, cudaMemPool_t *out);
 
+// Blocks of kPinnedBlock bytes of page-locked host memory from a
+// process-wide slab.  cudaMallocHost / cudaFreeHost cost tens of
+// microseconds and cudaFreeHost synchronises the device, which every
+// load / free would otherwise pay.  Blocks are 256-byte aligned.
+constexpr size_t kPinnedBlock = 512;
+void *pinned_block();  // nullptr if page-locked memory is unavailable
+void pinned_release(void *p);
+
 }  // namespace mhs

@@ -80,6 +80,31 @@ cudaError_t mhs::pool_for(int dev, cudaMemPool_t *out) {
 }
 
 namespace {
+std::mutex g_pin_mu;
+std::vector<void *> g_pin_free;  // slab blocks not in use (the slab is never returned)
+}  // namespace
+
+void *mhs::pinned_block() {
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    if (g_pin_free.empty()) {
+        constexpr size_t kChunk = 128 * kPinnedBlock;
+        void *c = nullptr;
+        if (cudaMallocHost(&c, kChunk) != cudaSuccess) return nullptr;
+        for (size_t o = 0; o < kChunk; o += kPinnedBlock)
+            g_pin_free.push_back(static_cast<uint8_t *>(c) + o);
+    }
+    void *b = g_pin_free.back();
+    g_pin_free.pop_back();
+    return b;
+}
+
+void mhs::pinned_release(void *p) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    g_pin_free.push_back(p);
+}
+
+namespace {
 
 // Sub-allocation plan of one arena.
 struct Arena {
@@ -114,8 +139,11 @@ struct mhs_instance {
     Plan *dplan = nullptr;
     BatchCounters *dctr = nullptr;
     int32_t *dkerr = nullptr;
-    BatchCounters *hctr = nullptr;  // pinned
-    int32_t *hkerr = nullptr;       // pinned
+    // one pinned slab block: counters [0, 64), error word [64, 128), plan
+    // header staging [128, 256), a single instance's tensor maps [256, 512)
+    uint8_t *pin = nullptr;
+    BatchCounters *hctr = nullptr;
+    int32_t *hkerr = nullptr;
     int64_t max_nnz = 0, max_m = 0, max_n = 0;
     // arena offsets of the batch-wide input arrays
     int64_t in_eptr = 0, in_evtx = 0, in_f = 0;
@@ -135,18 +163,20 @@ struct mhs_instance {
 
 namespace {
 
+static_assert(sizeof(BatchCounters) <= 64, "counters fit their pinned slot");
+static_assert(sizeof(Plan) <= 128, "plan header fits its pinned slot");
+
 void destroy(mhs_instance *h) {
     if (!h) return;
+    // no copy may still target the pinned block when it returns to the slab
     if (h->stream) cudaStreamSynchronize(h->stream);
     for (auto &g : h->graph)
         if (g) cudaGraphExecDestroy(g);
     if (h->loop_graph) cudaGraphExecDestroy(h->loop_graph);
     for (auto &e : h->ev)
         if (e) cudaEventDestroy(e);
-    if (h->arena) cudaFreeAsync(h->arena, h->stream);
-    if (h->stream) cudaStreamSynchronize(h->stream);
-    if (h->hctr) cudaFreeHost(h->hctr);
-    if (h->hkerr) cudaFreeHost(h->hkerr);
+    if (h->arena) cudaFreeAsync(h->arena, h->stream);  // stream-ordered
+    pinned_release(h->pin);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
 }
@@ -338,11 +368,13 @@ mhs_status create(int32_t count, const int32_t *n, const int32_t *m, const int64
     h->dplan = reinterpret_cast<Plan *>(base + off_plan);
     h->dctr = reinterpret_cast<BatchCounters *>(base + off_ctr);
     h->dkerr = reinterpret_cast<int32_t *>(base + off_kerr);
-    if (cudaMallocHost(&h->hctr, sizeof(BatchCounters)) != cudaSuccess ||
-        cudaMallocHost(&h->hkerr, sizeof(int32_t)) != cudaSuccess) {
+    h->pin = static_cast<uint8_t *>(pinned_block());
+    if (!h->pin) {
         destroy(h);
         return fail(MHS_ENOMEM, "pinned host allocation failed");
     }
+    h->hctr = reinterpret_cast<BatchCounters *>(h->pin);
+    h->hkerr = reinterpret_cast<int32_t *>(h->pin + 64);
     h->hstate.resize(count);
     int64_t vbase = 0, ebase = 0;
     for (int b = 0; b < count; ++b) {
@@ -409,10 +441,10 @@ mhs_status create(int32_t count, const int32_t *n, const int32_t *m, const int64
     p.tile_list = reinterpret_cast<int64_t *>(base + off_list);
     p.list_cap = (int32_t)std::min<int64_t>(list_cap, INT32_MAX);
     p.group_rows = tile_group_rows();
-    ce = cudaMemcpyAsync(h->dplan, &p, sizeof(p), cudaMemcpyHostToDevice, h->stream);
+    std::memcpy(h->pin + 128, &p, sizeof(p));  // staged in pinned memory: no synchronisation
+    ce = cudaMemcpyAsync(h->dplan, h->pin + 128, sizeof(p), cudaMemcpyHostToDevice, h->stream);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(h->dkerr, 0, 4, h->stream);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(h->dctr, 0, sizeof(BatchCounters), h->stream);
-    if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);  // p is a stack object
     if (ce != cudaSuccess) {
         destroy(h);
         return fail(MHS_ECUDA, "setup copy failed: %s", cudaGetErrorString(ce));
@@ -427,17 +459,19 @@ mhs_status finish_load(mhs_instance *h, int64_t tmap_off) {
     const bool dense = h->contraction == kFp8;
     if (dense) {
         CUDA_TRY(prepare_tc_contract());
-        std::vector<uint8_t> maps(tmap_bytes() * 2 * h->count);
+        const size_t mb = tmap_bytes() * 2 * h->count;
+        // one instance: staged in its pinned block; a batch: a local vector
+        const bool pinned = mb <= kPinnedBlock - 256;
+        std::vector<uint8_t> local(pinned ? 0 : mb);
+        uint8_t *maps = pinned ? h->pin + 256 : local.data();
         for (int b = 0; b < h->count; ++b) {
             const InstState &s = h->hstate[b];
-            if (!make_operand_tmap(maps.data() + tmap_bytes() * 2 * b, s.A, s.A_pitch, s.A_rows) ||
-                !make_operand_tmap(maps.data() + tmap_bytes() * (2 * b + 1), s.At, s.At_pitch,
-                                   s.At_rows))
+            if (!make_operand_tmap(maps + tmap_bytes() * 2 * b, s.A, s.A_pitch, s.A_rows) ||
+                !make_operand_tmap(maps + tmap_bytes() * (2 * b + 1), s.At, s.At_pitch, s.At_rows))
                 return fail(MHS_ECUDA, "cuTensorMapEncodeTiled failed for instance %d", b);
         }
-        CUDA_TRY(cudaMemcpyAsync(h->arena + tmap_off, maps.data(), maps.size(),
-                                 cudaMemcpyHostToDevice, h->stream));
-        CUDA_TRY(cudaStreamSynchronize(h->stream));  // `maps` is pageable and local
+        CUDA_TRY(cudaMemcpyAsync(h->arena + tmap_off, maps, mb, cudaMemcpyHostToDevice, h->stream));
+        if (!pinned) CUDA_TRY(cudaStreamSynchronize(h->stream));  // `local` goes out of scope
     }
     CUDA_TRY(cudaMemcpyAsync(h->dstate, h->hstate.data(), sizeof(InstState) * h->count,
                              cudaMemcpyHostToDevice, h->stream));
@@ -728,9 +762,7 @@ mhs_status mhs_load_device(int32_t n, int32_t m, const int32_t *edge_ptr, const 
         return fail(MHS_EINVAL, "malformed device instance (status 0x%x: %s)", status,
                     status_text(status));
     }
-    st = finish_load(h, tmoff);
-    if (st == MHS_OK && cudaStreamSynchronize(h->stream) != cudaSuccess)
-        st = fail(MHS_ECUDA, "load failed");
+    st = finish_load(h, tmoff);  // device inputs: nothing to wait for before returning
     if (st) {
         destroy(h);
         return st;
