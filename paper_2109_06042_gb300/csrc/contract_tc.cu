@@ -299,9 +299,10 @@ __device__ __forceinline__ int32_t kit_next(KIter &k) {
 }
 
 // Build this phase's tile list: every tile of the upper triangle (in the
-// grouped order of tc_tile_coords) that shares a nonzero K block -- and, in
-// a DP pass of an instance with a hyperedge f > |e|, every tile, since zero
-// counts can then supersede.  Zero tiles otherwise change nothing: in DP a
+// grouped order of tc_tile_coords) that holds a candidate row or column
+// (incremental rounds) and shares a nonzero K block -- or, in a DP pass of
+// an instance with a hyperedge f > |e|, every such tile, since zero counts
+// can then supersede.  Zero tiles otherwise change nothing: in DP a
 // zero count supersedes only from a hyperedge with f > |e|, and in MD a
 // zero count only adds dominators of a vertex in no hyperedge, which is
 // deleted anyway (its maximum demand is 0).  Warp-aggregated appends keep
@@ -336,12 +337,20 @@ __global__ void k_tile_list(InstState *st, Plan *plan, int phase) {
             } else {
                 tc_tile_coords(t - plan->tile_off[lo], ti.R, G, &ti.bi, &ti.bj);
             }
-            if ((phase == 0 && s.has_loose) || s.no_skip) {
-                keep = true;
+            if (s.no_skip) {
+                keep = true;  // the dense formulation: every tile, every round
             } else {
-                KIter k;
-                kit_init(k, s, phase, ti);
-                keep = kit_next(k) >= 0;
+                // only tiles that hold a candidate row (incremental rounds) ...
+                const uint8_t *drb = phase == 0 ? s.e_dirty_rb : s.v_dirty_rb;
+                const int32_t r0 = kPair ? 2 * ti.bp : ti.bi;
+                keep = !drb || (phase == 1 && s.md_full) || drb[r0] || (kPair && drb[r0 + 1]) ||
+                       drb[2 * ti.bj] || drb[2 * ti.bj + 1];
+                // ... and share a nonzero K block, unless zero counts matter
+                if (keep && !(phase == 0 && s.has_loose)) {
+                    KIter k;
+                    kit_init(k, s, phase, ti);
+                    keep = kit_next(k) >= 0;
+                }
             }
             packed = pack_tile(lo, ti.bi, ti.bj);
         }

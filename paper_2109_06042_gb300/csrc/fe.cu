@@ -145,6 +145,7 @@ __global__ void __launch_bounds__(1024) k_fe_compact(InstState *st, int count, B
             atomicSub(&ctr->m_alive, m - m2);
             atomicSub(&ctr->n_alive, n - n2);
         }
+        if (changed) s.md_full = 1;  // lowered demands change maxf of untouched vertices too
         if (!changed) {
             s.active = 0;
             if (ctr) {
@@ -155,12 +156,14 @@ __global__ void __launch_bounds__(1024) k_fe_compact(InstState *st, int count, B
             atomicOr(&ctr->changed_any, 1);
         }
     }
-    if (changed) {  // hyperedge rows of the next round's DP pass
+    if (changed) {  // hyperedge rows of the next round's DP pass, all candidates
         for (int32_t r = threadIdx.x; r < m2; r += blockDim.x) {
             s.e_f[r] = s.f[s.e_c2o[r]];
-            s.e_s[r] = 0;
+            s.e_s[r] = -1;
             s.e_del[r] = 0;
         }
+        if (s.e_dirty_rb)
+            for (int32_t w = threadIdx.x; w < (m2 + 127) / 128; w += blockDim.x) s.e_dirty_rb[w] = 0;
         if (s.occ[0]) {
             const int64_t words = (int64_t)((m2 + 255) / 256) * 2 * s.occ_words[0];
             for (int64_t w = threadIdx.x; w < words; w += blockDim.x) s.occ[0][w] = 0;

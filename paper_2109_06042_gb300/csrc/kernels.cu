@@ -152,12 +152,18 @@ __global__ void k_init(InstState *st, int count, int32_t max_rounds) {
     }
     if (s.forced)
         for (int32_t v = threadIdx.x; v < s.n0; v += blockDim.x) s.forced[v] = 0;
+    if (s.v_dirty)
+        for (int32_t v = threadIdx.x; v < s.n0; v += blockDim.x) s.v_dirty[v] = 0;
+    if (s.v_dirty_rb)
+        for (int32_t w = threadIdx.x; w < s.At_rows / 128; w += blockDim.x) s.v_dirty_rb[w] = 0;
+    if (s.e_dirty_rb)
+        for (int32_t w = threadIdx.x; w < s.A_rows / 128; w += blockDim.x) s.e_dirty_rb[w] = 0;
     zero_occupancy(s, 0, s.m0);
     if (threadIdx.x == 0) {
         s.n = s.n0; s.m = s.m0; s.m_dp = s.m0; s.n_next = s.n0;
         s.rounds = 0; s.active = s.status == 0; s.max_rounds = max_rounds; s.changed = 0;
         s.dp_deleted = 0; s.md_deleted = 0; s.has_loose = 0;
-        s.fe_stage = 0; s.fe_passes = 0;
+        s.fe_stage = 0; s.fe_passes = 0; s.md_full = 1;
     }
 }
 
@@ -220,7 +226,7 @@ __global__ void k_edge_rows(InstState *st, int count) {
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < s.m0;
          r += (int64_t)gridDim.x * blockDim.x) {
         s.e_f[r] = s.f[s.e_c2o[r]];
-        s.e_s[r] = 0;
+        s.e_s[r] = -1;  // never tested: every hyperedge is a DP candidate
         s.e_del[r] = 0;
     }
 }
@@ -298,9 +304,16 @@ __global__ void k_scatter(InstState *st, const Plan *plan) {
         const int32_t R = kPhase == 0 ? s.m : s.n;
         const int32_t K = kPhase == 0 ? s.n : s.m_dp;
         int32_t fresh_cnt = 0;
+        // phase 0 clear: a hyperedge this DP pass deleted makes its vertices
+        // MD candidates of this round
+        const bool mark_v = kPhase == 0 && !kSet && s.v_dirty && s.e_del[ce];
         for (int32_t p = s.eptr[e]; p < s.eptr[e + 1]; ++p) {
             const int32_t cv = s.v_o2c[s.evtx[p]];
             if (cv < 0) continue;
+            if (mark_v && cv < s.n) {
+                s.v_dirty[cv] = 1;
+                s.v_dirty_rb[cv >> 7] = 1;
+            }
             const int32_t r = kPhase == 0 ? ce : cv;
             const int32_t c = kPhase == 0 ? cv : ce;
             if (r >= R || c >= K) { atomicOr(&s.status, kErrCapacity); continue; }
@@ -341,6 +354,9 @@ __global__ void k_scatter(InstState *st, const Plan *plan) {
             }
         }
         if (kSet && kPhase == 0) {
+            // a hyperedge whose size changed since the previous DP pass (or
+            // never tested) makes its row block a DP candidate
+            if (s.e_dirty_rb && s.e_s[ce] != fresh_cnt) s.e_dirty_rb[ce >> 7] = 1;
             s.e_s[ce] = fresh_cnt;  // one thread owns the row
             // a count of 0 decides a pair only from a hyperedge with f > |e|
             // (DP) or an empty one (SE)
@@ -364,13 +380,16 @@ __global__ void k_compact_edges(InstState *st, int count) {
     int32_t carry = 0;
     for (int32_t base = 0; base < m; base += blockDim.x) {
         int32_t r = base + threadIdx.x;
-        int32_t keep = 0, orig = -1;
-        if (r < m) { keep = s.e_del[r] == 0; orig = s.e_c2o[r]; }
+        int32_t keep = 0, orig = -1, size = 0;
+        if (r < m) { keep = s.e_del[r] == 0; orig = s.e_c2o[r]; size = s.e_s[r]; }
         int32_t tot;
         int32_t ex = block_exclusive_scan<int32_t>(keep, &tot, sh);  // syncs after reads
         if (r < m) {
             s.e_o2c[orig] = keep ? carry + ex : -1;
-            if (keep) s.e_c2o[carry + ex] = orig;
+            if (keep) {
+                s.e_c2o[carry + ex] = orig;
+                s.e_s[carry + ex] = size;  // the size this DP pass saw moves with the row
+            }
         }
         carry += tot;
         __syncthreads();
@@ -408,7 +427,14 @@ __global__ void k_compact_vertices(InstState *st, int count, BatchCounters *ctr,
         for (int32_t base = 0; base < n; base += blockDim.x) {
             int32_t r = base + threadIdx.x;
             int32_t keep = 0, orig = -1;
-            if (r < n) { keep = s.v_cnt[r] < s.v_maxf[r]; orig = s.v_c2o[r]; s.v_del[r] = !keep; }
+            if (r < n) {
+                // a vertex that lost no hyperedge since it last survived MD
+                // survives again: its dominator count can only have dropped
+                const bool cand = s.md_full || !s.v_dirty || s.v_dirty[r];
+                keep = !cand || s.v_cnt[r] < s.v_maxf[r];
+                orig = s.v_c2o[r];
+                s.v_del[r] = !keep;
+            }
             int32_t tot;
             int32_t ex = block_exclusive_scan<int32_t>(keep, &tot, sh);
             if (r < n) {
@@ -425,6 +451,7 @@ __global__ void k_compact_vertices(InstState *st, int count, BatchCounters *ctr,
             s.m = s.m_dp;
             s.n = carry;
             s.rounds += 1;
+            s.md_full = 0;
             if (!s.changed && s.full_edges && s.max_rounds == 0) {
                 s.fe_stage = 1;  // fixpoint: rule FE decides (fe.cu) whether it goes on
             } else if (!s.changed || (s.max_rounds > 0 && s.rounds >= s.max_rounds)) {
@@ -435,13 +462,20 @@ __global__ void k_compact_vertices(InstState *st, int count, BatchCounters *ctr,
         __syncthreads();
         if (s.fe_stage)  // FE marks the vertices it takes here
             for (int32_t r = threadIdx.x; r < s.n; r += blockDim.x) s.v_del[r] = 0;
-        // hyperedge rows of the next round's DP pass
+        if (s.v_dirty) {  // MD candidates of the next round start empty
+            for (int32_t r = threadIdx.x; r < s.n; r += blockDim.x) s.v_dirty[r] = 0;
+            for (int32_t w = threadIdx.x; w < (s.n + 127) / 128; w += blockDim.x)
+                s.v_dirty_rb[w] = 0;
+        }
+        // hyperedge rows of the next round's DP pass (e_s keeps the sizes)
         if (s.active) {
             for (int32_t r = threadIdx.x; r < s.m; r += blockDim.x) {
                 s.e_f[r] = s.f[s.e_c2o[r]];
-                s.e_s[r] = 0;
                 s.e_del[r] = 0;
             }
+            if (s.e_dirty_rb)
+                for (int32_t w = threadIdx.x; w < (s.m + 127) / 128; w += blockDim.x)
+                    s.e_dirty_rb[w] = 0;
             zero_occupancy(s, 0, s.m);
             if (threadIdx.x == 0) s.has_loose = 0;
         }
@@ -497,6 +531,10 @@ __global__ void __launch_bounds__(256) k_pop_contract(InstState *st, const Plan 
         int32_t ti, tj;
         tri_tile(local, nt, &ti, &tj);
         const int32_t i0 = ti * kPopTile, j0 = tj * kPopTile;
+        {  // incremental rounds: only tiles that hold a candidate row or column
+            const uint8_t *drb = phase == 0 ? s.e_dirty_rb : s.v_dirty_rb;
+            if (drb && !(phase == 1 && s.md_full) && !drb[i0 >> 7] && !drb[j0 >> 7]) continue;
+        }
         int32_t acc[4][4];
 #pragma unroll
         for (int a = 0; a < 4; ++a)

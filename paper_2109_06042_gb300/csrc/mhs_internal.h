@@ -78,6 +78,15 @@ struct InstState {
     int32_t *v_cnt;        // C_j of Algorithm 2                         [n0 + 1]
     uint8_t *e_del;        // DP deletion flags
     uint8_t *v_del;        // MD deletion flags
+    // Incremental rounds.  After the first round, a pass can only delete
+    // through an item that changed since the previous pass of its kind: a
+    // hyperedge that lost a vertex (DP), or a vertex that lost a hyperedge
+    // (MD).  e_s keeps each hyperedge's size from the previous DP pass
+    // (-1: never tested).  NULL arrays mean every row is a candidate.
+    uint8_t *e_dirty_rb;   // per 128 hyperedge rows: some row changed (DP pass)
+    uint8_t *v_dirty;      // per current vertex: lost a hyperedge in this round's DP
+    uint8_t *v_dirty_rb;   // per 128 vertex rows: some v_dirty set
+    int32_t md_full;       // 1: every vertex is an MD candidate (first round, after FE)
 
     // dense FP8 operands: rows x pitch bytes (0x38 = 1.0 in E4M3)
     uint8_t *A;            // rows = current hyperedges, K = current vertices
