@@ -78,10 +78,15 @@ typedef enum {
 /* Order of the rows (and K columns) of the dense operands.  Results never
  * depend on it (ties are broken by input index); performance does. */
 typedef enum {
-    MHS_LAYOUT_AUTO = 0,    /* library choice (currently MHS_LAYOUT_SORTED) */
+    MHS_LAYOUT_AUTO = 0,    /* library choice (currently MHS_LAYOUT_DEGREE) */
     MHS_LAYOUT_INPUT = 1,   /* input order */
-    MHS_LAYOUT_SORTED = 2   /* hyperedges by their smallest vertex id: interval-like
+    MHS_LAYOUT_SORTED = 2,  /* hyperedges by their smallest vertex id: interval-like
                                (low Dilworth number) inputs become banded */
+    MHS_LAYOUT_DEGREE = 3   /* vertices grouped by degree class floor(log4 deg), ascending,
+                               input order inside a class; hyperedges by their smallest
+                               vertex position, i.e. by their rarest vertex.  Skewed degrees
+                               then concentrate the nonzero blocks; near-uniform degrees keep
+                               the input order and its locality */
 } mhs_layout;
 
 /* Block-sparse skipping in the tcgen05 contraction.  Exact either way: a

@@ -17,6 +17,11 @@ mhs_status set_error(mhs_status st, const char *fmt, ...);
 // kept for reuse, so load/free loops do not reach the driver).
 cudaError_t pool_for(int dev, cudaMemPool_t *out);
 
+// InstState::layout_sorted for an mhs_layout option.
+inline int32_t layout_code(int32_t layout) {
+    return layout == MHS_LAYOUT_INPUT ? 0 : layout == MHS_LAYOUT_SORTED ? 1 : 2;
+}
+
 // Blocks of kPinnedBlock bytes of page-locked host memory from a
 // process-wide slab.  cudaMallocHost / cudaFreeHost cost tens of
 // microseconds and cudaFreeHost synchronises the device, which every

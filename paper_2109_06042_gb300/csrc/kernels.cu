@@ -145,6 +145,8 @@ __global__ void k_init(InstState *st, int count, int32_t max_rounds) {
     if (b >= count) return;
     InstState &s = st[b];
     for (int32_t v = threadIdx.x; v < s.n0; v += blockDim.x) { s.v_o2c[v] = v; s.v_c2o[v] = v; }
+    if (s.layout_sorted == 2)  // degrees for the vertex layout (v_maxf is free until MD)
+        for (int32_t v = threadIdx.x; v < s.n0; v += blockDim.x) s.v_maxf[v] = 0;
     if (s.layout_sorted) {
         for (int32_t v = threadIdx.x; v <= s.n0; v += blockDim.x) { s.v_cnt[v] = 0; s.v_deg[v] = 0; }
     } else {
@@ -167,17 +169,84 @@ __global__ void k_init(InstState *st, int count, int32_t max_rounds) {
     }
 }
 
-// Sorted layout, step 1 (blockIdx.y = instance): key of each hyperedge =
-// its smallest vertex id (n0 if empty), kept in e_s; bucket counts in v_cnt.
+// Degree layout, step 1 (blockIdx.y = instance): vertex degrees into v_maxf.
+__global__ void k_vertex_degrees(InstState *st, int count) {
+    const int b = blockIdx.y;
+    if (b >= count) return;
+    InstState &s = st[b];
+    if (s.layout_sorted != 2 || s.status) return;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < s.nnz0;
+         p += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&s.v_maxf[s.evtx[p]], 1);
+}
+
+// Degree layout, step 2 (one block of 1024 threads per instance): vertices
+// grouped by degree class floor(log4(deg)) in ascending order, input order
+// inside a class (a stable counting sort).  With skewed degrees, sorting
+// hyperedges by their smallest position then places each hyperedge by its
+// rarest vertex: the rows of a row block share rare vertices, and their
+// popular vertices fall in the few K blocks at the end, so far fewer
+// (row block, K block) pairs are occupied.  Near-uniform degrees keep the
+// input order (one or two classes), and with it any locality.
+constexpr int kDegClasses = 16;
+__device__ __forceinline__ int deg_class(int32_t d) {
+    return d <= 1 ? 0 : min((31 - __clz(d)) / 2, kDegClasses - 1);
+}
+__global__ void __launch_bounds__(1024) k_vertex_layout(InstState *st, int count) {
+    __shared__ int32_t start[kDegClasses];
+    __shared__ int32_t wcnt[32][kDegClasses];  // this chunk: per warp, per class
+    const int b = blockIdx.x;
+    if (b >= count) return;
+    InstState &s = st[b];
+    if (s.layout_sorted != 2 || s.status) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x < kDegClasses) start[threadIdx.x] = 0;
+    __syncthreads();
+    for (int32_t v = threadIdx.x; v < s.n0; v += blockDim.x) atomicAdd(&start[deg_class(s.v_maxf[v])], 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {  // exclusive prefix over the classes
+        int32_t acc = 0;
+        for (int c = 0; c < kDegClasses; ++c) { const int32_t x = start[c]; start[c] = acc; acc += x; }
+    }
+    __syncthreads();
+    for (int32_t base = 0; base < s.n0; base += blockDim.x) {
+        const int32_t v = base + threadIdx.x;
+        const int c = v < s.n0 ? deg_class(s.v_maxf[v]) : -1;
+        const uint32_t peers = __match_any_sync(0xffffffffu, c);
+        const int rank = __popc(peers & ((1u << lane) - 1u));
+        if (lane < kDegClasses) wcnt[warp][lane] = 0;
+        __syncwarp();
+        if (c >= 0 && rank == 0) wcnt[warp][c] = __popc(peers);
+        __syncthreads();
+        if (threadIdx.x < kDegClasses) {  // per class: prefix over the warps, then advance
+            int32_t acc = start[threadIdx.x];
+            for (int w = 0; w < 32; ++w) { const int32_t x = wcnt[w][threadIdx.x]; wcnt[w][threadIdx.x] = acc; acc += x; }
+            start[threadIdx.x] = acc;
+        }
+        __syncthreads();
+        if (c >= 0) {
+            const int32_t pos = wcnt[warp][c] + rank;
+            s.v_c2o[pos] = v;
+            s.v_o2c[v] = pos;
+        }
+        __syncthreads();
+    }
+}
+
+// Sorted layouts, step 1 (blockIdx.y = instance): key of each hyperedge =
+// its smallest vertex id (layout 1) or position (layout 2), n0 if empty,
+// kept in e_s; bucket counts in v_cnt.
 __global__ void k_layout_keys(InstState *st, int count) {
     const int b = blockIdx.y;
     if (b >= count) return;
     InstState &s = st[b];
     if (!s.layout_sorted || s.status) return;
+    const bool by_pos = s.layout_sorted == 2;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < s.m0;
          e += (int64_t)gridDim.x * blockDim.x) {
         int32_t key = s.n0;
-        for (int32_t p = s.eptr[e]; p < s.eptr[e + 1]; ++p) key = min(key, s.evtx[p]);
+        for (int32_t p = s.eptr[e]; p < s.eptr[e + 1]; ++p)
+            key = min(key, by_pos ? s.v_o2c[s.evtx[p]] : s.evtx[p]);
         s.e_s[e] = key;
         atomicAdd(&s.v_cnt[key], 1);
     }
@@ -689,12 +758,16 @@ cudaError_t launch_gather_bounds(const int64_t *gptr, const int64_t *e0, int64_t
 
 cudaError_t launch_build(InstState *st, int count, int32_t max_rounds, int64_t max_nnz,
                          int64_t max_m, int64_t max_n, cudaStream_t s) {
-    (void)max_nnz;
     (void)max_n;
     int gx = (int)((max_m + 255) / 256);
     if (gx > 256) gx = 256;
     if (gx < 1) gx = 1;
+    int gz = (int)((max_nnz + 255) / 256);
+    if (gz > 256) gz = 256;
+    if (gz < 1) gz = 1;
     k_init<<<count, 1024, 0, s>>>(st, count, max_rounds);
+    k_vertex_degrees<<<dim3(gz, count), 256, 0, s>>>(st, count);
+    k_vertex_layout<<<count, 1024, 0, s>>>(st, count);
     k_layout_keys<<<dim3(gx, count), 256, 0, s>>>(st, count);
     k_layout_scan<<<count, 1024, 0, s>>>(st, count);
     k_layout_place<<<dim3(gx, count), 256, 0, s>>>(st, count);

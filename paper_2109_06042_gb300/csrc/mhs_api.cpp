@@ -188,8 +188,9 @@ mhs_status check_options(const mhs_options *opt, mhs_options *out) {
     if (out->contraction < 0 || out->contraction > 2)
         return fail(MHS_EINVAL, "options.contraction must be 0 (auto), 1 (fp8) or 2 (popcount)");
     if (out->max_rounds < 0) return fail(MHS_EINVAL, "options.max_rounds must be >= 0");
-    if (out->layout < 0 || out->layout > 2)
-        return fail(MHS_EINVAL, "options.layout must be 0 (auto), 1 (input) or 2 (sorted)");
+    if (out->layout < 0 || out->layout > 3)
+        return fail(MHS_EINVAL,
+                    "options.layout must be 0 (auto), 1 (input), 2 (sorted) or 3 (degree)");
     if (out->sparsity < 0 || out->sparsity > 2)
         return fail(MHS_EINVAL, "options.sparsity must be 0 (auto), 1 (skip) or 2 (dense)");
     if (out->edge_rule < 0 || out->edge_rule > 1)
@@ -393,7 +394,7 @@ mhs_status create(int32_t count, const int32_t *n, const int32_t *m, const int64
         s.m0 = m[b];
         s.nnz0 = nnz[b];
         s.k = k[b];
-        s.layout_sorted = opt.layout != MHS_LAYOUT_INPUT;
+        s.layout_sorted = layout_code(opt.layout);
         s.no_skip = opt.sparsity == MHS_SPARSITY_DENSE;
         s.edge_rule = opt.edge_rule;
         s.full_edges = opt.full_edges;

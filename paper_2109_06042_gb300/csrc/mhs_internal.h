@@ -7,8 +7,9 @@
 //
 // Ids.  "Original" ids are the input ids.  "Current" ids (positions) number
 // the items still alive in the layout order of the dense operands: input
-// order, or hyperedges sorted by smallest vertex id.  Compaction preserves
-// the layout order.  The lowest-index tie-breaks of Algorithms 1 and 2
+// order; hyperedges sorted by smallest vertex id; or vertices grouped by
+// degree class and hyperedges sorted by smallest vertex position.
+// Compaction preserves the layout order.  The lowest-index tie-breaks of Algorithms 1 and 2
 // always compare ORIGINAL ids (e_c2o / v_c2o), so results do not depend on
 // the layout.
 #pragma once
@@ -64,7 +65,8 @@ struct InstState {
     int32_t changed;       // last round deleted something
     int32_t dp_deleted, md_deleted;
     int32_t status;        // kErr* bits
-    int32_t layout_sorted; // 1: hyperedge rows ordered by smallest vertex id
+    int32_t layout_sorted; // 0: input order; 1: hyperedges by smallest vertex id;
+                           // 2: vertices by degree class, hyperedges by smallest vertex position
 
     // id maps (capacity n0 / m0)
     int32_t *v_o2c, *v_c2o;

@@ -198,7 +198,7 @@ mhs_status admit(Lane &Ln, int si, std::shared_ptr<Request> req) {
     s.m0 = req->m;
     s.nnz0 = nnz;
     s.k = req->k;
-    s.layout_sorted = S->opt.layout != MHS_LAYOUT_INPUT;
+    s.layout_sorted = layout_code(S->opt.layout);
     s.no_skip = S->opt.sparsity == MHS_SPARSITY_DENSE;
     s.edge_rule = S->opt.edge_rule;
     s.full_edges = S->opt.full_edges;
@@ -597,7 +597,8 @@ mhs_status mhs_server_create(const mhs_server_options *opt_in, void *cuda_stream
     if (opt.contraction < 0 || opt.contraction > 2)
         return set_error(MHS_EINVAL, "contraction must be 0, 1 or 2");
     if (opt.hbm_budget_bytes < 0) return set_error(MHS_EINVAL, "hbm_budget_bytes must be >= 0");
-    if (opt.layout < 0 || opt.layout > 2) return set_error(MHS_EINVAL, "layout must be 0, 1 or 2");
+    if (opt.layout < 0 || opt.layout > 3)
+        return set_error(MHS_EINVAL, "layout must be 0, 1, 2 or 3");
     if (opt.sparsity < 0 || opt.sparsity > 2)
         return set_error(MHS_EINVAL, "sparsity must be 0, 1 or 2");
     if (opt.edge_rule < 0 || opt.edge_rule > 1)

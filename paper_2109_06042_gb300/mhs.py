@@ -32,7 +32,7 @@ class MhsError(RuntimeError):
         self.status = status
 
 
-LAYOUTS = {"auto": 0, "input": 1, "sorted": 2}
+LAYOUTS = {"auto": 0, "input": 1, "sorted": 2, "degree": 3}
 SPARSITY = {"auto": 0, "skip": 1, "dense": 2}
 RULES = {"dp": 0, "se": 1}
 

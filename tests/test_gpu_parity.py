@@ -311,11 +311,12 @@ def test_bounded_wait_times_out_and_context_survives(mhs):
 
 
 @pytest.mark.parametrize("mode", MODES)
-@pytest.mark.parametrize("layout", ["input", "sorted"])
+@pytest.mark.parametrize("layout", ["input", "sorted", "degree"])
 def test_layouts_and_tie_breaks(mhs, mode, layout):
-    """Rows in input order or sorted by smallest vertex: the lowest-index
-    tie-breaks compare input ids, so the result is the same either way.
-    Tiny instances carry duplicate hyperedges and twin vertices."""
+    """Rows in input order, hyperedges sorted by smallest vertex, or vertices
+    grouped by degree class: the lowest-index tie-breaks compare input ids,
+    so the result is the same either way.  Tiny instances carry duplicate
+    hyperedges and twin vertices; the power-law ones skewed degrees."""
     for seed in range(300):
         inst = I.tiny_random(seed, nmax=24, mmax=30)
         _same(mhs.kernelize(inst, contraction=mode, layout=layout), O.reduce(inst),
@@ -324,6 +325,9 @@ def test_layouts_and_tie_breaks(mhs, mode, layout):
         inst = I.config_interval(seed, n=3000, m=6000)
         _same(mhs.kernelize(inst, contraction=mode, layout=layout), O.reduce(inst),
               f"{layout} interval {seed}")
+        inst = I.config_powerlaw(seed, n=3000, m=6000)
+        _same(mhs.kernelize(inst, contraction=mode, layout=layout), O.reduce(inst),
+              f"{layout} powerlaw {seed}")
 
 
 @pytest.mark.parametrize("sparsity", ["skip", "dense"])

@@ -109,7 +109,7 @@ def test_powerlaw_full_size(mhs, rule, fe):
 
 
 def test_interval_medium_layouts(mhs):
-    for layout in ("input", "sorted"):
+    for layout in ("input", "sorted", "degree"):
         for rule, fe in VARIANTS:
             inst = I.config_interval(2, n=6000, m=12000)
             _same(_run(mhs, inst, "fp8", rule, fe, layout=layout),
