@@ -105,6 +105,69 @@ void mhs::pinned_release(void *p) {
 }
 
 namespace {
+// Dense operand regions that are known to be all zero, kept for reuse by
+// later loads of similar size.  Every phase clears exactly the incidences it
+// set, so an instance that finished without a device error leaves its
+// operands all zero; a load that reuses them skips the memset (the largest
+// fixed cost of a load: 1.6 GB for the 20,000 x 40,000 power-law instance).
+struct ZeroBlock {
+    int dev;
+    uint8_t *p;
+    int64_t bytes;
+};
+std::mutex g_zero_mu;
+std::vector<ZeroBlock> g_zero;
+constexpr int64_t kZeroCacheBytes = 16ll << 30;
+
+uint8_t *zero_take(int dev, int64_t bytes) {
+    std::lock_guard<std::mutex> lk(g_zero_mu);
+    for (size_t i = 0; i < g_zero.size(); ++i) {
+        const ZeroBlock &z = g_zero[i];
+        if (z.dev == dev && z.bytes >= bytes && z.bytes <= bytes + bytes / 4) {
+            uint8_t *p = z.p;
+            g_zero.erase(g_zero.begin() + (long)i);
+            return p;
+        }
+    }
+    return nullptr;
+}
+
+// Keep an all-zero region (its stream has been synchronised); the oldest go
+// back to the pool beyond the cache's budget.
+void zero_put(int dev, uint8_t *p, int64_t bytes) {
+    std::vector<uint8_t *> drop;
+    {
+        std::lock_guard<std::mutex> lk(g_zero_mu);
+        g_zero.push_back({dev, p, bytes});
+        int64_t total = 0;
+        for (const ZeroBlock &z : g_zero) total += z.bytes;
+        while (total > kZeroCacheBytes && !g_zero.empty()) {
+            total -= g_zero.front().bytes;
+            drop.push_back(g_zero.front().p);
+            g_zero.erase(g_zero.begin());
+        }
+    }
+    for (uint8_t *q : drop) cudaFreeAsync(q, nullptr);
+}
+
+// Return every cached region of a device to the pool (before retrying an
+// allocation that failed).
+void zero_flush(int dev) {
+    std::vector<uint8_t *> drop;
+    {
+        std::lock_guard<std::mutex> lk(g_zero_mu);
+        for (size_t i = 0; i < g_zero.size();) {
+            if (g_zero[i].dev == dev) {
+                drop.push_back(g_zero[i].p);
+                g_zero.erase(g_zero.begin() + (long)i);
+            } else {
+                ++i;
+            }
+        }
+    }
+    for (uint8_t *q : drop) cudaFreeAsync(q, nullptr);
+    if (!drop.empty()) cudaDeviceSynchronize();
+}
 
 // Sub-allocation plan of one arena.
 struct Arena {
@@ -148,7 +211,11 @@ struct mhs_instance {
     // arena offsets of the batch-wide input arrays
     int64_t in_eptr = 0, in_evtx = 0, in_f = 0;
     int64_t sum_m1 = 0, sum_nnz = 0, sum_m = 0;
-    int64_t dense_off = 0, dense_bytes = 0;
+    // dense operands: a separate allocation, reusable when known all zero
+    uint8_t *dense = nullptr;
+    int64_t dense_bytes = 0;
+    bool dense_zeroed = false;  // taken all-zero from the cache or memset at load
+    bool faulted = false;       // a device error was seen: the operands may be dirty
     // round graphs: graph[0] plain, graph[1] with timing events
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     // the whole fixpoint: a conditional WHILE node whose body is one round
@@ -176,6 +243,11 @@ void destroy(mhs_instance *h) {
     for (auto &e : h->ev)
         if (e) cudaEventDestroy(e);
     if (h->arena) cudaFreeAsync(h->arena, h->stream);  // stream-ordered
+    if (h->dense) {
+        const bool clean = h->dense_zeroed && !h->faulted && (!h->hkerr || *h->hkerr == 0);
+        if (clean) zero_put(h->device, h->dense, h->dense_bytes);
+        else cudaFreeAsync(h->dense, h->stream);
+    }
     pinned_release(h->pin);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
@@ -325,26 +397,26 @@ mhs_status create(int32_t count, const int32_t *n, const int32_t *m, const int64
         tiles_dp += tc_tiles((int32_t)m0);
         tiles_md += tc_tiles((int32_t)n0);
     }
-    // the operands of all instances, contiguous, zeroed once at load: the
-    // scatter/clear passes leave them all-zero between phases
-    const int64_t off_dense0 = ar.bytes;
+    // the operands of all instances, contiguous in their own allocation,
+    // all zero at load: the scatter/clear passes leave them all-zero between
+    // phases
+    Arena ad;
     for (int b = 0; b < count; ++b) {
         Layout &L = lay[b];
         const int64_t n0 = n[b], m0 = m[b];
         const int64_t arows = round_up(std::max<int64_t>(m0, 1), kRowAlign);
         const int64_t atrows = round_up(std::max<int64_t>(n0, 1), kRowAlign);
         if (dense) {
-            L.A = ar.take(arows * kpad_bytes(n0));
-            L.At = ar.take(atrows * kpad_bytes(m0));
+            L.A = ad.take(arows * kpad_bytes(n0));
+            L.At = ad.take(atrows * kpad_bytes(m0));
             L.Ab = L.Atb = -1;
         } else {
-            L.Ab = ar.take(arows * kpad_words(n0) * 4);
-            L.Atb = ar.take(atrows * kpad_words(m0) * 4);
+            L.Ab = ad.take(arows * kpad_words(n0) * 4);
+            L.Atb = ad.take(atrows * kpad_words(m0) * 4);
             L.A = L.At = -1;
         }
     }
-    h->dense_off = off_dense0;
-    h->dense_bytes = ar.bytes - off_dense0;
+    h->dense_bytes = ad.bytes;
     // batch-level objects
     const int64_t off_state = ar.take((int64_t)sizeof(InstState) * count);
     const int64_t off_plan = ar.take(sizeof(Plan));
@@ -359,16 +431,28 @@ mhs_status create(int32_t count, const int32_t *n, const int32_t *m, const int64
 
     cudaMemPool_t pool;
     cudaError_t ce = pool_for(h->device, &pool);
-    if (ce == cudaSuccess)
-        ce = cudaMallocFromPoolAsync(reinterpret_cast<void **>(&h->arena), (size_t)ar.bytes, pool,
-                                     h->stream);
+    h->dense = zero_take(h->device, h->dense_bytes);
+    h->dense_zeroed = h->dense != nullptr;
+    for (int attempt = 0; attempt < 2 && ce == cudaSuccess; ++attempt) {
+        if (!h->arena)
+            ce = cudaMallocFromPoolAsync(reinterpret_cast<void **>(&h->arena), (size_t)ar.bytes,
+                                         pool, h->stream);
+        if (ce == cudaSuccess && !h->dense)
+            ce = cudaMallocFromPoolAsync(reinterpret_cast<void **>(&h->dense),
+                                         (size_t)h->dense_bytes, pool, h->stream);
+        if (ce != cudaErrorMemoryAllocation || attempt == 1) break;
+        cudaGetLastError();
+        zero_flush(h->device);  // cached zero regions go back to the pool, then retry
+        ce = cudaSuccess;
+    }
     if (ce != cudaSuccess) {
         destroy(h);
         return fail(ce == cudaErrorMemoryAllocation ? MHS_ENOMEM : MHS_ECUDA,
-                    "device allocation of %lld bytes failed: %s", (long long)ar.bytes,
-                    cudaGetErrorString(ce));
+                    "device allocation of %lld bytes failed: %s",
+                    (long long)(ar.bytes + h->dense_bytes), cudaGetErrorString(ce));
     }
     uint8_t *base = h->arena;
+    uint8_t *dbase = h->dense;
     h->dstate = reinterpret_cast<InstState *>(base + off_state);
     h->dplan = reinterpret_cast<Plan *>(base + off_plan);
     h->dctr = reinterpret_cast<BatchCounters *>(base + off_ctr);
@@ -425,16 +509,16 @@ mhs_status create(int32_t count, const int32_t *n, const int32_t *m, const int64
             s.occ[1] = reinterpret_cast<uint32_t *>(base + L.occ1);
             s.occ_words[0] = (int32_t)occ_words(n[b]);
             s.occ_words[1] = (int32_t)occ_words(m[b]);
-            s.A = base + L.A;
-            s.At = base + L.At;
+            s.A = dbase + L.A;
+            s.At = dbase + L.At;
             s.A_pitch = kpad_bytes(n[b]);
             s.At_pitch = kpad_bytes(m[b]);
             uint8_t *tm = base + off_tmaps + (int64_t)tmap_bytes() * 2 * b;
             s.tmap_A = tm;
             s.tmap_At = tm + tmap_bytes();
         } else {
-            s.Ab = reinterpret_cast<uint32_t *>(base + L.Ab);
-            s.Atb = reinterpret_cast<uint32_t *>(base + L.Atb);
+            s.Ab = reinterpret_cast<uint32_t *>(dbase + L.Ab);
+            s.Atb = reinterpret_cast<uint32_t *>(dbase + L.Atb);
             s.Ab_pitch = (int32_t)kpad_words(n[b]);
             s.Atb_pitch = (int32_t)kpad_words(m[b]);
         }
@@ -483,7 +567,10 @@ mhs_status finish_load(mhs_instance *h, int64_t tmap_off) {
     }
     CUDA_TRY(cudaMemcpyAsync(h->dstate, h->hstate.data(), sizeof(InstState) * h->count,
                              cudaMemcpyHostToDevice, h->stream));
-    CUDA_TRY(cudaMemsetAsync(h->arena + h->dense_off, 0, (size_t)h->dense_bytes, h->stream));
+    if (!h->dense_zeroed) {
+        CUDA_TRY(cudaMemsetAsync(h->dense, 0, (size_t)h->dense_bytes, h->stream));
+        h->dense_zeroed = true;
+    }
     CUDA_TRY(launch_build(h->dstate, h->count, h->opt.max_rounds, h->max_nnz, h->max_m,
                           h->max_n, h->stream));
     return MHS_OK;
@@ -499,9 +586,14 @@ const char *status_text(int32_t st) {
 }
 
 mhs_status check_device_status(mhs_instance *h) {
-    if (*h->hkerr) return fail(MHS_EDEVICE, "kernel reported error status 0x%x", *h->hkerr);
-    if (h->hctr->status_any)
+    if (*h->hkerr) {
+        h->faulted = true;
+        return fail(MHS_EDEVICE, "kernel reported error status 0x%x", *h->hkerr);
+    }
+    if (h->hctr->status_any) {
+        h->faulted = true;
         return fail(MHS_EDEVICE, "instance reported error status 0x%x", h->hctr->status_any);
+    }
     return MHS_OK;
 }
 
@@ -959,12 +1051,16 @@ int32_t mhs_count(const mhs_instance *inst) { return inst ? inst->count : 0; }
 
 mhs_status mhs_reduce_round(mhs_instance *inst, mhs_round_stats *stats) {
     if (!inst) return fail(MHS_EINVAL, "instance is NULL");
-    return run_rounds(inst, 1, stats);
+    const mhs_status st = run_rounds(inst, 1, stats);
+    if (st) inst->faulted = true;  // a round may have stopped half way
+    return st;
 }
 
 mhs_status mhs_kernelize(mhs_instance *inst, mhs_round_stats *stats) {
     if (!inst) return fail(MHS_EINVAL, "instance is NULL");
-    return run_rounds(inst, 0, stats);
+    const mhs_status st = run_rounds(inst, 0, stats);
+    if (st) inst->faulted = true;
+    return st;
 }
 
 mhs_status mhs_result_at(const mhs_instance *inst, int32_t index, int32_t *vtx_out,

@@ -392,3 +392,21 @@ def test_cluster_pair_tiles_in_subprocess(mhs):
     out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
                          timeout=600)
     assert out.returncode == 0 and "pairs ok" in out.stdout, out.stderr[-2000:]
+
+
+def test_reused_operand_regions(mhs):
+    """Dense operand regions return to a zero-state cache when an instance is
+    freed and are reused by later loads without a memset: results must not
+    depend on what used the region before (full runs, runs stopped after one
+    round, other sizes, both contractions)."""
+    insts = [I.config_powerlaw(7, n=3000, m=6000), I.config_uniform(12),
+             I.config_interval(3, n=3000, m=6000)]
+    refs = [O.reduce(i) for i in insts]
+    for rep in range(3):
+        for inst, ref in zip(insts, refs):
+            _same(mhs.kernelize(inst, contraction="fp8"), ref, f"rep {rep}")
+            with mhs.Instance.load(inst, contraction="fp8") as h:
+                h.reduce_round()  # freed between rounds
+            with mhs.Instance.load(inst, contraction="fp8", full_edges=True) as h:
+                h.kernelize()
+            _same(mhs.kernelize(inst, contraction="popcount"), ref, f"rep {rep} popcount")
