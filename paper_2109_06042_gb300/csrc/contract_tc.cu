@@ -21,6 +21,7 @@
 // Every mbarrier wait is bounded: on timeout the kernel records
 // kErrTimeout, stops issuing work, frees its TMEM and returns.
 #include <cuda.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 
@@ -382,6 +383,8 @@ struct __align__(8) SharedCtl {
     int abort;
     float2 colAB[kTcN];  // DP: (f_j, f_j - s_j)   MD: (d_j, 0)
     int32_t colO[kTcN];  // input index of column j (tie-breaks)
+    __half colA16[kTcN];  // colAB as FP16 (exact when |value| <= 1024): the paired fast path
+    __half colB16[kTcN];
     int32_t ccnt[kTcN];
 };
 
@@ -664,6 +667,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             // DP stages f and f - s per hyperedge, SE stages f and s
             const bool se = phase == 0 && s.edge_rule != 0;
             // stage the column data of this tile
+            bool vals_small = true;  // every staged value fits FP16 exactly, with room for a sum
             epi_bar();  // every epilogue thread has read the entry
             if (et == 0) ring_release(it);
             for (int c = et; c < kTcN; c += kEpiThreads) {
@@ -682,6 +686,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 ctl->colAB[c] = make_float2(a, bb);
                 ctl->colO[c] = o;
+                ctl->colA16[c] = __float2half_rn(a);
+                ctl->colB16[c] = __float2half_rn(bb);
+                vals_small = vals_small && fabsf(a) <= 1024.f && fabsf(bb) <= 1024.f;
             }
             float ri_f = 0.f, ri_a = 0.f;  // DP: f_i, f_i - s_i ; SE: f_i, s_i ; MD: d_i
             int32_t ri_o = 0;              // input index of row i
@@ -695,7 +702,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     ri_o = s.v_c2o[i];
                 }
             }
-            epi_bar();
+            vals_small = vals_small && fabsf(ri_f) <= 1024.f && fabsf(ri_a) <= 1024.f;
+            const bool tile_small = epi_bar_and(vals_small);  // also publishes the staged columns
             const bool ok = epi_bar_and(mbar_wait(smem_u32(&ctl->tmem_full[acc]), acc_phase, abort, kWaitNs));
             if (!ok) { *abort = 1; break; }
             tc_fence_after();
@@ -723,12 +731,11 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                         for (int c = 0; c < 32; ++c) v[c] = 0.f;
                     }
-                    if (!zero_matters) {  // skip 32 x 32 blocks of zero counts
-                        uint32_t orv = 0;
+                    float vmax = 0.f;  // counts are >= 0
 #pragma unroll
-                        for (int c = 0; c < 32; ++c) orv |= __float_as_uint(v[c]);
-                        if (!__any_sync(0xffffffffu, orv != 0)) continue;
-                    }
+                    for (int c = 0; c < 32; ++c) vmax = fmaxf(vmax, v[c]);
+                    // skip 32 x 32 blocks of zero counts
+                    if (!zero_matters && !__any_sync(0xffffffffu, vmax > 0.f)) continue;
                     uint32_t colmask = 0;
                     const float2 *cab = ctl->colAB + ch * 32;
                     // Fast path for a chunk whose pairs are all valid (i < j < R for
@@ -738,7 +745,52 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const int32_t jc0 = j0 + ch * 32;
                     const int32_t wi0 = ti.bi * kTcM + 32 * q;  // first row of this warp
                     bool slow = !(wi0 + 31 < R && jc0 + 31 < R && jc0 > wi0 + 31);
-                    if (!slow) {
+                    // Paired form of the fast path: two counts per FP16x2 instruction.
+                    // Counts and staged values up to 1024 and their sums (<= 2048)
+                    // are integers FP16 holds exactly, so every test is exact.
+                    bool paired = !slow && tile_small && __all_sync(0xffffffffu, vmax <= 1024.f);
+                    if (paired) {
+                        const __half2 *ca2 = reinterpret_cast<const __half2 *>(ctl->colA16 + ch * 32);
+                        const __half2 *cb2 = reinterpret_cast<const __half2 *>(ctl->colB16 + ch * 32);
+                        const __half2 rf2 = __float2half2_rn(ri_f), ra2 = __float2half2_rn(ri_a);
+                        // bit k: column 2k, bit 16 + k: column 2k + 1
+                        uint32_t cm = 0, rm = 0, mm = 0;
+#pragma unroll
+                        for (int k = 0; k < 16; ++k) {
+                            const __half2 x2 = __floats2half2_rn(v[2 * k], v[2 * k + 1]);
+                            const __half2 a2 = ca2[k], b2 = cb2[k];
+                            const uint32_t sel = (1u << k) | (1u << (16 + k));
+                            uint32_t mij, mji;
+                            if (phase == 0 && !se) {
+                                mij = __hge2_mask(__hadd2(x2, ra2), a2);  // x + f_i - s_i >= f_j
+                                mji = __hge2_mask(__hadd2(x2, b2), rf2);  // x + f_j - s_j >= f_i
+                            } else if (phase == 0) {
+                                mij = __heq2_mask(x2, ra2) & __hge2_mask(rf2, a2);  // x = s_i, f_i >= f_j
+                                mji = __heq2_mask(x2, b2) & __hge2_mask(a2, rf2);   // x = s_j, f_j >= f_i
+                            } else {
+                                mij = __heq2_mask(x2, a2);   // x = d_j
+                                mji = __heq2_mask(x2, rf2);  // x = d_i
+                            }
+                            cm |= mij & sel;
+                            rm |= mji & sel;
+                            mm |= mij & mji;
+                        }
+                        if (!__any_sync(0xffffffffu, mm != 0)) {
+                            // back to bit c = column c (interleave the two halves)
+                            auto spread = [](uint32_t x) {
+                                x = (x | (x << 8)) & 0x00FF00FFu;
+                                x = (x | (x << 4)) & 0x0F0F0F0Fu;
+                                x = (x | (x << 2)) & 0x33333333u;
+                                return (x | (x << 1)) & 0x55555555u;
+                            };
+                            colmask = spread(cm & 0xFFFFu) | (spread(cm >> 16) << 1);
+                            if (phase == 0) rowflag |= rm != 0;
+                            else rowcnt += __popc(rm);
+                        } else {
+                            slow = true;  // a mutual pair: the tie-breaks decide
+                        }
+                    }
+                    if (!slow && !paired) {
                         uint32_t cm = 0;
                         bool rf = false, mut = false;
                         int32_t rc = 0;
