@@ -352,8 +352,9 @@ __global__ void k_plan(InstState *st, Plan *plan, int phase, int tc, BatchCounte
 
 // --------------------------------------------------------------- encode --
 
-// One thread per current hyperedge e' (rows of phase 0, K columns of phase
-// 1), walking the hyperedge's original vertex list.  Phase 0 sets
+// One current hyperedge e' per lane (rows of phase 0, K columns of phase
+// 1), a warp walking the original vertex lists of its 32 hyperedges
+// together.  Phase 0 sets
 // A[e'][v'] (rows = current hyperedges, K = current vertices) and counts
 // |e| (= I^E_ii); phase 1 sets At[v'][e'] (rows = current vertices, K =
 // hyperedges alive after DP) and counts deg(v) (= I^V_jj) and the maximum
@@ -362,74 +363,119 @@ __global__ void k_plan(InstState *st, Plan *plan, int phase, int tc, BatchCounte
 // contraction has read them.  A set counts only incidences that were not
 // already set, so a repeated id inside one hyperedge counts once.
 template <int kPhase, bool kSet, bool kDense>
-__global__ void k_scatter(InstState *st, const Plan *plan) {
+__global__ void __launch_bounds__(256) k_scatter(InstState *st, const Plan *plan) {
+    // Each warp takes 32 consecutive rows and walks the incidences of all of
+    // them together, 32 at a time, so a hyperedge of 64 vertices does not
+    // hold its warp 64 dependent atomics long.
+    __shared__ int32_t wfresh[8][32];  // fresh incidences per row of each warp
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int32_t total = plan->total_rows;
-    for (int32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < total;
-         g += gridDim.x * blockDim.x) {
-        const int b = find_owner(plan->row_off, plan->count, g);
-        InstState &s = st[b];
-        const int32_t ce = g - plan->row_off[b];
-        const int32_t e = s.e_c2o[ce];
-        const int32_t R = kPhase == 0 ? s.m : s.n;
-        const int32_t K = kPhase == 0 ? s.n : s.m_dp;
-        int32_t fresh_cnt = 0;
-        // phase 0 clear: a hyperedge this DP pass deleted makes its vertices
-        // MD candidates of this round
-        const bool mark_v = kPhase == 0 && !kSet && s.v_dirty && s.e_del[ce];
-        for (int32_t p = s.eptr[e]; p < s.eptr[e + 1]; ++p) {
-            const int32_t cv = s.v_o2c[s.evtx[p]];
+    const int32_t nw = gridDim.x * (blockDim.x >> 5);
+    for (int32_t g0 = (blockIdx.x * (blockDim.x >> 5) + wib) * 32; g0 < total; g0 += nw * 32) {
+        const int32_t g = g0 + lane;
+        int b = 0;
+        int32_t ce = 0, e = 0, p0 = 0, len = 0;
+        bool mark = false;
+        if (g < total) {
+            b = find_owner(plan->row_off, plan->count, g);
+            const InstState &s = st[b];
+            ce = g - plan->row_off[b];
+            e = s.e_c2o[ce];
+            p0 = s.eptr[e];
+            len = s.eptr[e + 1] - p0;
+            // phase 0 clear: a hyperedge this DP pass deleted makes its
+            // vertices MD candidates of this round
+            mark = kPhase == 0 && !kSet && s.v_dirty && s.e_del[ce];
+        }
+        int32_t incl = len;  // inclusive prefix of the row lengths over the warp
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int32_t start = incl - len;
+        const int32_t tot = __shfl_sync(0xffffffffu, incl, 31);
+        if (kSet && kPhase == 0) wfresh[wib][lane] = 0;
+        __syncwarp();
+        for (int32_t f0 = 0; f0 < tot; f0 += 32) {
+            const int32_t f = f0 + lane;
+            // owner row: the last lane whose run starts at or before f
+            int r = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const int c = r + step;
+                const int32_t sc = __shfl_sync(0xffffffffu, start, c & 31);
+                if (c < 32 && sc <= f) r = c;
+            }
+            const int rb = __shfl_sync(0xffffffffu, b, r);
+            const int32_t rce = __shfl_sync(0xffffffffu, ce, r);
+            const int32_t re = __shfl_sync(0xffffffffu, e, r);
+            const int32_t rp = __shfl_sync(0xffffffffu, p0, r) + f - __shfl_sync(0xffffffffu, start, r);
+            const bool rmark = __shfl_sync(0xffffffffu, mark, r);
+            if (f >= tot) continue;
+            InstState &s = st[rb];
+            const int32_t cv = s.v_o2c[s.evtx[rp]];
             if (cv < 0) continue;
-            if (mark_v && cv < s.n) {
+            if (rmark && cv < s.n) {
                 s.v_dirty[cv] = 1;
                 s.v_dirty_rb[cv >> 7] = 1;
             }
-            const int32_t r = kPhase == 0 ? ce : cv;
-            const int32_t c = kPhase == 0 ? cv : ce;
-            if (r >= R || c >= K) { atomicOr(&s.status, kErrCapacity); continue; }
+            const int32_t R = kPhase == 0 ? s.m : s.n;
+            const int32_t K = kPhase == 0 ? s.n : s.m_dp;
+            const int32_t rr = kPhase == 0 ? rce : cv;
+            const int32_t cc = kPhase == 0 ? cv : rce;
+            if (rr >= R || cc >= K) { atomicOr(&s.status, kErrCapacity); continue; }
             bool fresh = false;
             if (kDense) {
                 uint8_t *row = (kPhase == 0 ? s.A : s.At) +
-                               (int64_t)r * (kPhase == 0 ? s.A_pitch : s.At_pitch);
+                               (int64_t)rr * (kPhase == 0 ? s.A_pitch : s.At_pitch);
                 if (kSet) {
-                    uint32_t *w = reinterpret_cast<uint32_t *>(row + (c & ~3));
-                    const uint32_t sh = 8u * (c & 3);
+                    uint32_t *w = reinterpret_cast<uint32_t *>(row + (cc & ~3));
+                    const uint32_t sh = 8u * (cc & 3);
                     const uint32_t old = atomicOr(w, (uint32_t)kFp8One << sh);
                     fresh = ((old >> sh) & 0xffu) == 0;
-                    // occupancy of (row block r/128, K block c/128)
-                    uint32_t *ow = s.occ[kPhase] + (int64_t)(r >> 7) * s.occ_words[kPhase] +
-                                   ((c >> 7) >> 5);
-                    const uint32_t ob = 1u << ((c >> 7) & 31);
+                    // occupancy of (row block rr/128, K block cc/128)
+                    uint32_t *ow = s.occ[kPhase] + (int64_t)(rr >> 7) * s.occ_words[kPhase] +
+                                   ((cc >> 7) >> 5);
+                    const uint32_t ob = 1u << ((cc >> 7) & 31);
                     if (!(*reinterpret_cast<volatile uint32_t *>(ow) & ob)) atomicOr(ow, ob);
                 } else {
-                    row[c] = 0;
+                    row[cc] = 0;
                 }
             } else {
                 uint32_t *row = (kPhase == 0 ? s.Ab : s.Atb) +
-                                (int64_t)r * (kPhase == 0 ? s.Ab_pitch : s.Atb_pitch);
+                                (int64_t)rr * (kPhase == 0 ? s.Ab_pitch : s.Atb_pitch);
                 if (kSet) {
-                    const uint32_t bit = 1u << (c & 31);
-                    fresh = (atomicOr(&row[c >> 5], bit) & bit) == 0;
+                    const uint32_t bit = 1u << (cc & 31);
+                    fresh = (atomicOr(&row[cc >> 5], bit) & bit) == 0;
                 } else {
-                    row[c >> 5] = 0;  // every set bit of this word is cleared by some thread
+                    row[cc >> 5] = 0;  // every set bit of this word is cleared by some thread
                 }
             }
             if (kSet && fresh) {
                 if (kPhase == 0) {
-                    ++fresh_cnt;
+                    atomicAdd(&wfresh[wib][r], 1);
                 } else {
                     atomicAdd(&s.v_deg[cv], 1);
-                    atomicMax(&s.v_maxf[cv], s.f[e]);
+                    atomicMax(&s.v_maxf[cv], s.f[re]);
                 }
             }
         }
         if (kSet && kPhase == 0) {
-            // a hyperedge whose size changed since the previous DP pass (or
-            // never tested) makes its row block a DP candidate
-            if (s.e_dirty_rb && s.e_s[ce] != fresh_cnt) s.e_dirty_rb[ce >> 7] = 1;
-            s.e_s[ce] = fresh_cnt;  // one thread owns the row
-            // a count of 0 decides a pair only from a hyperedge with f > |e|
-            // (DP) or an empty one (SE)
-            if (kDense && (s.edge_rule ? fresh_cnt == 0 : s.e_f[ce] > fresh_cnt)) s.has_loose = 1;
+            __syncwarp();
+            if (g < total) {
+                InstState &s = st[b];
+                const int32_t fresh_cnt = wfresh[wib][lane];
+                // a hyperedge whose size changed since the previous DP pass (or
+                // never tested) makes its row block a DP candidate
+                if (s.e_dirty_rb && s.e_s[ce] != fresh_cnt) s.e_dirty_rb[ce >> 7] = 1;
+                s.e_s[ce] = fresh_cnt;  // one lane owns the row
+                // a count of 0 decides a pair only from a hyperedge with f > |e|
+                // (DP) or an empty one (SE)
+                if (kDense && (s.edge_rule ? fresh_cnt == 0 : s.e_f[ce] > fresh_cnt))
+                    s.has_loose = 1;
+            }
+            __syncwarp();  // wfresh is reused by the next group of rows
         }
     }
 }
