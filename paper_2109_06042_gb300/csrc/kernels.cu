@@ -785,8 +785,20 @@ cudaError_t launch_loop_cond(cudaGraphConditionalHandle h, BatchCounters *ctr, i
 
 static int grid_for(int sms, int per_sm) { return sms * per_sm; }
 
+// Blocks per instance for a grid-stride kernel over `items` per instance:
+// enough for the largest instance, but for a batch no more than about 16
+// blocks per SM in all (a block that finds no work still costs a launch).
+static int per_instance_grid(int64_t items, int count) {
+    int64_t g = (items + 255) / 256;
+    const int64_t cap = count > 1 ? (152 * 16 + count - 1) / count : 256;
+    if (g > cap) g = cap;
+    if (g > 256) g = 256;
+    return g < 1 ? 1 : (int)g;
+}
+
 cudaError_t launch_validate(InstState *st, int count, cudaStream_t s) {
-    k_validate<<<dim3(count > 1 ? 16 : 256, count), 256, 0, s>>>(st, count);
+    k_validate<<<dim3(count > 1 ? per_instance_grid(1 << 20, count) : 256, count), 256, 0, s>>>(
+        st, count);
     return cudaGetLastError();
 }
 
@@ -805,12 +817,8 @@ cudaError_t launch_gather_bounds(const int64_t *gptr, const int64_t *e0, int64_t
 cudaError_t launch_build(InstState *st, int count, int32_t max_rounds, int64_t max_nnz,
                          int64_t max_m, int64_t max_n, cudaStream_t s) {
     (void)max_n;
-    int gx = (int)((max_m + 255) / 256);
-    if (gx > 256) gx = 256;
-    if (gx < 1) gx = 1;
-    int gz = (int)((max_nnz + 255) / 256);
-    if (gz > 256) gz = 256;
-    if (gz < 1) gz = 1;
+    const int gx = per_instance_grid(max_m, count);
+    const int gz = per_instance_grid(max_nnz, count);
     k_init<<<count, 1024, 0, s>>>(st, count, max_rounds);
     k_vertex_degrees<<<dim3(gz, count), 256, 0, s>>>(st, count);
     k_vertex_layout<<<count, 1024, 0, s>>>(st, count);
