@@ -380,7 +380,8 @@ def run_ours(args, rank, world, dist):
         # tensor work actually issued (block-sparse skipping leaves out zero blocks)
         issued = kblocks * 2.0 * 128 * 256 * 128 / (contract_ms / 1e3) / 1e12
         roof = {"bound": "tensor", "achieved": round(achieved, 2), "peak": round(peak, 1),
-                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+                "traffic": measured_traffic(args, desc),
                 "kernel": "k_tc_contract", "peak_source": f"{kind}: 2 x bf16_tflops (burst)",
                 "launches_per_step": 2 * rounds, "avg_launch_ms": round(per_launch, 4),
                 "achieved_basis": "dense-formulation MACs x 2 (m^2 n + n^2 m' per round)",
@@ -521,6 +522,43 @@ def run_stream(args, rank, world):
                     "closed_loop_p99_ms": round(1e3 * float(np.percentile(lat0, 99)), 3),
                     "sweep": sweep},
     }
+
+
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "k_tc_contract_traffic_powerlaw_n20000_m40000.md")
+TRAFFIC_SOURCES = ("contract_tc.cu", "kernels.cu", "mhs_internal.h")
+
+
+def kernel_sources_sha256():
+    """Digest of the sources that decide the contraction's DRAM traffic."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, "paper_2109_06042_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(args, desc):
+    """DRAM bytes per k_tc_contract launch from the committed ncu capture of
+    this workload (dram__bytes_read.sum + dram__bytes_write.sum over one
+    kernelization's launches), or None when the workload or options differ
+    or the kernel sources changed since the capture."""
+    default = (args.workload == "powerlaw" and args.seed == 0 and args.sparsity == "skip" and
+               args.rule == "dp" and not args.full_edges and args.contraction == "fp8")
+    if not default or not os.path.exists(TRAFFIC_PROFILE):
+        return None
+    fields = {}
+    with open(TRAFFIC_PROFILE) as fh:
+        for line in fh:
+            if ":" in line and line.startswith(("traffic_bytes_per_launch", "source_sha256")):
+                k, v = line.split(":", 1)
+                fields[k.strip()] = v.strip()
+    if fields.get("source_sha256") != kernel_sources_sha256():
+        return None
+    try:
+        return int(float(fields["traffic_bytes_per_launch"]))
+    except (KeyError, ValueError):
+        return None
 
 
 def variant_name(args):
