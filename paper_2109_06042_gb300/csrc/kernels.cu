@@ -2,8 +2,8 @@
 // contraction with the fused DP / MD epilogue.
 //
 // Round structure (Algorithm 3, Section 4.1), all on the device:
-//   plan(phase 0) -> encode_edges -> contract(DP or SE) -> compact_edges
-//   plan(phase 1) -> encode_vertices -> contract(MD) -> compact_vertices
+//   plan(phase 0) -> encode A -> contract(DP or SE) -> compact_edges
+//   plan(phase 1) -> clear A + encode A^T -> contract(MD) -> clear A^T -> compact_vertices
 //   [rule FE at a fixpoint, fe.cu]
 // The contraction of either kind (this file: popcount; contract_tc.cu:
 // tcgen05 FP8) computes the pair counts of Eq. (1) / Eq. (2) tile by tile
@@ -318,7 +318,10 @@ __global__ void k_plan(InstState *st, Plan *plan, int phase, int tc, BatchCounte
         if (b < count) {
             const InstState &s = st[b];
             if (s.active && s.status == 0) {
-                rows = phase == 0 ? s.m : s.m_dp;  // hyperedges to scatter
+                // hyperedges to scatter: phase 0 the current ones; phase 1 the
+                // rows DP saw (the fused pass clears A at those rows and sets
+                // A^T for the ones DP kept)
+                rows = s.m;
                 const int32_t R = phase == 0 ? s.m : s.n;
                 tiles = tc == 2 ? tc_pair_tiles(R) : tc == 1 ? tc_tiles(R) : pop_tiles(R);
                 act_any = 1;
@@ -352,16 +355,18 @@ __global__ void k_plan(InstState *st, Plan *plan, int phase, int tc, BatchCounte
 
 // --------------------------------------------------------------- encode --
 
-// One current hyperedge e' per lane (rows of phase 0, K columns of phase
-// 1), a warp walking the original vertex lists of its 32 hyperedges
-// together.  Phase 0 sets
-// A[e'][v'] (rows = current hyperedges, K = current vertices) and counts
-// |e| (= I^E_ii); phase 1 sets At[v'][e'] (rows = current vertices, K =
-// hyperedges alive after DP) and counts deg(v) (= I^V_jj) and the maximum
-// demand.  The operands are all-zero between phases: kClear writes zeros at
-// exactly the positions kSet wrote, with the same id maps, after the
-// contraction has read them.  A set counts only incidences that were not
-// already set, so a repeated id inside one hyperedge counts once.
+// One hyperedge row per lane, a warp walking the original vertex lists of
+// its 32 hyperedges together.  Phase 0 (rows = current hyperedges) sets
+// A[e'][v'] (K = current vertices) and counts |e| (= I^E_ii).  Phase 1 walks
+// the rows the DP pass saw (e_prev): its set pass clears their entries of A
+// (the DP pass's clear, fused in since it walks the same incidences), marks
+// the vertices of the hyperedges DP deleted as MD candidates, and for the
+// kept ones sets At[v'][e''] (rows = current vertices, K = the hyperedges'
+// positions after DP) and counts deg(v) (= I^V_jj) and the maximum demand;
+// its clear pass clears At after the MD contraction.  So the operands are
+// all-zero between rounds, and A^T between phases.  A set counts only
+// incidences that were not already set, so a repeated id inside one
+// hyperedge counts once.
 template <int kPhase, bool kSet, bool kDense>
 __global__ void __launch_bounds__(256) k_scatter(InstState *st, const Plan *plan) {
     // Each warp takes 32 consecutive rows and walks the incidences of all of
@@ -376,16 +381,20 @@ __global__ void __launch_bounds__(256) k_scatter(InstState *st, const Plan *plan
         int b = 0;
         int32_t ce = 0, e = 0, p0 = 0, len = 0;
         bool mark = false;
+        int32_t cnew = 0;  // phase 1: the row's position after DP, -1 if DP deleted it
         if (g < total) {
             b = find_owner(plan->row_off, plan->count, g);
             const InstState &s = st[b];
             ce = g - plan->row_off[b];
-            e = s.e_c2o[ce];
+            e = kPhase == 0 ? s.e_c2o[ce] : s.e_prev[ce];
+            if (kPhase == 1) cnew = s.e_o2c[e];
             p0 = s.eptr[e];
             len = s.eptr[e + 1] - p0;
-            // phase 0 clear: a hyperedge this DP pass deleted makes its
+            // phase 1 set: a hyperedge the DP pass deleted makes its
             // vertices MD candidates of this round
-            mark = kPhase == 0 && !kSet && s.v_dirty && s.e_del[ce];
+            mark = kPhase == 1 && kSet && s.v_dirty && cnew < 0;
+            // phase 1 clear: A^T holds only the rows DP kept
+            if (kPhase == 1 && !kSet && cnew < 0) len = 0;
         }
         int32_t incl = len;  // inclusive prefix of the row lengths over the warp
 #pragma unroll
@@ -409,6 +418,7 @@ __global__ void __launch_bounds__(256) k_scatter(InstState *st, const Plan *plan
             }
             const int rb = __shfl_sync(0xffffffffu, b, r);
             const int32_t rce = __shfl_sync(0xffffffffu, ce, r);
+            const int32_t rnew = __shfl_sync(0xffffffffu, cnew, r);
             const int32_t re = __shfl_sync(0xffffffffu, e, r);
             const int32_t rp = __shfl_sync(0xffffffffu, p0, r) + f - __shfl_sync(0xffffffffu, start, r);
             const bool rmark = __shfl_sync(0xffffffffu, mark, r);
@@ -420,10 +430,15 @@ __global__ void __launch_bounds__(256) k_scatter(InstState *st, const Plan *plan
                 s.v_dirty[cv] = 1;
                 s.v_dirty_rb[cv >> 7] = 1;
             }
+            if (kPhase == 1 && kSet) {  // the DP pass's clear of A, fused in
+                if (kDense) s.A[(int64_t)rce * s.A_pitch + cv] = 0;
+                else s.Ab[(int64_t)rce * s.Ab_pitch + (cv >> 5)] = 0;
+                if (rnew < 0) continue;  // deleted by DP: nothing in A^T
+            }
             const int32_t R = kPhase == 0 ? s.m : s.n;
             const int32_t K = kPhase == 0 ? s.n : s.m_dp;
             const int32_t rr = kPhase == 0 ? rce : cv;
-            const int32_t cc = kPhase == 0 ? cv : rce;
+            const int32_t cc = kPhase == 0 ? cv : rnew;
             if (rr >= R || cc >= K) { atomicOr(&s.status, kErrCapacity); continue; }
             bool fresh = false;
             if (kDense) {
@@ -496,7 +511,12 @@ __global__ void k_compact_edges(InstState *st, int count) {
     for (int32_t base = 0; base < m; base += blockDim.x) {
         int32_t r = base + threadIdx.x;
         int32_t keep = 0, orig = -1, size = 0;
-        if (r < m) { keep = s.e_del[r] == 0; orig = s.e_c2o[r]; size = s.e_s[r]; }
+        if (r < m) {
+            keep = s.e_del[r] == 0;
+            orig = s.e_c2o[r];
+            size = s.e_s[r];
+            s.e_prev[r] = orig;  // row r of A as this DP pass saw it
+        }
         int32_t tot;
         int32_t ex = block_exclusive_scan<int32_t>(keep, &tot, sh);  // syncs after reads
         if (r < m) {
@@ -862,8 +882,9 @@ cudaError_t launch_round_phase(InstState *st, Plan *plan, BatchCounters *ctr, in
         k_pop_contract<<<grid_for(sms, 6), 256, 0, s>>>(st, plan, phase);
     }
     if (ev_contract_end) cudaEventRecordWithFlags(ev_contract_end, s, cudaEventRecordExternal);
-    if (phase == 0) launch_scatter<0>(st, plan, false, tc, grid, s);
-    else launch_scatter<1>(st, plan, false, tc, grid, s);
+    // (the DP pass's clear of A runs inside the MD set pass, which walks the
+    // same incidences)
+    if (phase == 1) launch_scatter<1>(st, plan, false, tc, grid, s);
     if (phase == 0) k_compact_edges<<<count, 1024, 0, s>>>(st, count);
     else k_compact_vertices<<<count, 1024, 0, s>>>(st, count, ctr, done_list);
     return cudaGetLastError();

@@ -306,7 +306,7 @@ struct Layout {  // byte offsets inside the arena for one instance
     int64_t occ0, occ1;
     int64_t eptr, evtx, f;
     int64_t v_o2c, v_c2o, e_o2c, e_c2o, e_f, e_s, v_deg, v_maxf, v_cnt, e_del, v_del, forced;
-    int64_t e_dirty_rb, v_dirty, v_dirty_rb;
+    int64_t e_dirty_rb, v_dirty, v_dirty_rb, e_prev;
     int64_t A, At, Ab, Atb;
 };
 
@@ -384,6 +384,7 @@ mhs_status create(int32_t count, const int32_t *n, const int32_t *m, const int64
         L.v_del = ar.take(n0);
         L.forced = opt.full_edges ? ar.take(n0) : -1;
         L.v_dirty = ar.take(n0);
+        L.e_prev = ar.take(4 * m0);
         L.e_dirty_rb = ar.take(round_up(std::max<int64_t>(m0, 1), kRowAlign) / kTcM);
         L.v_dirty_rb = ar.take(round_up(std::max<int64_t>(n0, 1), kRowAlign) / kTcM);
         if (dense) {
@@ -484,6 +485,7 @@ mhs_status create(int32_t count, const int32_t *n, const int32_t *m, const int64
         s.full_edges = opt.full_edges;
         s.forced = L.forced >= 0 ? base + L.forced : nullptr;
         s.v_dirty = base + L.v_dirty;
+        s.e_prev = reinterpret_cast<int32_t *>(base + L.e_prev);
         s.e_dirty_rb = base + L.e_dirty_rb;
         s.v_dirty_rb = base + L.v_dirty_rb;
         s.eptr = reinterpret_cast<int32_t *>(base + L.eptr);

@@ -71,6 +71,7 @@ struct InstState {
     // id maps (capacity n0 / m0)
     int32_t *v_o2c, *v_c2o;
     int32_t *e_o2c, *e_c2o;
+    int32_t *e_prev;       // [m0] input id of each row as DP saw it (before compaction)
 
     // epilogue inputs, indexed by current id
     int32_t *e_f;          // f of current hyperedge

@@ -114,6 +114,7 @@ extern "C" mhs_status mhs_kernelize_noalloc(int32_t n, int32_t m, const int32_t 
     const int64_t o_kerr = take(sizeof(int32_t));
     const int64_t o_vo2c = take(4 * (int64_t)n), o_vc2o = take(4 * (int64_t)n);
     const int64_t o_eo2c = take(4 * (int64_t)m), o_ec2o = take(4 * (int64_t)m);
+    const int64_t o_eprev = take(4 * (int64_t)m);
     const int64_t o_ef = take(4 * (int64_t)m), o_es = take(4 * (int64_t)m);
     const int64_t o_vdeg = take(4 * ((int64_t)n + 1)), o_vmaxf = take(4 * (int64_t)n);
     const int64_t o_vcnt = take(4 * ((int64_t)n + 1));
@@ -136,6 +137,7 @@ extern "C" mhs_status mhs_kernelize_noalloc(int32_t n, int32_t m, const int32_t 
     st.v_c2o = reinterpret_cast<int32_t *>(base + o_vc2o);
     st.e_o2c = reinterpret_cast<int32_t *>(base + o_eo2c);
     st.e_c2o = reinterpret_cast<int32_t *>(base + o_ec2o);
+    st.e_prev = reinterpret_cast<int32_t *>(base + o_eprev);
     st.e_f = reinterpret_cast<int32_t *>(base + o_ef);
     st.e_s = reinterpret_cast<int32_t *>(base + o_es);
     st.v_deg = reinterpret_cast<int32_t *>(base + o_vdeg);
