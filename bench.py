@@ -402,10 +402,16 @@ def run_ours(args, rank, world, dist):
         seq = cpu_sequential(insts, desc, args.cpu_seconds) if variant_name(args) == "DP+MD" \
             else None
 
-    # load kernels incl. the result-mask kernel, plus per round: 10 + the loop-condition
-    # kernel (+ the 3 kernels of rule FE with --full-edges)
-    load_kernels = 5 if batch else 3
-    per_round = 11 + (3 if args.full_edges else 0)
+    # Kernels of one step.  Load: k_validate, k_init, k_vertex_degrees,
+    # k_vertex_layout, k_layout_keys, k_layout_scan, k_layout_place,
+    # k_edge_rows (a batch adds k_gather_bounds and k_localize_ptr), then the
+    # result-mask kernel.  Per round: k_plan, the A set scatter, [k_tile_list],
+    # the DP contraction, k_compact_edges, k_plan, the fused A clear / A^T set
+    # scatter, [k_tile_list], the MD contraction, the A^T clear scatter,
+    # k_compact_vertices and the loop-condition kernel ([] tcgen05 only), plus
+    # the three FE kernels with --full-edges.
+    load_kernels = 9 + (2 if batch else 0)
+    per_round = (12 if args.contraction == "fp8" else 10) + (3 if args.full_edges else 0)
     line = {
         "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
