@@ -675,10 +675,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                 float a = 0.f, bb = 0.f;
                 int32_t o = 0;
                 if (j < R) {
-                    if (phase == 0) {
-                        a = (float)s.e_f[j];
-                        bb = (float)(se ? s.e_s[j] : s.e_f[j] - s.e_s[j]);
-                        o = s.e_c2o[j];
+                    if (phase == 0) {  // {f, f - s (SE: s), input id}
+                        const int4 rec = s.e_rec[j];
+                        a = (float)rec.x;
+                        bb = (float)rec.y;
+                        o = rec.z;
                     } else {
                         a = (float)s.v_deg[j];
                         o = s.v_c2o[j];
@@ -694,9 +695,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             int32_t ri_o = 0;              // input index of row i
             if (i < R) {
                 if (phase == 0) {
-                    ri_f = (float)s.e_f[i];
-                    ri_a = (float)(se ? s.e_s[i] : s.e_f[i] - s.e_s[i]);
-                    ri_o = s.e_c2o[i];
+                    const int4 rec = s.e_rec[i];
+                    ri_f = (float)rec.x;
+                    ri_a = (float)rec.y;
+                    ri_o = rec.z;
                 } else {
                     ri_f = (float)s.v_deg[i];
                     ri_o = s.v_c2o[i];
@@ -709,9 +711,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc_fence_after();
             bool rowflag = false;
             int32_t rowcnt = 0;
-            // a tile with no shared K block has all counts 0 and no accumulator
-            bool nonzero;
-            {
+            // A listed tile contracts at least one K block, so its accumulator
+            // holds its counts -- except in a DP pass where zero counts matter:
+            // the list then keeps every tile, also tiles with no shared K block,
+            // which the MMA thread skips, leaving the accumulator stale.
+            bool nonzero = true;
+            if (phase == 0 && s.has_loose && !s.no_skip) {
                 KIter kit;
                 kit_init(kit, s, phase, ti);
                 nonzero = kit_next(kit) >= 0;

@@ -20,16 +20,6 @@ namespace {
 
 constexpr uint8_t kFp8One = 0x38;  // 1.0 in E4M3
 
-__device__ __forceinline__ int32_t warp_sum(int32_t v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-__device__ __forceinline__ int32_t warp_max(int32_t v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
 
 // Exclusive block scan of one value per thread (blockDim.x a multiple of
 // 32, at most 1024).  *total receives the block total.
@@ -485,6 +475,10 @@ __global__ void __launch_bounds__(256) k_scatter(InstState *st, const Plan *plan
                 // never tested) makes its row block a DP candidate
                 if (s.e_dirty_rb && s.e_s[ce] != fresh_cnt) s.e_dirty_rb[ce >> 7] = 1;
                 s.e_s[ce] = fresh_cnt;  // one lane owns the row
+                if (s.e_rec) {  // the tcgen05 epilogue stages this one record per row
+                    const int32_t fe = s.e_f[ce];
+                    s.e_rec[ce] = make_int4(fe, s.edge_rule ? fresh_cnt : fe - fresh_cnt, e, 0);
+                }
                 // a count of 0 decides a pair only from a hyperedge with f > |e|
                 // (DP) or an empty one (SE)
                 if (kDense && (s.edge_rule ? fresh_cnt == 0 : s.e_f[ce] > fresh_cnt))

@@ -306,7 +306,7 @@ struct Layout {  // byte offsets inside the arena for one instance
     int64_t occ0, occ1;
     int64_t eptr, evtx, f;
     int64_t v_o2c, v_c2o, e_o2c, e_c2o, e_f, e_s, v_deg, v_maxf, v_cnt, e_del, v_del, forced;
-    int64_t e_dirty_rb, v_dirty, v_dirty_rb, e_prev;
+    int64_t e_dirty_rb, v_dirty, v_dirty_rb, e_prev, e_rec;
     int64_t A, At, Ab, Atb;
 };
 
@@ -385,6 +385,7 @@ mhs_status create(int32_t count, const int32_t *n, const int32_t *m, const int64
         L.forced = opt.full_edges ? ar.take(n0) : -1;
         L.v_dirty = ar.take(n0);
         L.e_prev = ar.take(4 * m0);
+        L.e_rec = dense ? ar.take(16 * m0) : -1;
         L.e_dirty_rb = ar.take(round_up(std::max<int64_t>(m0, 1), kRowAlign) / kTcM);
         L.v_dirty_rb = ar.take(round_up(std::max<int64_t>(n0, 1), kRowAlign) / kTcM);
         if (dense) {
@@ -486,6 +487,7 @@ mhs_status create(int32_t count, const int32_t *n, const int32_t *m, const int64
         s.forced = L.forced >= 0 ? base + L.forced : nullptr;
         s.v_dirty = base + L.v_dirty;
         s.e_prev = reinterpret_cast<int32_t *>(base + L.e_prev);
+        s.e_rec = L.e_rec >= 0 ? reinterpret_cast<int4 *>(base + L.e_rec) : nullptr;
         s.e_dirty_rb = base + L.e_dirty_rb;
         s.v_dirty_rb = base + L.v_dirty_rb;
         s.eptr = reinterpret_cast<int32_t *>(base + L.eptr);

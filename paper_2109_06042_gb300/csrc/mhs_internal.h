@@ -16,6 +16,8 @@
 
 #include <cstdint>
 
+#include <cuda_runtime.h>
+
 namespace mhs {
 
 // Tile shapes.
@@ -79,6 +81,8 @@ struct InstState {
     int32_t *v_deg;        // degree over alive hyperedges (= I^V_jj)   [n0 + 1]
     int32_t *v_maxf;       // max demand over alive hyperedges (0 if none)
     int32_t *v_cnt;        // C_j of Algorithm 2                         [n0 + 1]
+    int4 *e_rec;           // tcgen05 path: per current hyperedge {f, f - |e| (SE: |e|), input id},
+                           // written by the DP set pass for the epilogue's staging
     uint8_t *e_del;        // DP deletion flags
     uint8_t *v_del;        // MD deletion flags
     // Incremental rounds.  After the first round, a pass can only delete

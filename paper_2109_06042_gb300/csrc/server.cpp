@@ -73,7 +73,7 @@ struct Request {
 // Device layout of one admitted instance inside its arena.
 struct Layout {
     int64_t eptr, evtx, f, v_o2c, v_c2o, e_o2c, e_c2o, e_f, e_s, v_deg, v_maxf, v_cnt, e_del,
-        v_del, forced, v_dirty, e_dirty_rb, v_dirty_rb, e_prev, occ0, occ1, tmaps, dense,
+        v_del, forced, v_dirty, e_dirty_rb, v_dirty_rb, e_prev, e_rec, occ0, occ1, tmaps, dense,
         dense_bytes, bytes;
 };
 
@@ -102,6 +102,7 @@ Layout plan_layout(int32_t n, int32_t m, int64_t nnz, bool dense, bool fe) {
     L.forced = fe ? take(n) : -1;
     L.v_dirty = take(n);
     L.e_prev = take(4 * (int64_t)m);
+    L.e_rec = dense ? take(16 * (int64_t)m) : -1;
     L.e_dirty_rb = take(up(m > 0 ? m : 1, kRowAlign) / kTcM);
     L.v_dirty_rb = take(up(n > 0 ? n : 1, kRowAlign) / kTcM);
     {
@@ -206,6 +207,7 @@ mhs_status admit(Lane &Ln, int si, std::shared_ptr<Request> req) {
     s.forced = fe ? a + L.forced : nullptr;
     s.v_dirty = a + L.v_dirty;
     s.e_prev = reinterpret_cast<int32_t *>(a + L.e_prev);
+    s.e_rec = L.e_rec >= 0 ? reinterpret_cast<int4 *>(a + L.e_rec) : nullptr;
     s.e_dirty_rb = a + L.e_dirty_rb;
     s.v_dirty_rb = a + L.v_dirty_rb;
     s.eptr = reinterpret_cast<int32_t *>(a + L.eptr);
