@@ -255,7 +255,10 @@ __device__ __forceinline__ void tile_info(const InstState *st, int phase, int64_
 
 // K blocks of a tile where both operands hold a nonzero: the occupancy
 // bits of row block bi AND those of the two row blocks of column block bj.
-// Every role walks the same sequence.
+// A bit covers kOccK = 64 columns, half a K block: a K block is loaded when
+// either of its halves is shared, so a nonzero of one operand in the low
+// half and one of the other in the high half do not cost a load.  Every
+// role walks the same sequence.
 struct KIter {
     const uint32_t *a, *a1, *b0, *b1;
     int32_t nkw, w, nk;
@@ -276,8 +279,8 @@ __device__ __forceinline__ void kit_init(KIter &k, const InstState &s, int phase
     }
     k.b0 = base + (int64_t)(2 * ti.bj) * W;
     k.b1 = k.b0 + W;
-    k.nk = ti.nk;
-    k.nkw = (ti.nk + 31) / 32;
+    k.nk = 2 * ti.nk;  // occupancy bits
+    k.nkw = (k.nk + 31) / 32;
     k.w = -1;
     k.mask = 0;
     k.all = s.no_skip != 0;
@@ -294,9 +297,9 @@ __device__ __forceinline__ int32_t kit_next(KIter &k) {
             k.mask = am & (__ldg(k.b0 + k.w) | __ldg(k.b1 + k.w));
         }
     }
-    const int32_t bit = __ffs(k.mask) - 1;
-    k.mask &= k.mask - 1;
-    return k.w * 32 + bit;
+    const int32_t bit = (__ffs(k.mask) - 1) & ~1;  // the K block's two bits
+    k.mask &= ~(3u << bit);
+    return (k.w * 32 + bit) >> 1;
 }
 
 // Build this phase's tile list: every tile of the upper triangle (in the

@@ -439,10 +439,11 @@ __global__ void __launch_bounds__(256) k_scatter(InstState *st, const Plan *plan
                     const uint32_t sh = 8u * (cc & 3);
                     const uint32_t old = atomicOr(w, (uint32_t)kFp8One << sh);
                     fresh = ((old >> sh) & 0xffu) == 0;
-                    // occupancy of (row block rr/128, K block cc/128)
+                    // occupancy of (row block rr/128, K block cc/kOccK)
+                    const int32_t kblk = cc / kOccK;
                     uint32_t *ow = s.occ[kPhase] + (int64_t)(rr >> 7) * s.occ_words[kPhase] +
-                                   ((cc >> 7) >> 5);
-                    const uint32_t ob = 1u << ((cc >> 7) & 31);
+                                   (kblk >> 5);
+                    const uint32_t ob = 1u << (kblk & 31);
                     if (!(*reinterpret_cast<volatile uint32_t *>(ow) & ob)) atomicOr(ow, ob);
                 } else {
                     row[cc] = 0;

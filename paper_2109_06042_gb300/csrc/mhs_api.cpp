@@ -49,8 +49,8 @@ inline int64_t kpad_bytes(int64_t K) { return round_up(std::max<int64_t>(K, 1), 
 inline int64_t kpad_words(int64_t K) {
     return round_up(std::max<int64_t>((K + 31) / 32, 1), 4);
 }
-// occupancy words per row block: one bit per K block of kTcK columns
-inline int64_t occ_words(int64_t K) { return (kpad_bytes(K) / kTcK + 31) / 32; }
+// occupancy words per row block: one bit per K block of kOccK columns
+inline int64_t occ_words(int64_t K) { return (kpad_bytes(K) / kOccK + 31) / 32; }
 
 }  // namespace
 

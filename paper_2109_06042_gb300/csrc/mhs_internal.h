@@ -25,6 +25,7 @@ constexpr int kPopTile = 64;     // popcount contraction: 64 x 64 pair tiles
 constexpr int kTcM = 128;        // tcgen05 contraction: 128 rows (i) ...
 constexpr int kTcN = 256;        // ... x 256 columns (j) per tile
 constexpr int kTcK = 128;        // K bytes per pipeline stage (FP8)
+constexpr int kOccK = 64;        // K columns per occupancy bit (half a stage)
 constexpr int kRowAlign = 256;   // row capacity rounded to this
 constexpr int kTraceRounds = 32; // rounds whose sizes an instance records
 
@@ -103,11 +104,12 @@ struct InstState {
     // bit-packed operands: rows x pitch 32-bit words
     uint32_t *Ab, *Atb;
     int32_t Ab_pitch, Atb_pitch;
-    // tcgen05 tensor maps (CUtensorMap, 128 bytes each) for A and At, in device memory
+    // tcgen05 tensor maps for A and At in device memory, each two CUtensorMaps
+    // (128 bytes each): full stages, then half stages
     const void *tmap_A;
     const void *tmap_At;
     // block-sparse skipping (tcgen05 path): per row block of 128 rows, one
-    // bit per K block of 128 columns that holds a nonzero of the operand of
+    // bit per K block of kOccK columns that holds a nonzero of the operand of
     // phase p (0: A, 1: At); occ_words[p] words per row block
     uint32_t *occ[2];
     int32_t occ_words[2];

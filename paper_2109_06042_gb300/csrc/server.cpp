@@ -48,7 +48,7 @@ namespace {
 inline int64_t up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 inline int64_t kbytes(int64_t K) { return up(K > 0 ? K : 1, kTcK); }
 inline int64_t kwords(int64_t K) { return up(((K + 31) / 32) > 0 ? (K + 31) / 32 : 1, 4); }
-inline int64_t occ_words(int64_t K) { return (kbytes(K) / kTcK + 31) / 32; }
+inline int64_t occ_words(int64_t K) { return (kbytes(K) / kOccK + 31) / 32; }
 constexpr int64_t kServerListCap = 16 << 20;  // tile-list entries shared by the slots
 inline int64_t now_ns() {
     return std::chrono::duration_cast<std::chrono::nanoseconds>(
