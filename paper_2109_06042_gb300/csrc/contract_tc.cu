@@ -341,6 +341,7 @@ __global__ void k_tile_list(InstState *st, Plan *plan, int phase) {
             } else {
                 tc_tile_coords(t - plan->tile_off[lo], ti.R, G, &ti.bi, &ti.bj);
             }
+            bool has_k = true;
             if (s.no_skip) {
                 keep = true;  // the dense formulation: every tile, every round
             } else {
@@ -350,13 +351,14 @@ __global__ void k_tile_list(InstState *st, Plan *plan, int phase) {
                 keep = !drb || (phase == 1 && s.md_full) || drb[r0] || (kPair && drb[r0 + 1]) ||
                        drb[2 * ti.bj] || drb[2 * ti.bj + 1];
                 // ... and share a nonzero K block, unless zero counts matter
-                if (keep && !(phase == 0 && s.has_loose)) {
+                if (keep) {
                     KIter k;
                     kit_init(k, s, phase, ti);
-                    keep = kit_next(k) >= 0;
+                    has_k = kit_next(k) >= 0;
+                    keep = has_k || (phase == 0 && s.has_loose);
                 }
             }
-            packed = pack_tile(lo, ti.bi, ti.bj);
+            packed = pack_tile(lo, ti.bi, ti.bj) | (has_k ? 0 : kTileNoK);
         }
         const uint32_t ballot = __ballot_sync(0xffffffffu, keep);
         int32_t start = 0;
@@ -381,6 +383,7 @@ struct __align__(8) SharedCtl {
     uint64_t ring_full[kRing];   // entry published (producer arrives)
     uint64_t ring_empty[kRing];  // entry read by the MMA thread and the epilogue (2 arrivals)
     int64_t ring[kRing];         // packed tile entry, -1 = no more tiles
+    uint32_t stage_last[kStages];  // the stage is its tile's last (written by the producer)
     uint64_t drain;
     uint32_t tmem_base;
     int abort;
@@ -524,11 +527,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                     fenced = tmap;
                 }
                 const int32_t yi = ti.bi * kTcM, yj = ti.bj * kTcN;
-                for (; kb >= 0; kb = kit_next(kit)) {
+                while (kb >= 0) {
+                    // one K block ahead: the MMA thread learns from the stage
+                    // whether it ends the tile, and walks no occupancy bits
+                    const int32_t kb_next = kit_next(kit);
                     if (!mbar_wait(smem_u32(&ctl->empty[stage]), phase_bit ^ 1, abort, kWaitNs)) {
                         aborted = true;
                         break;
                     }
+                    ctl->stage_last[stage] = kb_next < 0;  // published by the arrive below
                     const uint32_t full = smem_u32(&ctl->full[stage]);
                     mbar_expect_tx(full, kStageBytes);
                     const uint32_t sa = smem_u32(smem + stage * kStageBytes);
@@ -543,6 +550,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                     ++issued;
                     if (++stage == kStages) { stage = 0; phase_bit ^= 1; }
+                    kb = kb_next;
                 }
                 cur = nxt;
                 ti = nx;
@@ -580,16 +588,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                 *e = *reinterpret_cast<volatile int64_t *>(&ctl->ring[k % kRing]);
                 return true;
             };
-            TileInfo ti, nx;
-            KIter kit, nkit;
-            int32_t kb = -1, nkb = -1;
+            // The tile list flags tiles without a shared K block; the
+            // producer flags the last stage of every other tile.
             int64_t cur = -1;
             aborted = !take(0, &cur);
-            if (cur >= 0) {
-                tile_info(st, phase, cur, &ti, kPair, rank);
-                kit_init(kit, st[ti.b], phase, ti);
-                kb = kit_next(kit);
-            }
             while (cur >= 0 && !aborted) {
                 ring_release(it);  // done with entry `it`
                 int64_t nxt = -1;
@@ -597,11 +599,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     aborted = true;
                     break;
                 }
-                if (nxt >= 0) {  // prefetch the next tile's first K block
-                    tile_info(st, phase, nxt, &nx, kPair, rank);
-                    kit_init(nkit, st[nx.b], phase, nx);
-                    nkb = kit_next(nkit);
-                }
+                const bool has_k = (cur & kTileNoK) == 0;
                 const int acc = it & 1;
                 const uint32_t acc_phase = (it >> 1) & 1;
                 if (!mbar_wait(smem_u32(&ctl->tmem_empty[acc]), acc_phase ^ 1, abort, kWaitNs)) {
@@ -612,18 +610,25 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint32_t d = tmem + acc * kAccCols;
                 bool first = true;
                 ++n_tiles;
-                for (; kb >= 0; kb = kit_next(kit)) {
+                for (bool last = !has_k; !last;) {
                     if (!mbar_wait(smem_u32(&ctl->full[stage]), phase_bit, abort, kWaitNs)) {
                         aborted = true;
                         break;
                     }
                     tc_fence_after();
+                    // The flag must be read before this stage goes back to the
+                    // producer: the first MMA's accumulate flag depends on the
+                    // loaded word (which is 0 or 1, never 2), so the MMAs, and
+                    // the commit that releases the stage, issue after the load.
+                    const uint32_t lastw =
+                        *reinterpret_cast<volatile uint32_t *>(&ctl->stage_last[stage]);
+                    last = lastw != 0;
                     const uint32_t sa = smem_u32(smem + stage * kStageBytes);
                     const uint32_t sb = sa + kABytes;
 #pragma unroll
                     for (int k = 0; k < kTcK / 32; ++k)
                         mma_f8(d, smem_desc(sa + 32 * k), smem_desc(sb + 32 * k),
-                               (!first || k > 0) ? 1u : 0u);
+                               (!first || k > 0 || lastw == 2u) ? 1u : 0u);
                     first = false;
                     ++n_kblocks;
                     if (kPair) mma_commit_mc(smem_u32(&ctl->empty[stage]), (uint16_t)0x3);
@@ -632,9 +637,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 if (!aborted) mma_commit(smem_u32(&ctl->tmem_full[acc]));
                 cur = nxt;
-                ti = nx;
-                kit = nkit;
-                kb = nkb;
                 ++it;
             }
             if (aborted) {  // wait for the MMAs already issued before freeing TMEM
@@ -714,16 +716,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc_fence_after();
             bool rowflag = false;
             int32_t rowcnt = 0;
-            // A listed tile contracts at least one K block, so its accumulator
-            // holds its counts -- except in a DP pass where zero counts matter:
-            // the list then keeps every tile, also tiles with no shared K block,
-            // which the MMA thread skips, leaving the accumulator stale.
-            bool nonzero = true;
-            if (phase == 0 && s.has_loose && !s.no_skip) {
-                KIter kit;
-                kit_init(kit, s, phase, ti);
-                nonzero = kit_next(kit) >= 0;
-            }
+            // A tile contracts at least one K block, so its accumulator holds
+            // its counts -- except a tile the list flags as having no shared K
+            // block (kept only in a DP pass where zero counts matter), which
+            // the MMA thread skips, leaving the accumulator stale.
+            const bool nonzero = (entry & kTileNoK) == 0;
             // A count of 0 changes nothing unless some hyperedge has f > |e| (DP)
             // or is empty (SE): only from such a hyperedge does x = 0 delete; in
             // MD it only adds dominators of a vertex in no hyperedge, deleted anyway.

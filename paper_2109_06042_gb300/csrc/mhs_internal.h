@@ -148,8 +148,11 @@ __host__ __device__ inline int64_t pop_tiles(int32_t R) {
 __host__ __device__ inline int64_t pack_tile(int b, int32_t bi, int32_t bj) {
     return ((int64_t)b << 40) | ((int64_t)bi << 20) | (int64_t)bj;
 }
+// Flag of a tile-list entry (tcgen05 path): no K block holds a nonzero of
+// both operands, so the tile contracts nothing.
+constexpr int64_t kTileNoK = (int64_t)1 << 62;
 __host__ __device__ inline void unpack_tile(int64_t v, int *b, int32_t *bi, int32_t *bj) {
-    *b = (int)(v >> 40);
+    *b = (int)((v >> 40) & 0x3FFFFF);
     *bi = (int32_t)((v >> 20) & 0xFFFFF);
     *bj = (int32_t)(v & 0xFFFFF);
 }
