@@ -11,6 +11,7 @@
 // deletion flags of Algorithm 1 or the dominator counts of Algorithm 2.
 #include <cuda_runtime.h>
 
+#include "bounded_wait.cuh"
 #include "kernels.h"
 #include "mhs_internal.h"
 
@@ -120,10 +121,19 @@ __global__ void k_gather_bounds(const int64_t *gptr, const int64_t *e0, int64_t 
 
 // Zero the occupancy bits of phase p's operand for its first R rows (all
 // row blocks a tile over R rows can touch).  Block-cooperative.
-__device__ __forceinline__ void zero_occupancy(InstState &s, int p, int32_t R) {
+// Chained-scan compaction of a single instance (see k_compact_edges): status
+// word epochs (30 bits) and the time limit of a wait on a predecessor chunk.
+constexpr uint32_t kEpochMask = (1u << 30) - 1;
+constexpr uint64_t kChainWaitNs = 2000000000ull;  // 2 s
+
+__device__ __forceinline__ void zero_occupancy(InstState &s, int p, int32_t R, int64_t first,
+                                               int64_t stride) {
     if (!s.occ[p]) return;
     const int64_t words = (int64_t)((R + 255) / 256) * 2 * s.occ_words[p];
-    for (int64_t w = threadIdx.x; w < words; w += blockDim.x) s.occ[p][w] = 0;
+    for (int64_t w = first; w < words; w += stride) s.occ[p][w] = 0;
+}
+__device__ __forceinline__ void zero_occupancy(InstState &s, int p, int32_t R) {
+    zero_occupancy(s, p, R, threadIdx.x, blockDim.x);
 }
 
 // Round state and vertex id maps (one block per instance).  In input
@@ -151,6 +161,8 @@ __global__ void k_init(InstState *st, int count, int32_t max_rounds) {
     if (s.e_dirty_rb)
         for (int32_t w = threadIdx.x; w < s.A_rows / 128; w += blockDim.x) s.e_dirty_rb[w] = 0;
     zero_occupancy(s, 0, s.m0);
+    if (s.scan_status)
+        for (int32_t c = threadIdx.x; c < s.scan_chunks; c += blockDim.x) s.scan_status[c] = 0;
     if (threadIdx.x == 0) {
         s.n = s.n0; s.m = s.m0; s.m_dp = s.m0; s.n_next = s.n0;
         s.rounds = 0; s.active = s.status == 0; s.max_rounds = max_rounds; s.changed = 0;
@@ -307,6 +319,10 @@ __global__ void k_plan(InstState *st, Plan *plan, int phase, int tc, BatchCounte
         int64_t tiles = 0;
         if (b < count) {
             const InstState &s = st[b];
+            if (s.scan_status) {  // this phase's compaction: tickets from 0, a new epoch
+                st[b].scan_ticket = 0;
+                st[b].scan_epoch = (s.scan_epoch + 1) & kEpochMask;
+            }
             if (s.active && s.status == 0) {
                 // hyperedges to scatter: phase 0 the current ones; phase 1 the
                 // rows DP saw (the fused pass clears A at those rows and sets
@@ -492,18 +508,66 @@ __global__ void __launch_bounds__(256) k_scatter(InstState *st, const Plan *plan
 
 // ----------------------------------------------------------- compaction --
 
+// Chained scan across the blocks compacting one instance: the exclusive
+// prefix, over chunks 0..c-1 of this launch, of the kept counts, given
+// chunk c's own count `agg` (decoupled look-back, one thread per block).
+// Chunk c first publishes its count, then walks back over its
+// predecessors until one has published its inclusive prefix, and
+// publishes its own.  Returns -1 if a predecessor published nothing within
+// the time limit.  Every predecessor belongs to a block that took its
+// ticket earlier, so it is running.
+__device__ int32_t chain_exclusive(unsigned long long *status, uint32_t epoch, int32_t c,
+                                   int32_t agg) {
+    const unsigned long long tag = (unsigned long long)epoch << 34;
+    if (c == 0) {
+        atomicExch(&status[0], tag | (2ull << 32) | (uint32_t)agg);
+        return 0;
+    }
+    atomicExch(&status[c], tag | (1ull << 32) | (uint32_t)agg);
+    int32_t excl = 0;
+    uint64_t t0 = 0;
+    for (int32_t p = c - 1; p >= 0;) {
+        const unsigned long long w = *reinterpret_cast<volatile unsigned long long *>(&status[p]);
+        const uint32_t flag = (uint32_t)(w >> 32) & 3u;
+        if ((uint32_t)(w >> 34) != epoch || flag == 0) {  // not published in this launch yet
+            const uint64_t t = globaltimer();
+            if (t0 == 0) t0 = t;
+            else if (t - t0 > kChainWaitNs) return -1;
+            continue;
+        }
+        excl += (int32_t)(uint32_t)w;
+        if (flag == 2) break;
+        --p;
+    }
+    atomicExch(&status[c], tag | (2ull << 32) | (uint32_t)(excl + agg));
+    return excl;
+}
+
 // Order-preserving compaction of the hyperedges that DP kept (Algorithm 1's
-// returned rows).  One block per instance; chunked so the in-place update
-// of e_c2o never overwrites an entry not yet read.
+// returned rows), and the zeroed vertex rows of this round's MD pass.  With
+// one block per instance (blockIdx.y), chunked so the in-place update of
+// e_c2o never overwrites an entry not yet read.  With several blocks (a
+// single instance), block t of the ticket order takes chunk t of 1024 rows:
+// it writes only after every earlier chunk has published its count, which
+// each does after reading its rows, and never beyond its own chunk.
 __global__ void k_compact_edges(InstState *st, int count) {
     __shared__ int32_t sh[33];
-    const int b = blockIdx.x;
+    __shared__ int32_t sh_x[2];
+    const int b = blockIdx.y;
     if (b >= count) return;
     InstState &s = st[b];
+    const bool chained = gridDim.x > 1;
+    int32_t c = 0;  // this block's chunk (chained)
+    if (chained) {
+        if (threadIdx.x == 0) sh_x[0] = (int32_t)atomicAdd(&s.scan_ticket, 1u);
+        __syncthreads();
+        c = sh_x[0];
+    }
     if (!s.active || s.status) return;
     const int32_t m = s.m;
-    int32_t carry = 0;
-    for (int32_t base = 0; base < m; base += blockDim.x) {
+    int32_t kept = 0;  // rows kept before this block's chunk (chained: of chunk c)
+    bool last_chunk = false;
+    for (int32_t base = chained ? c * 1024 : 0; base < m; base += blockDim.x) {
         int32_t r = base + threadIdx.x;
         int32_t keep = 0, orig = -1, size = 0;
         if (r < m) {
@@ -514,28 +578,45 @@ __global__ void k_compact_edges(InstState *st, int count) {
         }
         int32_t tot;
         int32_t ex = block_exclusive_scan<int32_t>(keep, &tot, sh);  // syncs after reads
-        if (r < m) {
-            s.e_o2c[orig] = keep ? carry + ex : -1;
-            if (keep) {
-                s.e_c2o[carry + ex] = orig;
-                s.e_s[carry + ex] = size;  // the size this DP pass saw moves with the row
+        if (chained) {
+            if (threadIdx.x == 0)
+                sh_x[1] = chain_exclusive(s.scan_status, s.scan_epoch, c, tot);
+            __syncthreads();
+            kept = sh_x[1];
+            if (kept < 0) {
+                if (threadIdx.x == 0) atomicOr(&s.status, kErrTimeout);
+                return;
             }
         }
-        carry += tot;
+        if (r < m) {
+            s.e_o2c[orig] = keep ? kept + ex : -1;
+            if (keep) {
+                s.e_c2o[kept + ex] = orig;
+                s.e_s[kept + ex] = size;  // the size this DP pass saw moves with the row
+            }
+        }
+        kept += tot;
+        if (chained) {
+            last_chunk = base + 1024 >= m;
+            break;
+        }
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        s.m_dp = carry;
-        s.dp_deleted = m - carry;
+    if (m == 0 && c == 0) last_chunk = true;
+    if (threadIdx.x == 0 && (chained ? last_chunk : true)) {
+        s.m_dp = kept;
+        s.dp_deleted = m - kept;
         if (s.rounds < kTraceRounds) {
             s.trace[s.rounds][0] = m;
             s.trace[s.rounds][1] = s.n;
-            s.trace[s.rounds][2] = carry;
+            s.trace[s.rounds][2] = kept;
         }
     }
-    zero_occupancy(s, 1, s.n);
-    // vertex rows of this round's MD pass
-    for (int32_t r = threadIdx.x; r < s.n; r += blockDim.x) {
+    // vertex rows of this round's MD pass (s.n is not changed here)
+    const int64_t first = chained ? (int64_t)c * 1024 + threadIdx.x : threadIdx.x;
+    const int64_t stride = chained ? (int64_t)gridDim.x * 1024 : blockDim.x;
+    zero_occupancy(s, 1, s.n, first, stride);
+    for (int64_t r = first; r < s.n; r += stride) {
         s.v_deg[r] = 0;
         s.v_maxf[r] = 0;
         s.v_cnt[r] = 0;
@@ -544,17 +625,35 @@ __global__ void k_compact_edges(InstState *st, int count) {
 }
 
 // MD decision (Algorithm 2: delete v_j iff C_j >= max f over E(v_j)),
-// order-preserving compaction of the vertices, and round bookkeeping.
+// order-preserving compaction of the vertices, and round bookkeeping.  One
+// block per instance, or (a single instance) one block per chunk of 1024
+// vertices as in k_compact_edges; then the block of the last chunk keeps
+// the books, and each block clears the next round's rows in its own range.
 __global__ void k_compact_vertices(InstState *st, int count, BatchCounters *ctr,
                                    int32_t *done_list) {
     __shared__ int32_t sh[33];
-    const int b = blockIdx.x;
+    __shared__ int32_t sh_x[2];
+    const int b = blockIdx.y;
     if (b >= count) return;
     InstState &s = st[b];
-    if (s.active && s.status == 0) {
-        const int32_t n = s.n;
-        int32_t carry = 0;
-        for (int32_t base = 0; base < n; base += blockDim.x) {
+    const bool chained = gridDim.x > 1;
+    int32_t c = 0;
+    if (chained) {
+        if (threadIdx.x == 0) sh_x[0] = (int32_t)atomicAdd(&s.scan_ticket, 1u);
+        __syncthreads();
+        c = sh_x[0];
+    }
+    // The state is read before any block can finish the books: the block
+    // of chunk 0 reads it before publishing, and the last chunk waits for
+    // that.  A block without a chunk does only the clears of its range.
+    const bool run = s.active && s.status == 0;
+    const int32_t n = s.n, m_dp = s.m_dp;
+    bool books = !chained;  // this block keeps the books
+    if (run) {
+        int32_t kept = 0;
+        // (chained: chunk 0 runs even when n = 0, so that some block keeps the books)
+        for (int32_t base = chained ? c * 1024 : 0; base < n || (chained && base == 0);
+             base += blockDim.x) {
             int32_t r = base + threadIdx.x;
             int32_t keep = 0, orig = -1;
             if (r < n) {
@@ -567,50 +666,76 @@ __global__ void k_compact_vertices(InstState *st, int count, BatchCounters *ctr,
             }
             int32_t tot;
             int32_t ex = block_exclusive_scan<int32_t>(keep, &tot, sh);
-            if (r < n) {
-                s.v_o2c[orig] = keep ? carry + ex : -1;
-                if (keep) s.v_c2o[carry + ex] = orig;
+            if (chained) {
+                if (threadIdx.x == 0)
+                    sh_x[1] = chain_exclusive(s.scan_status, s.scan_epoch, c, tot);
+                __syncthreads();
+                kept = sh_x[1];
+                if (kept < 0) {
+                    if (threadIdx.x == 0) atomicOr(&s.status, kErrTimeout);
+                    return;
+                }
             }
-            carry += tot;
+            if (r < n) {
+                s.v_o2c[orig] = keep ? kept + ex : -1;
+                if (keep) s.v_c2o[kept + ex] = orig;
+            }
+            kept += tot;
+            if (chained) {
+                books = base + 1024 >= n;
+                break;
+            }
             __syncthreads();
         }
-        if (threadIdx.x == 0) {
-            s.n_next = carry;
-            s.md_deleted = n - carry;
+        if (threadIdx.x == 0 && books) {
+            s.n_next = kept;
+            s.md_deleted = n - kept;
             s.changed = (s.dp_deleted + s.md_deleted) > 0;
-            s.m = s.m_dp;
-            s.n = carry;
+            s.m = m_dp;
+            s.n = kept;
             s.rounds += 1;
             s.md_full = 0;
             if (!s.changed && s.full_edges && s.max_rounds == 0) {
-                s.fe_stage = 1;  // fixpoint: rule FE decides (fe.cu) whether it goes on
+                // fixpoint: rule FE decides (fe.cu) whether it goes on; no
+                // vertex was deleted, so v_del is already all zero
+                s.fe_stage = 1;
             } else if (!s.changed || (s.max_rounds > 0 && s.rounds >= s.max_rounds)) {
                 s.active = 0;
                 if (done_list && ctr) done_list[atomicAdd(&ctr->n_done, 1)] = b;
             }
         }
-        __syncthreads();
-        if (s.fe_stage)  // FE marks the vertices it takes here
-            for (int32_t r = threadIdx.x; r < s.n; r += blockDim.x) s.v_del[r] = 0;
-        if (s.v_dirty) {  // MD candidates of the next round start empty
-            for (int32_t r = threadIdx.x; r < s.n; r += blockDim.x) s.v_dirty[r] = 0;
-            for (int32_t w = threadIdx.x; w < (s.n + 127) / 128; w += blockDim.x)
-                s.v_dirty_rb[w] = 0;
+        // the next round's rows: MD candidates start empty; hyperedge rows
+        // of the DP pass (e_s keeps the sizes).  One block skips them once
+        // the instance has finished; several blocks cannot know that and
+        // clear them anyway, which is harmless.
+        bool next_rows = true;
+        int32_t nv = n;  // vertex rows to clear
+        if (!chained) {
+            __syncthreads();  // the books are kept
+            next_rows = s.active != 0;
+            nv = s.n;
         }
-        // hyperedge rows of the next round's DP pass (e_s keeps the sizes)
-        if (s.active) {
-            for (int32_t r = threadIdx.x; r < s.m; r += blockDim.x) {
+        if (next_rows) {
+            const int64_t first = chained ? (int64_t)c * 1024 + threadIdx.x : threadIdx.x;
+            const int64_t stride = chained ? (int64_t)gridDim.x * 1024 : blockDim.x;
+            if (s.v_dirty) {
+                for (int64_t r = first; r < nv; r += stride) s.v_dirty[r] = 0;
+                for (int64_t w = first; w < (nv + 127) / 128; w += stride) s.v_dirty_rb[w] = 0;
+            }
+            for (int64_t r = first; r < m_dp; r += stride) {
                 s.e_f[r] = s.f[s.e_c2o[r]];
                 s.e_del[r] = 0;
             }
             if (s.e_dirty_rb)
-                for (int32_t w = threadIdx.x; w < (s.m + 127) / 128; w += blockDim.x)
-                    s.e_dirty_rb[w] = 0;
-            zero_occupancy(s, 0, s.m);
-            if (threadIdx.x == 0) s.has_loose = 0;
+                for (int64_t w = first; w < (m_dp + 127) / 128; w += stride) s.e_dirty_rb[w] = 0;
+            zero_occupancy(s, 0, m_dp, first, stride);
+            if (first == 0) s.has_loose = 0;
         }
+    } else {
+        books = !chained || c == 0;  // nothing changes: one block reports it
     }
-    if (threadIdx.x == 0 && ctr) {
+    if (threadIdx.x == 0 && ctr && books) {
+        __threadfence();
         atomicAdd(&ctr->active, s.active);
         atomicAdd(&ctr->n_alive, s.n);
         atomicAdd(&ctr->m_alive, s.m);
@@ -859,7 +984,8 @@ static void launch_scatter(InstState *st, const Plan *plan, bool set, bool dense
 cudaError_t launch_round_phase(InstState *st, Plan *plan, BatchCounters *ctr, int count,
                                int phase, int contraction, int sms, int32_t *kerr,
                                cudaStream_t s, cudaEvent_t ev_contract_begin,
-                               cudaEvent_t ev_contract_end, int32_t *done_list) {
+                               cudaEvent_t ev_contract_end, int32_t *done_list,
+                               int compact_blocks) {
     const bool tc = contraction == kFp8;
     k_plan<<<1, 1024, 0, s>>>(st, plan, phase, tc ? (tc_pairs() ? 2 : 1) : 0, ctr);
     const int grid = grid_for(sms, 8);
@@ -880,8 +1006,10 @@ cudaError_t launch_round_phase(InstState *st, Plan *plan, BatchCounters *ctr, in
     // (the DP pass's clear of A runs inside the MD set pass, which walks the
     // same incidences)
     if (phase == 1) launch_scatter<1>(st, plan, false, tc, grid, s);
-    if (phase == 0) k_compact_edges<<<count, 1024, 0, s>>>(st, count);
-    else k_compact_vertices<<<count, 1024, 0, s>>>(st, count, ctr, done_list);
+    // compact_blocks > 1: a single instance, one block per chunk of 1024 ids
+    const dim3 cgrid(compact_blocks > 1 ? compact_blocks : 1, count);
+    if (phase == 0) k_compact_edges<<<cgrid, 1024, 0, s>>>(st, count);
+    else k_compact_vertices<<<cgrid, 1024, 0, s>>>(st, count, ctr, done_list);
     return cudaGetLastError();
 }
 

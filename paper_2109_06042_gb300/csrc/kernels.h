@@ -39,7 +39,8 @@ cudaError_t launch_build(InstState *st, int count, int32_t max_rounds, int64_t m
 cudaError_t launch_round_phase(InstState *st, Plan *plan, BatchCounters *ctr, int count,
                                int phase, int contraction, int sms, int32_t *kerr,
                                cudaStream_t s, cudaEvent_t ev_contract_begin,
-                               cudaEvent_t ev_contract_end, int32_t *done_list = nullptr);
+                               cudaEvent_t ev_contract_end, int32_t *done_list = nullptr,
+                               int compact_blocks = 1);
 // End of one round of the device-side fixpoint loop: keep looping while
 // some instance is active, no error was raised and fewer than round_cap
 // rounds ran (hitting the cap raises kErrRoundCap).

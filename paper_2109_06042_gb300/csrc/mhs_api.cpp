@@ -51,6 +51,10 @@ inline int64_t kpad_words(int64_t K) {
 }
 // occupancy words per row block: one bit per K block of kOccK columns
 inline int64_t occ_words(int64_t K) { return (kpad_bytes(K) / kOccK + 31) / 32; }
+// chunks of 1024 ids in the larger of an instance's two id ranges
+inline int64_t compact_chunks(int64_t n0, int64_t m0) {
+    return (std::max<int64_t>(std::max(n0, m0), 1) + 1023) / 1024;
+}
 
 }  // namespace
 
@@ -208,6 +212,7 @@ struct mhs_instance {
     BatchCounters *hctr = nullptr;
     int32_t *hkerr = nullptr;
     int64_t max_nnz = 0, max_m = 0, max_n = 0;
+    int32_t compact_blocks = 1;  // compaction blocks per instance (> 1: chained scan)
     // arena offsets of the batch-wide input arrays
     int64_t in_eptr = 0, in_evtx = 0, in_f = 0;
     int64_t sum_m1 = 0, sum_nnz = 0, sum_m = 0;
@@ -306,7 +311,7 @@ struct Layout {  // byte offsets inside the arena for one instance
     int64_t occ0, occ1;
     int64_t eptr, evtx, f;
     int64_t v_o2c, v_c2o, e_o2c, e_c2o, e_f, e_s, v_deg, v_maxf, v_cnt, e_del, v_del, forced;
-    int64_t e_dirty_rb, v_dirty, v_dirty_rb, e_prev, e_rec;
+    int64_t e_dirty_rb, v_dirty, v_dirty_rb, e_prev, e_rec, scan;
     int64_t A, At, Ab, Atb;
 };
 
@@ -386,6 +391,8 @@ mhs_status create(int32_t count, const int32_t *n, const int32_t *m, const int64
         L.v_dirty = ar.take(n0);
         L.e_prev = ar.take(4 * m0);
         L.e_rec = dense ? ar.take(16 * m0) : -1;
+        // a single instance compacts with one block per chunk of 1024 ids
+        L.scan = count == 1 ? ar.take(8 * compact_chunks(n0, m0)) : -1;
         L.e_dirty_rb = ar.take(round_up(std::max<int64_t>(m0, 1), kRowAlign) / kTcM);
         L.v_dirty_rb = ar.take(round_up(std::max<int64_t>(n0, 1), kRowAlign) / kTcM);
         if (dense) {
@@ -487,6 +494,12 @@ mhs_status create(int32_t count, const int32_t *n, const int32_t *m, const int64
         s.forced = L.forced >= 0 ? base + L.forced : nullptr;
         s.v_dirty = base + L.v_dirty;
         s.e_prev = reinterpret_cast<int32_t *>(base + L.e_prev);
+        s.scan_status =
+            L.scan >= 0 ? reinterpret_cast<unsigned long long *>(base + L.scan) : nullptr;
+        s.scan_chunks = L.scan >= 0 ? (int32_t)compact_chunks(s.n0, s.m0) : 0;
+        if (s.scan_chunks > 1) h->compact_blocks = s.scan_chunks;
+        s.scan_ticket = 0;
+        s.scan_epoch = 0;
         s.e_rec = L.e_rec >= 0 ? reinterpret_cast<int4 *>(base + L.e_rec) : nullptr;
         s.e_dirty_rb = base + L.e_dirty_rb;
         s.v_dirty_rb = base + L.v_dirty_rb;
@@ -606,11 +619,12 @@ cudaError_t enqueue_round(mhs_instance *h, bool with_events) {
     cudaError_t e = launch_round_phase(h->dstate, h->dplan, h->dctr, h->count, 0, h->contraction,
                                        h->sms, h->dkerr, h->stream,
                                        with_events ? h->ev[0] : nullptr,
-                                       with_events ? h->ev[1] : nullptr);
+                                       with_events ? h->ev[1] : nullptr, nullptr,
+                                       h->compact_blocks);
     if (e != cudaSuccess) return e;
     e = launch_round_phase(h->dstate, h->dplan, h->dctr, h->count, 1, h->contraction, h->sms,
                            h->dkerr, h->stream, with_events ? h->ev[2] : nullptr,
-                           with_events ? h->ev[3] : nullptr);
+                           with_events ? h->ev[3] : nullptr, nullptr, h->compact_blocks);
     if (e == cudaSuccess && h->opt.full_edges)
         e = launch_full_edges(h->dstate, h->count, h->dctr, nullptr, h->sms, h->stream);
     if (e != cudaSuccess) return e;
@@ -670,10 +684,12 @@ mhs_status build_loop_graph(mhs_instance *h) {
                                       cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return bail(e, "capture");
     cudaError_t e1 = launch_round_phase(h->dstate, h->dplan, h->dctr, h->count, 0, h->contraction,
-                                        h->sms, h->dkerr, h->stream, nullptr, nullptr);
+                                        h->sms, h->dkerr, h->stream, nullptr, nullptr, nullptr,
+                                        h->compact_blocks);
     if (e1 == cudaSuccess)
         e1 = launch_round_phase(h->dstate, h->dplan, h->dctr, h->count, 1, h->contraction, h->sms,
-                                h->dkerr, h->stream, nullptr, nullptr);
+                                h->dkerr, h->stream, nullptr, nullptr, nullptr,
+                                h->compact_blocks);
     if (e1 == cudaSuccess && h->opt.full_edges)
         e1 = launch_full_edges(h->dstate, h->count, h->dctr, nullptr, h->sms, h->stream);
     if (e1 == cudaSuccess)

@@ -75,6 +75,15 @@ struct InstState {
     int32_t *v_o2c, *v_c2o;
     int32_t *e_o2c, *e_c2o;
     int32_t *e_prev;       // [m0] input id of each row as DP saw it (before compaction)
+    // Compaction of a single instance by several blocks (a chained scan over
+    // chunks of 1024 ids, one per block): per chunk a status word
+    // {epoch << 34 | flag << 32 | count}; blocks take chunks by ticket, in
+    // arrival order.  k_plan resets the ticket and advances the epoch before
+    // every phase.  nullptr: one block compacts the instance.
+    unsigned long long *scan_status;  // [scan_chunks]
+    int32_t scan_chunks;
+    uint32_t scan_ticket;
+    uint32_t scan_epoch;
 
     // epilogue inputs, indexed by current id
     int32_t *e_f;          // f of current hyperedge
