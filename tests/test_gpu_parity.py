@@ -73,6 +73,30 @@ def test_ragged_tile_boundaries(mhs, mode, n, m):
 
 
 @pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("n,m", [(1024, 1024), (1025, 1024), (1000, 2049), (3073, 1023),
+                                 (2048, 4100)])
+def test_compaction_chunk_boundaries(mhs, mode, n, m):
+    """A single instance compacts with one block per 1024 ids (a chained
+    scan across blocks): id ranges on, just past and well past the chunk
+    edges, with n and m on different sides of them, plus the round-by-round
+    path, whose graphs launch the same kernels."""
+    for seed in range(2):
+        inst = I.uniform_random(n, m, 1, 10, 3, n // 8, 61_000 + 7 * n + m + seed)
+        ref = O.reduce(inst)
+        _same(mhs.kernelize(inst, contraction=mode), ref, f"seed {seed}")
+    with mhs.Instance.load(inst, contraction=mode) as h:
+        r = 0
+        while True:
+            st = h.reduce_round()
+            r += 1
+            ref = O.reduce(inst, max_rounds=r)
+            _same(h.result(), ref, f"round {r}")
+            if not ref["changed"]:
+                assert st["changed"] == 0
+                break
+
+
+@pytest.mark.parametrize("mode", MODES)
 def test_round_by_round(mhs, mode):
     """mhs_reduce_round after each round equals the oracle's state after as many rounds."""
     for seed in range(5):
