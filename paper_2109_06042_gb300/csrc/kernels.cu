@@ -613,10 +613,11 @@ __global__ void k_compact_edges(InstState *st, int count) {
         }
     }
     // vertex rows of this round's MD pass (s.n is not changed here)
-    const int64_t first = chained ? (int64_t)c * 1024 + threadIdx.x : threadIdx.x;
-    const int64_t stride = chained ? (int64_t)gridDim.x * 1024 : blockDim.x;
-    zero_occupancy(s, 1, s.n, first, stride);
-    for (int64_t r = first; r < s.n; r += stride) {
+    const int32_t first = chained ? c * 1024 + (int32_t)threadIdx.x : (int32_t)threadIdx.x;
+    const int32_t stride = chained ? (int32_t)gridDim.x * 1024 : (int32_t)blockDim.x;
+    const int32_t nv = s.n;
+    zero_occupancy(s, 1, nv, first, stride);
+    for (int32_t r = first; r < nv; r += stride) {
         s.v_deg[r] = 0;
         s.v_maxf[r] = 0;
         s.v_cnt[r] = 0;
@@ -715,27 +716,26 @@ __global__ void k_compact_vertices(InstState *st, int count, BatchCounters *ctr,
             next_rows = s.active != 0;
             nv = s.n;
         }
-        if (next_rows) {
-            const int64_t first = chained ? (int64_t)c * 1024 + threadIdx.x : threadIdx.x;
-            const int64_t stride = chained ? (int64_t)gridDim.x * 1024 : blockDim.x;
+        if (next_rows) {  // (32 bits suffice: blocks x 1024 < max(n0, m0) + 1024)
+            const int32_t first = chained ? c * 1024 + (int32_t)threadIdx.x : (int32_t)threadIdx.x;
+            const int32_t stride = chained ? (int32_t)gridDim.x * 1024 : (int32_t)blockDim.x;
             if (s.v_dirty) {
-                for (int64_t r = first; r < nv; r += stride) s.v_dirty[r] = 0;
-                for (int64_t w = first; w < (nv + 127) / 128; w += stride) s.v_dirty_rb[w] = 0;
+                for (int32_t r = first; r < nv; r += stride) s.v_dirty[r] = 0;
+                for (int32_t w = first; w < (nv + 127) / 128; w += stride) s.v_dirty_rb[w] = 0;
             }
-            for (int64_t r = first; r < m_dp; r += stride) {
+            for (int32_t r = first; r < m_dp; r += stride) {
                 s.e_f[r] = s.f[s.e_c2o[r]];
                 s.e_del[r] = 0;
             }
             if (s.e_dirty_rb)
-                for (int64_t w = first; w < (m_dp + 127) / 128; w += stride) s.e_dirty_rb[w] = 0;
+                for (int32_t w = first; w < (m_dp + 127) / 128; w += stride) s.e_dirty_rb[w] = 0;
             zero_occupancy(s, 0, m_dp, first, stride);
             if (first == 0) s.has_loose = 0;
         }
     } else {
         books = !chained || c == 0;  // nothing changes: one block reports it
     }
-    if (threadIdx.x == 0 && ctr && books) {
-        __threadfence();
+    if (threadIdx.x == 0 && ctr && books) {  // read by a later kernel
         atomicAdd(&ctr->active, s.active);
         atomicAdd(&ctr->n_alive, s.n);
         atomicAdd(&ctr->m_alive, s.m);
