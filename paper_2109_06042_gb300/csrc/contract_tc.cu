@@ -253,6 +253,14 @@ __device__ __forceinline__ void tile_info(const InstState *st, int phase, int64_
     ti->nk = ((K > 0 ? K : 1) + kTcK - 1) / kTcK;
 }
 
+// The epilogue's per-row record of row or column j (zero past R): DP / SE
+// {f, f - |e| (SE: |e|), input id}; MD {deg, 0, input id}.
+__device__ __forceinline__ int4 epi_record(const InstState &s, int phase, int32_t j, int32_t R) {
+    if (j >= R) return make_int4(0, 0, 0, 0);
+    if (phase == 0) return s.e_rec[j];
+    return make_int4(s.v_deg[j], 0, s.v_c2o[j], 0);
+}
+
 // K blocks of a tile where both operands hold a nonzero: the occupancy
 // bits of row block bi AND those of the two row blocks of column block bj.
 // A bit covers kOccK = 64 columns, half a K block: a K block is loaded when
@@ -654,6 +662,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int half = (warp - 2) >> 2;   // which 128 columns of the tile
         const int et = threadIdx.x - 64;
         TileInfo ti;
+        // The next tile's records, loaded into registers while this tile
+        // waits for its accumulator and is tested (the records do not
+        // change during a launch): the entry they belong to, or -1.
+        int64_t pre_entry = -1;
+        int4 pre_col = make_int4(0, 0, 0, 0), pre_row = make_int4(0, 0, 0, 0);
+        static_assert(kEpiThreads == kTcN, "one staged column per epilogue thread");
         for (int it = 0;; ++it) {
             const int slot = it % kRing;
             if (!epi_bar_and(ring_wait(it))) {
@@ -675,42 +689,41 @@ __global__ void __launch_bounds__(kThreads, 1)
             bool vals_small = true;  // every staged value fits FP16 exactly, with room for a sum
             epi_bar();  // every epilogue thread has read the entry
             if (et == 0) ring_release(it);
-            for (int c = et; c < kTcN; c += kEpiThreads) {
-                const int32_t j = j0 + c;
-                float a = 0.f, bb = 0.f;
-                int32_t o = 0;
-                if (j < R) {
-                    if (phase == 0) {  // {f, f - s (SE: s), input id}
-                        const int4 rec = s.e_rec[j];
-                        a = (float)rec.x;
-                        bb = (float)rec.y;
-                        o = rec.z;
-                    } else {
-                        a = (float)s.v_deg[j];
-                        o = s.v_c2o[j];
-                    }
-                }
-                ctl->colAB[c] = make_float2(a, bb);
-                ctl->colO[c] = o;
-                ctl->colA16[c] = __float2half_rn(a);
-                ctl->colB16[c] = __float2half_rn(bb);
-                vals_small = vals_small && fabsf(a) <= 1024.f && fabsf(bb) <= 1024.f;
+            const bool have = pre_entry == entry;
+            {  // column j0 + et
+                const int4 rec = have ? pre_col : epi_record(s, phase, j0 + et, R);
+                const float a = (float)rec.x, bb = (float)rec.y;
+                ctl->colAB[et] = make_float2(a, bb);
+                ctl->colO[et] = rec.z;
+                ctl->colA16[et] = __float2half_rn(a);
+                ctl->colB16[et] = __float2half_rn(bb);
+                vals_small = fabsf(a) <= 1024.f && fabsf(bb) <= 1024.f;
             }
-            float ri_f = 0.f, ri_a = 0.f;  // DP: f_i, f_i - s_i ; SE: f_i, s_i ; MD: d_i
-            int32_t ri_o = 0;              // input index of row i
-            if (i < R) {
-                if (phase == 0) {
-                    const int4 rec = s.e_rec[i];
-                    ri_f = (float)rec.x;
-                    ri_a = (float)rec.y;
-                    ri_o = rec.z;
-                } else {
-                    ri_f = (float)s.v_deg[i];
-                    ri_o = s.v_c2o[i];
-                }
-            }
+            // DP: f_i, f_i - s_i ; SE: f_i, s_i ; MD: d_i ; and the input index of row i
+            const int4 rrec = have ? pre_row : epi_record(s, phase, i, R);
+            const float ri_f = (float)rrec.x, ri_a = (float)rrec.y;
+            const int32_t ri_o = rrec.z;
             vals_small = vals_small && fabsf(ri_f) <= 1024.f && fabsf(ri_a) <= 1024.f;
             const bool tile_small = epi_bar_and(vals_small);  // also publishes the staged columns
+            // Load the next tile's records if its entry is published (it
+            // usually is: the producer publishes one entry ahead).
+            pre_entry = -1;
+            {
+                const int nk = it + 1;
+                const uint32_t nbar = smem_u32(&ctl->ring_full[nk % kRing]);
+                const uint32_t npar = (nk / kRing) & 1;
+                if (kPair ? mbar_try_cl(nbar, npar) : mbar_try(nbar, npar)) {
+                    const int64_t ne = *reinterpret_cast<volatile int64_t *>(&ctl->ring[nk % kRing]);
+                    if (ne >= 0) {
+                        TileInfo nt;
+                        tile_info(st, phase, ne, &nt, kPair, rank);
+                        const InstState &ns = st[nt.b];
+                        pre_col = epi_record(ns, phase, nt.bj * kTcN + et, nt.R);
+                        pre_row = epi_record(ns, phase, nt.bi * kTcM + 32 * q + lane, nt.R);
+                        pre_entry = ne;
+                    }
+                }
+            }
             const bool ok = epi_bar_and(mbar_wait(smem_u32(&ctl->tmem_full[acc]), acc_phase, abort, kWaitNs));
             if (!ok) { *abort = 1; break; }
             tc_fence_after();
