@@ -9,6 +9,8 @@
 // tcgen05 FP8) computes the pair counts of Eq. (1) / Eq. (2) tile by tile
 // and never writes them out: the epilogue turns each count into the
 // deletion flags of Algorithm 1 or the dominator counts of Algorithm 2.
+#include <algorithm>
+
 #include <cuda_runtime.h>
 
 #include "bounded_wait.cuh"
@@ -140,30 +142,32 @@ __device__ __forceinline__ void zero_occupancy(InstState &s, int p, int32_t R) {
 // layout the hyperedge maps are the identity too; in sorted layout they are
 // filled by the k_layout_* kernels below, whose buckets (v_cnt) and cursors
 // (v_deg) are zeroed here.
+// (blockIdx.y = instance; the blocks of an instance split its ranges)
 __global__ void k_init(InstState *st, int count, int32_t max_rounds) {
-    const int b = blockIdx.x;
+    const int b = blockIdx.y;
     if (b >= count) return;
     InstState &s = st[b];
-    for (int32_t v = threadIdx.x; v < s.n0; v += blockDim.x) { s.v_o2c[v] = v; s.v_c2o[v] = v; }
+    const int32_t t0 = blockIdx.x * blockDim.x + threadIdx.x, ts = gridDim.x * blockDim.x;
+    for (int32_t v = t0; v < s.n0; v += ts) { s.v_o2c[v] = v; s.v_c2o[v] = v; }
     if (s.layout_sorted == 2)  // degrees for the vertex layout (v_maxf is free until MD)
-        for (int32_t v = threadIdx.x; v < s.n0; v += blockDim.x) s.v_maxf[v] = 0;
+        for (int32_t v = t0; v < s.n0; v += ts) s.v_maxf[v] = 0;
     if (s.layout_sorted) {
-        for (int32_t v = threadIdx.x; v <= s.n0; v += blockDim.x) { s.v_cnt[v] = 0; s.v_deg[v] = 0; }
+        for (int32_t v = t0; v <= s.n0; v += ts) { s.v_cnt[v] = 0; s.v_deg[v] = 0; }
     } else {
-        for (int32_t e = threadIdx.x; e < s.m0; e += blockDim.x) { s.e_o2c[e] = e; s.e_c2o[e] = e; }
+        for (int32_t e = t0; e < s.m0; e += ts) { s.e_o2c[e] = e; s.e_c2o[e] = e; }
     }
     if (s.forced)
-        for (int32_t v = threadIdx.x; v < s.n0; v += blockDim.x) s.forced[v] = 0;
+        for (int32_t v = t0; v < s.n0; v += ts) s.forced[v] = 0;
     if (s.v_dirty)
-        for (int32_t v = threadIdx.x; v < s.n0; v += blockDim.x) s.v_dirty[v] = 0;
+        for (int32_t v = t0; v < s.n0; v += ts) s.v_dirty[v] = 0;
     if (s.v_dirty_rb)
-        for (int32_t w = threadIdx.x; w < s.At_rows / 128; w += blockDim.x) s.v_dirty_rb[w] = 0;
+        for (int32_t w = t0; w < s.At_rows / 128; w += ts) s.v_dirty_rb[w] = 0;
     if (s.e_dirty_rb)
-        for (int32_t w = threadIdx.x; w < s.A_rows / 128; w += blockDim.x) s.e_dirty_rb[w] = 0;
-    zero_occupancy(s, 0, s.m0);
+        for (int32_t w = t0; w < s.A_rows / 128; w += ts) s.e_dirty_rb[w] = 0;
+    zero_occupancy(s, 0, s.m0, t0, ts);
     if (s.scan_status)
-        for (int32_t c = threadIdx.x; c < s.scan_chunks; c += blockDim.x) s.scan_status[c] = 0;
-    if (threadIdx.x == 0) {
+        for (int32_t c = t0; c < s.scan_chunks; c += ts) s.scan_status[c] = 0;
+    if (t0 == 0) {
         s.n = s.n0; s.m = s.m0; s.m_dp = s.m0; s.n_next = s.n0;
         s.rounds = 0; s.active = s.status == 0; s.max_rounds = max_rounds; s.changed = 0;
         s.dp_deleted = 0; s.md_deleted = 0; s.has_loose = 0;
@@ -254,20 +258,33 @@ __global__ void k_layout_keys(InstState *st, int count) {
     }
 }
 
-// Sorted layout, step 2 (one block per instance): bucket starts in v_deg.
+// Sorted layout, step 2 (one block per instance): bucket starts in v_deg,
+// an exclusive scan of the n0 + 1 bucket counts, 8 consecutive buckets per
+// thread.
 __global__ void k_layout_scan(InstState *st, int count) {
     __shared__ int32_t sh[33];
+    constexpr int kPer = 8;
     const int b = blockIdx.x;
     if (b >= count) return;
     InstState &s = st[b];
     if (!s.layout_sorted || s.status) return;
+    const int32_t nb = s.n0 + 1;
     int32_t carry = 0;
-    for (int32_t base = 0; base <= s.n0; base += blockDim.x) {
-        const int32_t i = base + threadIdx.x;
-        const int32_t x = i <= s.n0 ? s.v_cnt[i] : 0;
+    for (int32_t base = 0; base < nb; base += blockDim.x * kPer) {
+        const int32_t i0 = base + threadIdx.x * kPer;
+        int32_t x[kPer], sum = 0;
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            x[k] = i0 + k < nb ? s.v_cnt[i0 + k] : 0;
+            sum += x[k];
+        }
         int32_t tot;
-        const int32_t ex = block_exclusive_scan<int32_t>(x, &tot, sh);
-        if (i <= s.n0) s.v_deg[i] = carry + ex;
+        int32_t ex = carry + block_exclusive_scan<int32_t>(sum, &tot, sh);
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            if (i0 + k < nb) s.v_deg[i0 + k] = ex;
+            ex += x[k];
+        }
         carry += tot;
     }
 }
@@ -956,10 +973,11 @@ cudaError_t launch_gather_bounds(const int64_t *gptr, const int64_t *e0, int64_t
 
 cudaError_t launch_build(InstState *st, int count, int32_t max_rounds, int64_t max_nnz,
                          int64_t max_m, int64_t max_n, cudaStream_t s) {
-    (void)max_n;
     const int gx = per_instance_grid(max_m, count);
     const int gz = per_instance_grid(max_nnz, count);
-    k_init<<<count, 1024, 0, s>>>(st, count, max_rounds);
+    // a single instance splits its initial ranges over blocks
+    const int gi = count > 1 ? 1 : (int)std::min<int64_t>((std::max(max_m, max_n) + 4095) / 4096, 152);
+    k_init<<<dim3(gi > 0 ? gi : 1, count), 1024, 0, s>>>(st, count, max_rounds);
     k_vertex_degrees<<<dim3(gz, count), 256, 0, s>>>(st, count);
     k_vertex_layout<<<count, 1024, 0, s>>>(st, count);
     k_layout_keys<<<dim3(gx, count), 256, 0, s>>>(st, count);
