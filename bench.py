@@ -378,7 +378,7 @@ def run_ours(args, rank, world, dist):
         peak = 2.0 * peaks["bf16_tflops"]
         achieved = flops / (contract_ms / args.steps / 1e3) / 1e12
         # tensor work actually issued (block-sparse skipping leaves out zero blocks)
-        issued = kblocks * 2.0 * 128 * 256 * 128 / (contract_ms / 1e3) / 1e12
+        issued = kblocks * 2.0 * 128 * 256 * 64 / (contract_ms / 1e3) / 1e12
         roof = {"bound": "tensor", "achieved": round(achieved, 2), "peak": round(peak, 1),
                 "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
                 "traffic": measured_traffic(args, desc),

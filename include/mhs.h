@@ -283,8 +283,8 @@ mhs_status mhs_export(const mhs_instance *inst, int32_t index, int32_t *edge_ptr
  */
 mhs_status mhs_set_timing(mhs_instance *inst, int32_t enable);
 /*
- * Tensor-core work done since load (tcgen05 contraction): K blocks of
- * 128 x 256 x 128 MACs issued and tiles contracted.  With block-sparse
+ * Tensor-core work done since load (tcgen05 contraction): K steps of
+ * 128 x 256 x 64 MACs issued and tiles contracted.  With block-sparse
  * skipping this is below the dense formulation's count.
  */
 mhs_status mhs_work_stats(const mhs_instance *inst, int64_t *mma_kblocks, int64_t *mma_tiles);

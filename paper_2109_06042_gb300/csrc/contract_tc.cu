@@ -40,6 +40,14 @@ constexpr int kStages = 4;
 constexpr int kABytes = kTcM * kTcK;            // 16 KB
 constexpr int kBBytes = kTcN * kTcK;            // 32 KB
 constexpr int kStageBytes = kABytes + kBBytes;  // 48 KB
+// A stage whose K block shares a nonzero in only one of its two halves
+// loads just that half (kOccK columns of each operand, 64-byte swizzle,
+// 8 KB per 128-row box) into the front of the same slots.
+constexpr int kHalfBox = kTcM * kOccK;          // 8 KB
+constexpr int kHalfStageBytes = 3 * kHalfBox;   // 24 KB
+static_assert(2 * kOccK == kTcK, "a stage is two occupancy blocks");
+// An operand's tensor maps: the full-stage map, then the half-stage map.
+constexpr int kTmapBytes = 128;
 constexpr int kAccCols = kTcN;                  // FP32 columns per accumulator
 constexpr int kTmemCols = 2 * kAccCols;         // 512
 constexpr int kEpiWarps = 8;                    // two per TMEM lane quarter
@@ -98,16 +106,17 @@ __device__ __forceinline__ void tc_fence_before() {
 __device__ __forceinline__ void tc_fence_after() {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms
-// of 1024 bytes (stride byte offset), version 1 (bits 46-48).
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)1 << 16;            // leading byte offset (unused for swizzled K-major)
-    d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset
-    d |= (uint64_t)1 << 46;            // descriptor version
-    d |= (uint64_t)2 << 61;            // SWIZZLE_128B
-    return d;
+// Shared-memory matrix descriptors, K-major, version 1 (bits 46-48), the
+// leading byte offset unused (1): a full stage has 128-byte swizzled rows in
+// 8-row atoms of 1024 bytes (stride byte offset, layout type 2); a half
+// stage 64-byte swizzled rows in atoms of 512 bytes (layout type 4).  The
+// start address (bits 0-13, in 16-byte units) is OR-ed in per MMA.
+constexpr uint64_t kDescFull =
+    ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+constexpr uint64_t kDescHalf =
+    ((uint64_t)1 << 16) | ((uint64_t)(512 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
+__device__ __forceinline__ uint64_t smem_desc(uint64_t layout, uint32_t addr) {
+    return layout | (uint64_t)((addr & 0x3FFFFu) >> 4);
 }
 // Instruction descriptor, kind::f8f6f4: D = F32, A = B = E4M3, both K-major,
 // N = 256, M = 128.
@@ -265,12 +274,14 @@ __device__ __forceinline__ int4 epi_record(const InstState &s, int phase, int32_
 // bits of row block bi AND those of the two row blocks of column block bj.
 // A bit covers kOccK = 64 columns, half a K block: a K block is loaded when
 // either of its halves is shared, so a nonzero of one operand in the low
-// half and one of the other in the high half do not cost a load.  Every
-// role walks the same sequence.
+// half and one of the other in the high half do not cost a load; kit_next
+// leaves in `halves` which halves are shared (1: low, 2: high, 3: both).
+// Every role walks the same sequence.
 struct KIter {
     const uint32_t *a, *a1, *b0, *b1;
     int32_t nkw, w, nk;
     uint32_t mask;
+    uint32_t halves;
     bool all;
 };
 // For a pair tile the rows are both row blocks 2P and 2P+1 (the union).
@@ -306,6 +317,7 @@ __device__ __forceinline__ int32_t kit_next(KIter &k) {
         }
     }
     const int32_t bit = (__ffs(k.mask) - 1) & ~1;  // the K block's two bits
+    k.halves = (k.mask >> bit) & 3u;
     k.mask &= ~(3u << bit);
     return (k.w * 32 + bit) >> 1;
 }
@@ -391,7 +403,8 @@ struct __align__(8) SharedCtl {
     uint64_t ring_full[kRing];   // entry published (producer arrives)
     uint64_t ring_empty[kRing];  // entry read by the MMA thread and the epilogue (2 arrivals)
     int64_t ring[kRing];         // packed tile entry, -1 = no more tiles
-    uint32_t stage_last[kStages];  // the stage is its tile's last (written by the producer)
+    uint32_t stage_last[kStages];  // bit 0: the stage ends its tile; bit 1: a half stage
+                                   // (written by the producer)
     uint64_t drain;
     uint32_t tmem_base;
     int abort;
@@ -508,6 +521,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             TileInfo ti, nx;
             KIter kit, nkit;
             int32_t kb = -1, nkb = -1;
+            uint32_t hv = 3u, nhv = 3u;
             int it = 0;
             int64_t cur = publish(0);
             aborted = cur == -2;
@@ -515,6 +529,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tile_info(st, phase, cur, &ti, kPair, rank);
                 kit_init(kit, st[ti.b], phase, ti);
                 kb = kit_next(kit);
+                hv = kit.halves;
             }
             while (cur >= 0 && !aborted) {
                 const int64_t nxt = publish(it + 1);
@@ -526,11 +541,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                     tile_info(st, phase, nxt, &nx, kPair, rank);
                     kit_init(nkit, st[nx.b], phase, nx);
                     nkb = kit_next(nkit);
+                    nhv = nkit.halves;
                 }
                 const InstState &s = st[ti.b];
-                const void *tmap = phase == 0 ? s.tmap_A : s.tmap_At;
+                const void *tmap = phase == 0 ? s.tmap_A : s.tmap_At;  // full map, then half map
+                const void *tmap64 = static_cast<const uint8_t *>(tmap) + kTmapBytes;
                 if (tmap != fenced) {  // the maps were written to global memory by a copy
                     asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmap)
+                                 : "memory");
+                    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmap64)
                                  : "memory");
                     fenced = tmap;
                 }
@@ -539,31 +558,42 @@ __global__ void __launch_bounds__(kThreads, 1)
                     // one K block ahead: the MMA thread learns from the stage
                     // whether it ends the tile, and walks no occupancy bits
                     const int32_t kb_next = kit_next(kit);
+                    const uint32_t hv_next = kit.halves;
                     if (!mbar_wait(smem_u32(&ctl->empty[stage]), phase_bit ^ 1, abort, kWaitNs)) {
                         aborted = true;
                         break;
                     }
-                    ctl->stage_last[stage] = kb_next < 0;  // published by the arrive below
+                    // a whole K block, or one shared half: kOccK columns at x (a
+                    // multiple of 64 bytes) through the half map, into the front
+                    // of each slot; the flag tells the MMA thread which, and
+                    // whether the stage ends its tile (published by the arrive)
+                    const bool whole = hv == 3u;
+                    ctl->stage_last[stage] = (kb_next < 0 ? 1u : 0u) | (whole ? 0u : 2u);
                     const uint32_t full = smem_u32(&ctl->full[stage]);
-                    mbar_expect_tx(full, kStageBytes);
                     const uint32_t sa = smem_u32(smem + stage * kStageBytes);
                     const uint32_t sb = sa + kABytes;
-                    tma_load_2d(sa, tmap, kb * kTcK, yi, full);
+                    const void *map = whole ? tmap : tmap64;
+                    const int32_t x = kb * kTcK + (hv == 2u ? kOccK : 0);
+                    const uint32_t box = whole ? (uint32_t)kABytes : (uint32_t)kHalfBox;
+                    mbar_expect_tx(full, whole ? kStageBytes : kHalfStageBytes);
+                    tma_load_2d(sa, map, x, yi, full);
                     if (kPair) {  // this CTA's half of the rows j, to both CTAs
-                        tma_load_2d_mc(sb + rank * kABytes, tmap, kb * kTcK, yj + (int32_t)rank * kTcM,
-                                       full, (uint16_t)0x3);
+                        tma_load_2d_mc(sb + rank * box, map, x, yj + (int32_t)rank * kTcM, full,
+                                       (uint16_t)0x3);
                     } else {
-                        tma_load_2d(sb, tmap, kb * kTcK, yj, full);
-                        tma_load_2d(sb + kABytes, tmap, kb * kTcK, yj + kTcM, full);
+                        tma_load_2d(sb, map, x, yj, full);
+                        tma_load_2d(sb + box, map, x, yj + kTcM, full);
                     }
                     ++issued;
                     if (++stage == kStages) { stage = 0; phase_bit ^= 1; }
                     kb = kb_next;
+                    hv = hv_next;
                 }
                 cur = nxt;
                 ti = nx;
                 kit = nkit;
                 kb = nkb;
+                hv = nhv;
                 ++it;
             }
             if (aborted) {  // let the loads still in flight land before exiting
@@ -626,19 +656,24 @@ __global__ void __launch_bounds__(kThreads, 1)
                     tc_fence_after();
                     // The flag must be read before this stage goes back to the
                     // producer: the first MMA's accumulate flag depends on the
-                    // loaded word (which is 0 or 1, never 2), so the MMAs, and
-                    // the commit that releases the stage, issue after the load.
+                    // loaded word (which is below 4), so the MMAs, and the
+                    // commit that releases the stage, issue after the load.
                     const uint32_t lastw =
                         *reinterpret_cast<volatile uint32_t *>(&ctl->stage_last[stage]);
-                    last = lastw != 0;
+                    last = (lastw & 1u) != 0;
                     const uint32_t sa = smem_u32(smem + stage * kStageBytes);
                     const uint32_t sb = sa + kABytes;
+                    // K = 32 per MMA: four for a whole K block, two for a half
+                    const bool half_st = (lastw & 2u) != 0;
+                    const uint64_t layout = half_st ? kDescHalf : kDescFull;
+                    const int nmma = half_st ? kOccK / 32 : kTcK / 32;
 #pragma unroll
                     for (int k = 0; k < kTcK / 32; ++k)
-                        mma_f8(d, smem_desc(sa + 32 * k), smem_desc(sb + 32 * k),
-                               (!first || k > 0 || lastw == 2u) ? 1u : 0u);
+                        if (k < nmma)
+                            mma_f8(d, smem_desc(layout, sa + 32 * k), smem_desc(layout, sb + 32 * k),
+                                   (!first || k > 0 || lastw == 4u) ? 1u : 0u);
                     first = false;
-                    ++n_kblocks;
+                    n_kblocks += nmma / 2;
                     if (kPair) mma_commit_mc(smem_u32(&ctl->empty[stage]), (uint16_t)0x3);
                     else mma_commit(smem_u32(&ctl->empty[stage]));
                     if (++stage == kStages) { stage = 0; phase_bit ^= 1; }
@@ -930,26 +965,31 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn() {
     return fn;
 }
 
-// 2D uint8 tensor map over a rows x pitch byte matrix, box 128 x 128 bytes,
-// 128-byte swizzle; out-of-range rows read as zero.
-bool make_operand_tmap(void *out128, const void *base, int64_t pitch, int64_t rows) {
+// Two 2D uint8 tensor maps over a rows x pitch byte matrix, 128-row boxes;
+// out-of-range rows read as zero: a full stage (box 128 bytes wide, 128-byte
+// swizzle), then a half stage (box 64 bytes wide, 64-byte swizzle).
+static_assert(sizeof(CUtensorMap) == kTmapBytes, "tensor map size");
+bool make_operand_tmap(void *out, const void *base, int64_t pitch, int64_t rows) {
     PFN_cuTensorMapEncodeTiled_v12000 fn = get_encode_fn();
     if (!fn) return false;
-    CUtensorMap m;
-    std::memset(&m, 0, sizeof(m));
-    cuuint64_t dims[2] = {(cuuint64_t)pitch, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)pitch};
-    cuuint32_t box[2] = {(cuuint32_t)kTcK, (cuuint32_t)kTcM};
-    cuuint32_t estr[2] = {1, 1};
-    CUresult r = fn(&m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void *>(base), dims, strides,
-                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return false;
-    std::memcpy(out128, &m, sizeof(m));
+    for (int h = 0; h < 2; ++h) {
+        CUtensorMap m;
+        std::memset(&m, 0, sizeof(m));
+        cuuint64_t dims[2] = {(cuuint64_t)pitch, (cuuint64_t)rows};
+        cuuint64_t strides[1] = {(cuuint64_t)pitch};
+        cuuint32_t box[2] = {(cuuint32_t)(h ? kOccK : kTcK), (cuuint32_t)kTcM};
+        cuuint32_t estr[2] = {1, 1};
+        CUresult r = fn(&m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void *>(base), dims,
+                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        h ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return false;
+        std::memcpy(static_cast<uint8_t *>(out) + h * kTmapBytes, &m, sizeof(m));
+    }
     return true;
 }
 
-size_t tmap_bytes() { return sizeof(CUtensorMap); }
+size_t tmap_bytes() { return 2 * sizeof(CUtensorMap); }
 
 namespace {
 int g_pair_grid = 0;  // CTAs of the 2-CTA cluster launch (0: single-CTA tiles)

@@ -26,7 +26,7 @@ inline int32_t layout_code(int32_t layout) {
 // process-wide slab.  cudaMallocHost / cudaFreeHost cost tens of
 // microseconds and cudaFreeHost synchronises the device, which every
 // load / free would otherwise pay.  Blocks are 256-byte aligned.
-constexpr size_t kPinnedBlock = 512;
+constexpr size_t kPinnedBlock = 1024;
 void *pinned_block();  // nullptr if page-locked memory is unavailable
 void pinned_release(void *p);
 

@@ -22,7 +22,7 @@ struct BatchCounters {
     int32_t status_any;
     int32_t n_done;           // instances that reached their fixpoint in the last round
     int32_t loop_iters;       // rounds run by the device-side loop in this launch
-    unsigned long long mma_kblocks;  // K blocks contracted since load (tcgen05 path)
+    unsigned long long mma_kblocks;  // K steps of 64 contracted since load (tcgen05 path)
     unsigned long long mma_tiles;    // tiles contracted since load (tcgen05 path)
 };
 
@@ -69,7 +69,7 @@ bool tc_pairs();
 // Row blocks per L2 group of the tile order (environment MHS_TILE_GROUP_ROWS,
 // default 16); stored in Plan::group_rows.
 int32_t tile_group_rows();
-bool make_operand_tmap(void *out128, const void *base, int64_t pitch, int64_t rows);
+bool make_operand_tmap(void *out, const void *base, int64_t pitch, int64_t rows);
 size_t tmap_bytes();
 
 }  // namespace mhs

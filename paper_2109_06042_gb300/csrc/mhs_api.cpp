@@ -207,7 +207,7 @@ struct mhs_instance {
     BatchCounters *dctr = nullptr;
     int32_t *dkerr = nullptr;
     // one pinned slab block: counters [0, 64), error word [64, 128), plan
-    // header staging [128, 256), a single instance's tensor maps [256, 512)
+    // header staging [128, 256), a single instance's tensor maps [256, 768)
     uint8_t *pin = nullptr;
     BatchCounters *hctr = nullptr;
     int32_t *hkerr = nullptr;

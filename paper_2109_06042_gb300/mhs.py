@@ -307,7 +307,7 @@ class Instance:
         return {"dp_ms": a[0], "md_ms": a[1], "other_ms": a[2], "total_ms": a[3]}
 
     def work_stats(self):
-        """(K blocks of 128x256x128 MACs issued, tiles contracted) since load."""
+        """(K steps of 128x256x64 MACs issued, tiles contracted) since load."""
         kb = ctypes.c_int64()
         tl = ctypes.c_int64()
         _check(lib().mhs_work_stats(self._h, ctypes.byref(kb), ctypes.byref(tl)))
