@@ -28,6 +28,7 @@ data-path collective (weak scaling).
 from __future__ import annotations
 
 import argparse
+import datetime
 import json
 import os
 import statistics
@@ -127,23 +128,28 @@ def load_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    """nvidia-smi clocks and throttle reasons, sampled every 50 ms from before
+    the warm-up (so that the sampler is running when the timed region
+    starts); only samples whose own timestamp falls inside the timed window
+    are kept, or, for a window shorter than the interval, the ones nearest
+    to it."""
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_index):
         self.gpu = gpu_index
-        self.lines = []
+        self.lines = []  # (host receive time, line)
         self.proc = None
         self.thread = None
+        self.window = None
 
     def start(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                 "-lms", "200", "-i", str(self.gpu)],
+                 "-lms", "50", "-i", str(self.gpu)],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
@@ -153,7 +159,18 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.time(), line.strip()))
+
+    def mark(self, t0, t1):
+        """The timed window, in host time.time() seconds."""
+        self.window = (t0, t1)
+
+    @staticmethod
+    def _stamp(text, fallback):
+        try:
+            return datetime.datetime.strptime(text, "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return fallback
 
     def stop(self):
         if self.proc is not None:
@@ -164,24 +181,34 @@ class ClockSampler:
                 self.proc.kill()
         if self.thread is not None:
             self.thread.join(timeout=5)
-        sm, mx, reasons, pw = [], 0.0, set(), []
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        rows = []
+        for recv, ln in self.lines:
             parts = [x.strip() for x in ln.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                sm.append(float(parts[1]))
-                mx = max(mx, float(parts[2]))
-                pw.append(float(parts[3]))
+                rows.append((self._stamp(parts[0], recv), float(parts[2]), float(parts[3]),
+                             float(parts[4]), parts[6:10]))
             except ValueError:
                 continue
-            for nm, val in zip(names, parts[5:9]):
-                if val.lower().startswith("active"):
-                    reasons.add(nm)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
+        inside = rows
+        if self.window is not None and rows:
+            t0, t1 = self.window
+            inside = [r for r in rows if t0 <= r[0] <= t1]
+            if not inside:  # a window shorter than the interval: the nearest samples
+                before = [r for r in rows if r[0] < t0]
+                after = [r for r in rows if r[0] > t1]
+                inside = before[-1:] + after[:1]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = {nm for r in inside for nm, val in zip(names, r[4])
+                   if val.lower().startswith("active")}
+        sm = [r[1] for r in inside]
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max((r[2] for r in rows), default=0.0) or None,
                 "reasons": sorted(reasons), "samples": len(sm),
-                "power_w_max": max(pw) if pw else None}
+                "samples_in_window": sum(1 for r in rows if self.window
+                                         and self.window[0] <= r[0] <= self.window[1]),
+                "power_w_max": max((r[3] for r in inside), default=0.0) or None}
 
 
 def algorithmic_work(rows_list):
@@ -275,19 +302,20 @@ def run_ours(args, rank, world, dist):
     h.free()
     flops, pairs = algorithmic_work(traces)
 
-    for _ in range(args.warmup):
-        step()
-        step(timing=True)
-    torch.cuda.synchronize()
     gpu_index = rank
     vis = os.environ.get("CUDA_VISIBLE_DEVICES")
     if vis and vis.split(",")[0].strip().isdigit():
         gpu_index = int(vis.split(",")[torch.cuda.current_device()].strip())
     clocks = ClockSampler(gpu_index)
+    clocks.start()  # running before the timed region starts
+    for _ in range(args.warmup):
+        step()
+        step(timing=True)
+    torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks.start()
+    t_window0 = time.time()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
@@ -304,6 +332,7 @@ def run_ours(args, rank, world, dist):
         contract_ms += t["dp_ms"] + t["md_ms"]
         kblocks += t.get("kblocks", 0)
     torch.cuda.synchronize()
+    clocks.mark(t_window0, time.time())
     if dist is not None:
         dist.barrier()
     clk = clocks.stop()
