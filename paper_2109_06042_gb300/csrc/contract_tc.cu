@@ -66,40 +66,6 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const void *tmap, int3
         "l"(tmap), "r"(x), "r"(y), "r"(bar)
         : "memory");
 }
-// TMA load multicast to the CTAs of the cluster in `mask`: the box lands at
-// the same shared-memory offset in each, and completes bytes on the mbarrier
-// at the same offset in each.
-__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const void *tmap, int32_t x,
-                                               int32_t y, uint32_t bar, uint16_t mask) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        ".multicast::cluster [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(dst),
-        "l"(tmap), "r"(x), "r"(y), "r"(bar), "h"(mask)
-        : "memory");
-}
-__device__ __forceinline__ uint32_t cluster_rank() {
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-// Address of the same shared-memory location in CTA `rank` of the cluster.
-__device__ __forceinline__ uint32_t peer_addr(uint32_t addr, uint32_t rank) {
-    uint32_t r;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
-    return r;
-}
-__device__ __forceinline__ void mbar_arrive_peer(uint32_t cluster_addr) {
-    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr)
-                 : "memory");
-}
-__device__ __forceinline__ void st_peer_u64(uint32_t cluster_addr, int64_t v) {
-    asm volatile("st.shared::cluster.u64 [%0], %1;" ::"r"(cluster_addr), "l"(v) : "memory");
-}
-// All threads of both CTAs of the cluster.
-__device__ __forceinline__ void cluster_sync() {
-    asm volatile("barrier.cluster.arrive.release.aligned;\n"
-                 "barrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
 __device__ __forceinline__ void tc_fence_before() {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -134,14 +100,6 @@ __device__ __forceinline__ void mma_f8(uint32_t tmem_d, uint64_t adesc, uint64_t
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile(
         "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-        : "memory");
-}
-// Arrive (when this thread's MMAs so far have completed) on the mbarrier at
-// this offset in every CTA of `mask`.
-__device__ __forceinline__ void mma_commit_mc(uint32_t bar, uint16_t mask) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
-        " [%0], %1;" ::"r"(bar), "h"(mask)
         : "memory");
 }
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
@@ -217,45 +175,15 @@ __device__ void tc_tile_coords(int64_t t, int32_t R, int32_t G, int32_t *bi_out,
     }
 }
 
-// Pair tiles (2-CTA clusters): pair row P (row blocks 2P, 2P+1) against
-// column block bj >= P, in the same grouped order with G pair rows per group.
-__device__ void tc_pair_coords(int64_t t, int32_t R, int32_t G, int32_t *p_out, int32_t *bj_out) {
-    const int64_t cb = tc_col_blocks(R);
-    auto prefix = [cb](int64_t P) { return P * cb - P * (P - 1) / 2; };  // pairs in rows < P
-    const int32_t ng = (int32_t)((cb + G - 1) / G);
-    int32_t lo = 0, hi = ng;
-    while (hi - lo > 1) {
-        const int32_t mid = (lo + hi) >> 1;
-        if (prefix((int64_t)mid * G) <= t) lo = mid; else hi = mid;
-    }
-    const int32_t r0 = lo * G;
-    const int32_t gsz = (int32_t)min((int64_t)G, cb - r0);
-    int64_t q = t - prefix(r0);
-    // column r0 + c (c < gsz - 1) holds c + 1 pair rows; later columns hold gsz
-    for (int32_t c = 0; c < gsz - 1; ++c) {
-        if (q < c + 1) { *bj_out = r0 + c; *p_out = r0 + (int32_t)q; return; }
-        q -= c + 1;
-    }
-    *bj_out = r0 + gsz - 1 + (int32_t)(q / gsz);
-    *p_out = r0 + (int32_t)(q % gsz);
-}
-
 struct TileInfo {
     int b;
     int32_t bi, bj, R, nk;
-    int32_t bp;  // pair row P (2-CTA clusters), -1 for single tiles
 };
 
-// Sizes of the tile a packed tile-list entry names; for a pair entry, the
-// row block of CTA `rank` of the cluster.
+// Sizes of the tile a packed tile-list entry names.
 __device__ __forceinline__ void tile_info(const InstState *st, int phase, int64_t entry,
-                                          TileInfo *ti, bool pair = false, uint32_t rank = 0) {
+                                          TileInfo *ti) {
     unpack_tile(entry, &ti->b, &ti->bi, &ti->bj);
-    ti->bp = -1;
-    if (pair) {
-        ti->bp = ti->bi;
-        ti->bi = 2 * ti->bp + (int32_t)rank;
-    }
     const InstState &s = st[ti->b];
     ti->R = phase == 0 ? s.m : s.n;
     const int32_t K = phase == 0 ? s.n : s.m_dp;
@@ -278,24 +206,17 @@ __device__ __forceinline__ int4 epi_record(const InstState &s, int phase, int32_
 // leaves in `halves` which halves are shared (1: low, 2: high, 3: both).
 // Every role walks the same sequence.
 struct KIter {
-    const uint32_t *a, *a1, *b0, *b1;
+    const uint32_t *a, *b0, *b1;
     int32_t nkw, w, nk;
     uint32_t mask;
     uint32_t halves;
     bool all;
 };
-// For a pair tile the rows are both row blocks 2P and 2P+1 (the union).
 __device__ __forceinline__ void kit_init(KIter &k, const InstState &s, int phase,
                                          const TileInfo &ti) {
     const uint32_t *base = s.occ[phase];
     const int64_t W = s.occ_words[phase];
-    if (ti.bp >= 0) {
-        k.a = base + (int64_t)(2 * ti.bp) * W;
-        k.a1 = k.a + W;
-    } else {
-        k.a = base + (int64_t)ti.bi * W;
-        k.a1 = nullptr;
-    }
+    k.a = base + (int64_t)ti.bi * W;
     k.b0 = base + (int64_t)(2 * ti.bj) * W;
     k.b1 = k.b0 + W;
     k.nk = 2 * ti.nk;  // occupancy bits
@@ -311,9 +232,7 @@ __device__ __forceinline__ int32_t kit_next(KIter &k) {
             const int32_t left = k.nk - 32 * k.w;
             k.mask = left >= 32 ? 0xffffffffu : ((1u << left) - 1u);
         } else {
-            uint32_t am = __ldg(k.a + k.w);
-            if (k.a1) am |= __ldg(k.a1 + k.w);
-            k.mask = am & (__ldg(k.b0 + k.w) | __ldg(k.b1 + k.w));
+            k.mask = __ldg(k.a + k.w) & (__ldg(k.b0 + k.w) | __ldg(k.b1 + k.w));
         }
     }
     const int32_t bit = (__ffs(k.mask) - 1) & ~1;  // the K block's two bits
@@ -331,7 +250,6 @@ __device__ __forceinline__ int32_t kit_next(KIter &k) {
 // zero count only adds dominators of a vertex in no hyperedge, which is
 // deleted anyway (its maximum demand is 0).  Warp-aggregated appends keep
 // runs of 32 consecutive tiles together.
-template <bool kPair>
 __global__ void k_tile_list(InstState *st, Plan *plan, int phase) {
     const int lane = threadIdx.x & 31;
     const int64_t total = plan->total_tiles;
@@ -354,22 +272,15 @@ __global__ void k_tile_list(InstState *st, Plan *plan, int phase) {
             ti.R = phase == 0 ? s.m : s.n;
             const int32_t K = phase == 0 ? s.n : s.m_dp;
             ti.nk = ((K > 0 ? K : 1) + kTcK - 1) / kTcK;
-            ti.bp = -1;
-            if (kPair) {
-                tc_pair_coords(t - plan->tile_off[lo], ti.R, (G + 1) / 2, &ti.bp, &ti.bj);
-                ti.bi = ti.bp;  // the entry names the pair row
-            } else {
-                tc_tile_coords(t - plan->tile_off[lo], ti.R, G, &ti.bi, &ti.bj);
-            }
+            tc_tile_coords(t - plan->tile_off[lo], ti.R, G, &ti.bi, &ti.bj);
             bool has_k = true;
             if (s.no_skip) {
                 keep = true;  // the dense formulation: every tile, every round
             } else {
                 // only tiles that hold a candidate row (incremental rounds) ...
                 const uint8_t *drb = phase == 0 ? s.e_dirty_rb : s.v_dirty_rb;
-                const int32_t r0 = kPair ? 2 * ti.bp : ti.bi;
-                keep = !drb || (phase == 1 && s.md_full) || drb[r0] || (kPair && drb[r0 + 1]) ||
-                       drb[2 * ti.bj] || drb[2 * ti.bj + 1];
+                keep = !drb || (phase == 1 && s.md_full) || drb[ti.bi] || drb[2 * ti.bj] ||
+                       drb[2 * ti.bj + 1];
                 // ... and share a nonzero K block, unless zero counts matter
                 if (keep) {
                     KIter k;
@@ -415,12 +326,6 @@ struct __align__(8) SharedCtl {
     int32_t ccnt[kTcN];
 };
 
-// kPair: launched in clusters of 2 CTAs that contract the two row blocks of
-// a pair tile against the same column block.  Each CTA loads its own 128
-// rows i and one half of the 256 rows j, multicast to both CTAs, so the
-// rows j cross from L2 once for both; both MMA threads release a stage in
-// both CTAs.  The cluster's leader (rank 0) hands out the pair tiles.
-template <bool kPair>
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc_contract(InstState *st, const Plan *plan, BatchCounters *ctr, int phase, int32_t *kerr) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -430,23 +335,20 @@ __global__ void __launch_bounds__(kThreads, 1)
     SharedCtl *ctl = reinterpret_cast<SharedCtl *>(smem + kStages * kStageBytes);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     volatile int *abort = &ctl->abort;
-    const uint32_t rank = kPair ? cluster_rank() : 0;
-    const bool leader = rank == 0;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(smem_u32(&ctl->full[s]), 1);
-            mbar_init(smem_u32(&ctl->empty[s]), kPair ? 2 : 1);  // both MMA threads release
+            mbar_init(smem_u32(&ctl->empty[s]), 1);
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(smem_u32(&ctl->tmem_full[a]), 1);
             mbar_init(smem_u32(&ctl->tmem_empty[a]), kEpiThreads);
         }
-        // readers of a ring entry: the MMA thread and the epilogue of each
-        // CTA, and the other CTA's producer (pairs: the leader's ring counts all)
+        // readers of a ring entry: the MMA thread and the epilogue
         for (int r = 0; r < kRing; ++r) {
             mbar_init(smem_u32(&ctl->ring_full[r]), 1);
-            mbar_init(smem_u32(&ctl->ring_empty[r]), kPair ? 5 : 2);
+            mbar_init(smem_u32(&ctl->ring_empty[r]), 2);
         }
         mbar_init(smem_u32(&ctl->drain), 1);
         ctl->abort = 0;
@@ -463,22 +365,16 @@ __global__ void __launch_bounds__(kThreads, 1)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     tc_fence_before();
-    if (kPair) cluster_sync();  // the peer's barriers exist before anything reaches them
-    else __syncthreads();
+    __syncthreads();
     tc_fence_after();
     const uint32_t tmem = ctl->tmem_base;
-    // A reader is done with ring entry k: arrive on the slot's ring_empty of
-    // the CTA that publishes (pairs: the leader).
-    auto ring_release = [&](int k) {
-        const uint32_t bar = smem_u32(&ctl->ring_empty[k % kRing]);
-        if (kPair && !leader) mbar_arrive_peer(peer_addr(bar, 0));
-        else mbar_arrive(bar);
-    };
+    // A reader is done with ring entry k.
+    auto ring_release = [&](int k) { mbar_arrive(smem_u32(&ctl->ring_empty[k % kRing])); };
     // Wait for ring entry k (false on abort).
     auto ring_wait = [&](int k) -> bool {
         const uint32_t bar = smem_u32(&ctl->ring_full[k % kRing]);
         const uint32_t par = (k / kRing) & 1;
-        return kPair ? mbar_wait_cl(bar, par, abort, kWaitNs) : mbar_wait(bar, par, abort, kWaitNs);
+        return mbar_wait(bar, par, abort, kWaitNs);
     };
 
     if (warp == 0) {
@@ -492,26 +388,14 @@ __global__ void __launch_bounds__(kThreads, 1)
             // Publish ring entry k: wait until both readers are done with the
             // slot's previous entry, take the next list entry, and release it.
             // Returns the entry (-1: the list is exhausted), or -2 on abort.
-            // (Pairs: the leader publishes in both CTAs; the other CTA's
-            // producer reads the entries like the MMA thread does.)
             auto publish = [&](int k) -> int64_t {
                 const int slot = k % kRing;
-                if (kPair && !leader) {
-                    if (!ring_wait(k)) return -2;
-                    const int64_t e = *reinterpret_cast<volatile int64_t *>(&ctl->ring[slot]);
-                    ring_release(k);
-                    return e;
-                }
                 if (!mbar_wait(smem_u32(&ctl->ring_empty[slot]), ((k / kRing) & 1) ^ 1, abort,
                                kWaitNs))
                     return -2;
                 const int32_t t = atomicAdd(const_cast<int32_t *>(&plan->list_next), 1);
                 const int64_t e = t < plan->list_count ? plan->tile_list[t] : -1;
                 ctl->ring[slot] = e;
-                if (kPair) {
-                    st_peer_u64(peer_addr(smem_u32(&ctl->ring[slot]), 1), e);
-                    mbar_arrive_peer(peer_addr(smem_u32(&ctl->ring_full[slot]), 1));
-                }
                 mbar_arrive(smem_u32(&ctl->ring_full[slot]));
                 return e;
             };
@@ -526,7 +410,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             int64_t cur = publish(0);
             aborted = cur == -2;
             if (cur >= 0) {
-                tile_info(st, phase, cur, &ti, kPair, rank);
+                tile_info(st, phase, cur, &ti);
                 kit_init(kit, st[ti.b], phase, ti);
                 kb = kit_next(kit);
                 hv = kit.halves;
@@ -538,7 +422,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     break;
                 }
                 if (nxt >= 0) {
-                    tile_info(st, phase, nxt, &nx, kPair, rank);
+                    tile_info(st, phase, nxt, &nx);
                     kit_init(nkit, st[nx.b], phase, nx);
                     nkb = kit_next(nkit);
                     nhv = nkit.halves;
@@ -577,13 +461,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const uint32_t box = whole ? (uint32_t)kABytes : (uint32_t)kHalfBox;
                     mbar_expect_tx(full, whole ? kStageBytes : kHalfStageBytes);
                     tma_load_2d(sa, map, x, yi, full);
-                    if (kPair) {  // this CTA's half of the rows j, to both CTAs
-                        tma_load_2d_mc(sb + rank * box, map, x, yj + (int32_t)rank * kTcM, full,
-                                       (uint16_t)0x3);
-                    } else {
-                        tma_load_2d(sb, map, x, yj, full);
-                        tma_load_2d(sb + box, map, x, yj + kTcM, full);
-                    }
+                    tma_load_2d(sb, map, x, yj, full);
+                    tma_load_2d(sb + box, map, x, yj + kTcM, full);
                     ++issued;
                     if (++stage == kStages) { stage = 0; phase_bit ^= 1; }
                     kb = kb_next;
@@ -600,16 +479,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int64_t k = issued > kStages ? issued - kStages : 0; k < issued; ++k)
                     mbar_wait_ns(smem_u32(&ctl->full[k % kStages]), (uint32_t)((k / kStages) & 1),
                                  100000000ull);
-            }
-            if (kPair) {
-                // Every stage use has been released by both MMA threads (the
-                // other CTA's commits land here asynchronously): nothing may
-                // still arrive on this CTA once the cluster is released.
-                for (int sidx = 0; sidx < kStages && sidx < issued; ++sidx) {
-                    const int64_t uses = (issued - sidx + kStages - 1) / kStages;
-                    mbar_wait_ns(smem_u32(&ctl->empty[sidx]), (uint32_t)((uses - 1) & 1),
-                                 aborted ? 100000000ull : kWaitNs);
-                }
             }
         }
     } else if (warp == 1) {
@@ -674,8 +543,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                                    (!first || k > 0 || lastw == 4u) ? 1u : 0u);
                     first = false;
                     n_kblocks += nmma / 2;
-                    if (kPair) mma_commit_mc(smem_u32(&ctl->empty[stage]), (uint16_t)0x3);
-                    else mma_commit(smem_u32(&ctl->empty[stage]));
+                    mma_commit(smem_u32(&ctl->empty[stage]));
                     if (++stage == kStages) { stage = 0; phase_bit ^= 1; }
                 }
                 if (!aborted) mma_commit(smem_u32(&ctl->tmem_full[acc]));
@@ -711,7 +579,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             const int64_t entry = *reinterpret_cast<volatile int64_t *>(&ctl->ring[slot]);
             if (entry < 0) break;
-            tile_info(st, phase, entry, &ti, kPair, rank);
+            tile_info(st, phase, entry, &ti);
             InstState &s = st[ti.b];
             const int acc = it & 1;
             const uint32_t acc_phase = (it >> 1) & 1;
@@ -747,11 +615,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int nk = it + 1;
                 const uint32_t nbar = smem_u32(&ctl->ring_full[nk % kRing]);
                 const uint32_t npar = (nk / kRing) & 1;
-                if (kPair ? mbar_try_cl(nbar, npar) : mbar_try(nbar, npar)) {
+                if (mbar_try(nbar, npar)) {
                     const int64_t ne = *reinterpret_cast<volatile int64_t *>(&ctl->ring[nk % kRing]);
                     if (ne >= 0) {
                         TileInfo nt;
-                        tile_info(st, phase, ne, &nt, kPair, rank);
+                        tile_info(st, phase, ne, &nt);
                         const InstState &ns = st[nt.b];
                         pre_col = epi_record(ns, phase, nt.bj * kTcN + et, nt.R);
                         pre_row = epi_record(ns, phase, nt.bi * kTcM + 32 * q + lane, nt.R);
@@ -937,7 +805,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_fence_before();
     __syncthreads();
     if (threadIdx.x == 0 && *abort) atomicOr(kerr, kErrTimeout);
-    if (kPair) cluster_sync();  // no CTA leaves while the other may still reach it
     if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
@@ -991,68 +858,16 @@ bool make_operand_tmap(void *out, const void *base, int64_t pitch, int64_t rows)
 
 size_t tmap_bytes() { return 2 * sizeof(CUtensorMap); }
 
-namespace {
-int g_pair_grid = 0;  // CTAs of the 2-CTA cluster launch (0: single-CTA tiles)
-}
-
 cudaError_t prepare_tc_contract() {
-    static cudaError_t once = [] {
-        cudaError_t e = cudaFuncSetAttribute(k_tc_contract<false>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)kSmemBytes);
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(k_tc_contract<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kSmemBytes);
-        if (e != cudaSuccess) return e;
-        // Pair tiles halve the L2 reads of the rows j but contract the union
-        // of both row blocks' K blocks; on the measured workloads that costs
-        // more than it saves, so they are opt-in.
-        const char *env = std::getenv("MHS_TC_PAIRS");
-        if (!env || std::atoi(env) == 0) return cudaSuccess;
-        // as many clusters as can be resident at once (persistent CTAs)
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(2, 1, 1);
-        cfg.blockDim = dim3(kThreads, 1, 1);
-        cfg.dynamicSmemBytes = kSmemBytes;
-        cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeClusterDimension;
-        at[0].val.clusterDim.x = 2;
-        at[0].val.clusterDim.y = 1;
-        at[0].val.clusterDim.z = 1;
-        cfg.attrs = at;
-        cfg.numAttrs = 1;
-        int clusters = 0;
-        if (cudaOccupancyMaxActiveClusters(&clusters, k_tc_contract<true>, &cfg) == cudaSuccess &&
-            clusters >= 2)
-            g_pair_grid = 2 * clusters;
-        cudaGetLastError();  // an unsupported query leaves single-CTA tiles
-        return cudaSuccess;
-    }();
+    static cudaError_t once = cudaFuncSetAttribute(
+        k_tc_contract, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
     return once;
 }
 
-bool tc_pairs() { return g_pair_grid > 0; }
-
 cudaError_t launch_tc_contract(InstState *st, Plan *plan, BatchCounters *ctr, int phase, int sms,
                                int32_t *kerr, cudaStream_t s) {
-    if (!tc_pairs()) {
-        k_tc_contract<false><<<sms, kThreads, kSmemBytes, s>>>(st, plan, ctr, phase, kerr);
-        return cudaGetLastError();
-    }
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(g_pair_grid, 1, 1);
-    cfg.blockDim = dim3(kThreads, 1, 1);
-    cfg.dynamicSmemBytes = kSmemBytes;
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = 2;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    const Plan *cplan = plan;
-    return cudaLaunchKernelEx(&cfg, k_tc_contract<true>, st, cplan, ctr, phase, kerr);
+    k_tc_contract<<<sms, kThreads, kSmemBytes, s>>>(st, plan, ctr, phase, kerr);
+    return cudaGetLastError();
 }
 
 int32_t tile_group_rows() {
@@ -1065,8 +880,7 @@ int32_t tile_group_rows() {
 }
 
 cudaError_t launch_tc_tile_list(InstState *st, Plan *plan, int phase, int sms, cudaStream_t s) {
-    if (tc_pairs()) k_tile_list<true><<<sms * 4, 256, 0, s>>>(st, plan, phase);
-    else k_tile_list<false><<<sms * 4, 256, 0, s>>>(st, plan, phase);
+    k_tile_list<<<sms * 4, 256, 0, s>>>(st, plan, phase);
     return cudaGetLastError();
 }
 

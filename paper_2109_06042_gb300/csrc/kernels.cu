@@ -322,7 +322,7 @@ __global__ void k_edge_rows(InstState *st, int count) {
 // ------------------------------------------------------------- planning --
 
 // phase 0: rows = current hyperedges (DP); phase 1: rows = current vertices (MD).
-// tc: 0 popcount tiles, 1 tcgen05 tiles, 2 tcgen05 pair tiles.
+// tc: 0 popcount tiles, 1 tcgen05 tiles.
 __global__ void k_plan(InstState *st, Plan *plan, int phase, int tc, BatchCounters *ctr) {
     __shared__ int32_t sh[33];
     __shared__ int64_t sh64[33];
@@ -346,7 +346,7 @@ __global__ void k_plan(InstState *st, Plan *plan, int phase, int tc, BatchCounte
                 // A^T for the ones DP kept)
                 rows = s.m;
                 const int32_t R = phase == 0 ? s.m : s.n;
-                tiles = tc == 2 ? tc_pair_tiles(R) : tc == 1 ? tc_tiles(R) : pop_tiles(R);
+                tiles = tc ? tc_tiles(R) : pop_tiles(R);
                 act_any = 1;
             }
         }
@@ -1005,7 +1005,7 @@ cudaError_t launch_round_phase(InstState *st, Plan *plan, BatchCounters *ctr, in
                                cudaEvent_t ev_contract_end, int32_t *done_list,
                                int compact_blocks) {
     const bool tc = contraction == kFp8;
-    k_plan<<<1, 1024, 0, s>>>(st, plan, phase, tc ? (tc_pairs() ? 2 : 1) : 0, ctr);
+    k_plan<<<1, 1024, 0, s>>>(st, plan, phase, tc ? 1 : 0, ctr);
     const int grid = grid_for(sms, 8);
     if (phase == 0) launch_scatter<0>(st, plan, true, tc, grid, s);
     else launch_scatter<1>(st, plan, true, tc, grid, s);

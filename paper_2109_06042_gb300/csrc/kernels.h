@@ -63,9 +63,6 @@ cudaError_t launch_tc_contract(InstState *st, Plan *plan, BatchCounters *ctr, in
 // an instance with a hyperedge f > |e|, all tiles), into plan->tile_list.
 cudaError_t launch_tc_tile_list(InstState *st, Plan *plan, int phase, int sms, cudaStream_t s);
 cudaError_t prepare_tc_contract();  // once per process, before any capture
-// After prepare_tc_contract: true if the contraction runs pair tiles on 2-CTA
-// clusters (opt-in: environment MHS_TC_PAIRS=1).
-bool tc_pairs();
 // Row blocks per L2 group of the tile order (environment MHS_TILE_GROUP_ROWS,
 // default 16); stored in Plan::group_rows.
 int32_t tile_group_rows();

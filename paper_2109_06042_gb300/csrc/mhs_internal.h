@@ -172,14 +172,6 @@ __host__ __device__ inline int32_t tc_col_blocks(int32_t R) { return (R + kTcN -
 __host__ __device__ inline int32_t tc_row_blocks(int32_t R) { return (R + kTcM - 1) / kTcM; }
 // first column block holding a j > i for some i in row block bi
 __host__ __device__ inline int32_t tc_first_cb(int32_t bi) { return (bi * kTcM + 1) / kTcN; }
-// Pair tiles (tcgen05 path with 2-CTA clusters): row blocks 2P and 2P+1
-// against column block bj, needed iff bj >= P; an upper triangle of the
-// column-block grid.
-__host__ __device__ inline int64_t tc_pair_tiles(int32_t R) {
-    if (R <= 1) return 0;
-    const int64_t cb = tc_col_blocks(R);
-    return cb * (cb + 1) / 2;
-}
 __host__ __device__ inline int64_t tc_tiles(int32_t R) {
     if (R <= 1) return 0;
     // sum over row blocks bi of (cb - floor(bi/2))

@@ -389,35 +389,6 @@ def test_skip_and_dense_agree_and_skip_does_less(mhs):
     assert 0 < kb_skip < kb_dense and 0 < t_skip <= t_dense
 
 
-def test_cluster_pair_tiles_in_subprocess(mhs):
-    """The opt-in 2-CTA cluster form of the tcgen05 contraction (pair tiles,
-    multicast rows j) gives the same results; the switch is read once per
-    process, so the check runs in a child process."""
-    import os
-    import subprocess
-    import sys
-    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    code = (
-        "import sys; sys.path.insert(0, %r)\n"
-        "from oracle import oracle as O\n"
-        "from paper_2109_06042_gb300 import instances as I, mhs\n"
-        "cases = [I.config_uniform(s) for s in range(5)] + "
-        "[I.uniform_random(700, 1500, 1, 8, 4, 70, 81_000 + s) for s in range(2)] + "
-        "[I.config_powerlaw(0, n=4000, m=8000), I.config_interval(1, n=4000, m=8000)]\n"
-        "for c, inst in enumerate(cases):\n"
-        "    for rule, fe in (('dp', False), ('se', True)):\n"
-        "        g = mhs.kernelize(inst, contraction='fp8', rule=rule, full_edges=fe)\n"
-        "        r = O.reduce_variant(inst, rule, fe)\n"
-        "        for k in ('vertices', 'edges', 'demands'):\n"
-        "            assert g[k].tolist() == r[k].tolist(), (c, rule, k)\n"
-        "        assert g['rounds'] == r['rounds'] and g['k'] == r['k'], (c, rule)\n"
-        "print('pairs ok')\n" % root)
-    env = dict(os.environ, MHS_TC_PAIRS="1")
-    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
-                         timeout=600)
-    assert out.returncode == 0 and "pairs ok" in out.stdout, out.stderr[-2000:]
-
-
 def test_reused_operand_regions(mhs):
     """Dense operand regions return to a zero-state cache when an instance is
     freed and are reused by later loads without a memset: results must not
