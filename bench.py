@@ -213,15 +213,39 @@ class ClockSampler:
 
 def algorithmic_work(rows_list):
     """2 x MACs of the symmetric halves of I^E and I^V over alive, unpadded
-    sizes (DP: m_r^2 n_r / 2 MACs, MD: n_r^2 m'_r / 2) and the unordered pair
-    tests, summed over the rounds of every instance."""
+    sizes (DP: m_r^2 n_r / 2 MACs, MD: n_r^2 m'_r / 2), the unordered pair
+    tests, and the bit-packed operand bytes one pass of each product reads
+    ((m_r n_r + n_r m'_r) / 8), summed over the rounds of every instance."""
     flops = 0.0
     pairs = 0.0
+    bits_bytes = 0.0
     for rows in rows_list:
         for m, n, mdp in rows.tolist():
             flops += float(m) * m * n + float(n) * n * mdp
             pairs += m * (m - 1) / 2 + n * (n - 1) / 2
-    return flops, pairs
+            bits_bytes += (float(m) * n + float(n) * mdp) / 8.0
+    return flops, pairs, bits_bytes
+
+
+def sparse_intrinsic_work(inst, alive_per_round):
+    """Nonzero products of the two products per round, summed over rounds:
+    sum over alive vertices of deg^2 (I^E = A A^T, DP) plus sum over the
+    hyperedges DP kept of their alive size^2 (I^V = A^T A, MD).  The
+    dense formulation's MACs over this is its overhead factor.
+    alive_per_round: (vertex mask, edge mask) entering each round, then the
+    final state, over input ids."""
+    ptr = inst.edge_ptr.astype(np.int64)
+    vtx = inst.edge_vtx
+    row = np.repeat(np.arange(inst.m), np.diff(ptr))
+    total = 0.0
+    for (av, ae), (_, ae_next) in zip(alive_per_round[:-1], alive_per_round[1:]):
+        live = av[vtx] & ae[row]
+        deg = np.bincount(vtx[live], minlength=inst.n).astype(np.float64)
+        total += float((deg * deg).sum())
+        kept = av[vtx] & ae_next[row]  # hyperedges DP kept, over the vertices MD sees
+        size = np.bincount(row[kept], minlength=inst.m).astype(np.float64)
+        total += float((size * size).sum())
+    return total
 
 
 class DeviceInputs:
@@ -300,7 +324,24 @@ def run_ours(args, rank, world, dist):
     traces = [h.trace(b)[0] for b in range(D.count)]
     rounds = int(st["rounds"])
     h.free()
-    flops, pairs = algorithmic_work(traces)
+    flops, pairs, bits_bytes = algorithmic_work(traces)
+    # untimed: round by round through the public API, the alive sets entering
+    # each round (single instance) -> the sparse intrinsic work
+    intrinsic = None
+    if not batch and not args.full_edges:
+        inst0 = insts[0]
+        states = [(np.ones(inst0.n, bool), np.ones(inst0.m, bool))]
+        with mhs.Instance.load(inst0, contraction=args.contraction, use_graphs=False,
+                               stream=stream) as hr:
+            for _ in range(rounds):
+                hr.reduce_round()
+                r = hr.result()
+                av = np.zeros(inst0.n, bool)
+                ae = np.zeros(inst0.m, bool)
+                av[r["vertices"]] = True
+                ae[r["edges"]] = True
+                states.append((av, ae))
+        intrinsic = sparse_intrinsic_work(inst0, states)
 
     gpu_index = rank
     vis = os.environ.get("CUDA_VISIBLE_DEVICES")
@@ -401,29 +442,46 @@ def run_ours(args, rank, world, dist):
 
     peaks, kind = load_peaks()
     per_launch = contract_ms / args.steps / (2 * rounds)
+    contract_s_per_step = contract_ms / args.steps / 1e3
+    dense_equiv = flops / contract_s_per_step / 1e12
+    prof = kernel_profile(args)
     if args.contraction == "fp8":
         # FP8 dense = 2 x BF16 (4.5 / 2.25 PF nominal); the burst figure, since the
         # contraction is timed in short steps at full clock
         peak = 2.0 * peaks["bf16_tflops"]
-        achieved = flops / (contract_ms / args.steps / 1e3) / 1e12
-        # tensor work actually issued (block-sparse skipping leaves out zero blocks)
+        # tensor work actually issued: K steps of 128 x 256 x 64 MACs, counted by
+        # the kernel (block-sparse skipping leaves out K blocks and tiles whose
+        # products are all zero, so this is below the dense formulation's count)
         issued = kblocks * 2.0 * 128 * 256 * 64 / (contract_ms / 1e3) / 1e12
-        roof = {"bound": "tensor", "achieved": round(achieved, 2), "peak": round(peak, 1),
-                "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
-                "traffic": measured_traffic(args, desc),
+        roof = {"bound": "tensor", "achieved": round(issued, 2), "peak": round(peak, 1),
+                "unit": "TFLOP/s", "frac": round(issued / peak, 4),
+                "traffic": prof.get("traffic_bytes_per_launch"),
                 "kernel": "k_tc_contract", "peak_source": f"{kind}: 2 x bf16_tflops (burst)",
                 "launches_per_step": 2 * rounds, "avg_launch_ms": round(per_launch, 4),
-                "achieved_basis": "dense-formulation MACs x 2 (m^2 n + n^2 m' per round)",
-                "issued_tflops": round(issued, 2), "issued_frac": round(issued / peak, 4),
+                "achieved_basis": "tensor MACs issued x 2 (kernel counter, K steps of 64)",
+                "issued_flops_per_step": kblocks * 2.0 * 128 * 256 * 64 / args.steps,
+                "dense_equiv_tflops": round(dense_equiv, 2),
+                "dense_equiv_frac": round(dense_equiv / peak, 4),
+                "dense_formulation_flops_per_step": flops,
+                "sparse_intrinsic_macs_per_step": intrinsic,
+                "ncu_tensor_active_pct": prof.get("tensor_active_pct"),
+                "ncu_profile": prof.get("file"),
                 "sparsity": args.sparsity}
     else:
         sm_mhz = peaks.get("sm_max_mhz", 2070.0)
         peak = 152 * 16 * 32 * 2 * sm_mhz * 1e6 / 1e12  # 16 POPC/clk/SM x 32 bit-MACs
-        achieved = flops / (contract_ms / args.steps / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": round(achieved, 2), "peak": round(peak, 1),
-                "unit": "TOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+        # bit-packed operand bytes one pass reads, against the measured copy rate
+        hbm = bits_bytes / contract_s_per_step / 1e9
+        roof = {"bound": "alu", "achieved": round(dense_equiv, 2), "peak": round(peak, 1),
+                "unit": "TOP/s", "frac": round(dense_equiv / peak, 4), "traffic": None,
                 "kernel": "k_pop_contract", "peak_source": "derived: 16 POPC/clk/SM nominal",
-                "launches_per_step": 2 * rounds, "avg_launch_ms": round(per_launch, 4)}
+                "launches_per_step": 2 * rounds, "avg_launch_ms": round(per_launch, 4),
+                "achieved_basis": "bit-MACs of the dense formulation x 2 (every 64 x 64 "
+                                  "tile of the upper triangle is contracted)",
+                "sparse_intrinsic_macs_per_step": intrinsic,
+                "hbm": {"achieved": round(hbm, 2), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                        "frac": round(hbm / peaks["hbm_gbs"], 4),
+                        "basis": "bit-packed operand bytes per pass, (m n + n m') / 8"}}
 
     cpu = seq = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -559,41 +617,47 @@ def run_stream(args, rank, world):
     }
 
 
-TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "k_tc_contract_traffic_powerlaw_n20000_m40000.md")
-TRAFFIC_SOURCES = ("contract_tc.cu", "kernels.cu", "mhs_internal.h")
+PROFILE = os.path.join(ROOT, "profiles", "k_tc_contract_powerlaw_n20000_m40000.md")
+PROFILE_SOURCES = ("contract_tc.cu", "kernels.cu", "mhs_internal.h")
 
 
 def kernel_sources_sha256():
-    """Digest of the sources that decide the contraction's DRAM traffic."""
+    """Digest of the sources that decide the contraction's counters."""
     import hashlib
     h = hashlib.sha256()
-    for f in TRAFFIC_SOURCES:
+    for f in PROFILE_SOURCES:
         with open(os.path.join(ROOT, "paper_2109_06042_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
 
 
-def measured_traffic(args, desc):
-    """DRAM bytes per k_tc_contract launch from the committed ncu capture of
-    this workload (dram__bytes_read.sum + dram__bytes_write.sum over one
-    kernelization's launches), or None when the workload or options differ
-    or the kernel sources changed since the capture."""
+def kernel_profile(args):
+    """Counters of k_tc_contract from the committed ncu summary of this
+    workload: DRAM bytes per launch (dram__bytes_read.sum +
+    dram__bytes_write.sum, averaged over one kernelization's launches) and
+    the tensor pipe's active share; empty when the workload or options
+    differ or the kernel sources changed since the capture."""
     default = (args.workload == "powerlaw" and args.seed == 0 and args.sparsity == "skip" and
                args.rule == "dp" and not args.full_edges and args.contraction == "fp8")
-    if not default or not os.path.exists(TRAFFIC_PROFILE):
-        return None
+    if not default or not os.path.exists(PROFILE):
+        return {}
     fields = {}
-    with open(TRAFFIC_PROFILE) as fh:
+    with open(PROFILE) as fh:
         for line in fh:
-            if ":" in line and line.startswith(("traffic_bytes_per_launch", "source_sha256")):
+            if ":" in line and line.startswith(("traffic_bytes_per_launch", "source_sha256",
+                                                "tensor_active_pct")):
                 k, v = line.split(":", 1)
                 fields[k.strip()] = v.strip()
     if fields.get("source_sha256") != kernel_sources_sha256():
-        return None
-    try:
-        return int(float(fields["traffic_bytes_per_launch"]))
-    except (KeyError, ValueError):
-        return None
+        return {}
+    out = {"file": os.path.relpath(PROFILE, ROOT)}
+    for k, conv in (("traffic_bytes_per_launch", lambda v: int(float(v))),
+                    ("tensor_active_pct", float)):
+        try:
+            out[k] = conv(fields[k])
+        except (KeyError, ValueError):
+            pass
+    return out
 
 
 def variant_name(args):

@@ -304,18 +304,23 @@ mhs_status mhs_last_timing(const mhs_instance *inst, float *ms4);
  * alive_e (uint8[m]) DEVICE buffers receive 1 for surviving vertices /
  * hyperedges (input ids); *rounds_out (host, may be NULL) the round count.
  * Same rules and result as mhs_kernelize (bit-packed popcount contraction).
+ * Every array must be device (or managed) memory of the current device; any
+ * other pointer gives MHS_EINVAL before a kernel runs.  A malformed instance
+ * (bad edge_ptr, vertex id out of range) gives MHS_EINVAL; a kernel error
+ * status, or a round cap reached before the fixpoint, gives MHS_EDEVICE.
  *
  * All working memory is one file-scope device array of 6 MiB that every GPU
  * loading the library keeps until the process exits.  Limits: n <= 4096,
  * m <= 4096, nnz <= 65536; larger instances give MHS_EINVAL.  Every call
  * reuses the same array (the call clears what must start at zero), so calls
- * whose GPU work overlaps race and must be serialised by the caller.  The
- * first call on each device looks up the array's address
- * (cudaGetSymbolAddress) and should come before any stream capture.  The
- * call runs on cuda_stream (NULL: the default stream) and returns after the
- * work is done.  Errors are reported through the return value and, if
- * err_buf is non-NULL, a message in err_buf[err_cap] (mhs_last_error is not
- * used, so that no host string is allocated either).
+ * whose GPU work overlaps race and must be serialised by the caller.  Each
+ * call looks up the array's address (cudaGetSymbolAddress) on the current
+ * device; the first call on a device may load the library's device code and
+ * should come before any stream capture.  The call runs on cuda_stream
+ * (NULL: the default stream) and returns after the work is done.  Errors
+ * are reported through the return value and, if err_buf is non-NULL, a
+ * message in err_buf[err_cap] (mhs_last_error is not used, so that no host
+ * string is allocated either).
  */
 mhs_status mhs_kernelize_noalloc(int32_t n, int32_t m, const int32_t *edge_ptr,
                                  const int32_t *edge_vtx, const int32_t *demand, int32_t nnz,

@@ -20,14 +20,20 @@
 // GPU work overlaps (different streams or threads at the same time) race on
 // the array and give wrong results: serialise them.
 //
-// Set-up: the first call on each device looks up the array's device address
-// with cudaGetSymbolAddress (with that device current) and caches it; make
-// that first call before any stream capture.
+// Set-up: every call looks up the array's device address with
+// cudaGetSymbolAddress, with the caller's device current.  No address is
+// cached, so a context torn down and created again (cudaDeviceReset) cannot
+// leave a stale one behind.  The first call on a device may load the
+// library's device code into the context; make that first call before any
+// stream capture.
+//
+// Pointers: every device array the caller passes is checked with
+// cudaPointerGetAttributes (device or managed memory of the current device)
+// before any kernel touches it; anything else is MHS_EINVAL.
 #include <cuda_runtime.h>
 
 #include <cstdio>
 #include <cstring>
-#include <mutex>
 
 #include "kernels.h"
 #include "mhs.h"
@@ -42,9 +48,6 @@ constexpr int64_t kNoAllocMaxNnz = 65536;
 constexpr size_t kScratchBytes = (size_t)6 << 20;  // 6 MiB
 
 static __device__ __align__(256) uint8_t kScratch[kScratchBytes];
-
-std::mutex g_mu;
-void *g_scratch_dev[64] = {};  // device address of kScratch, per device
 
 inline int64_t up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 inline int64_t words(int64_t K) { return up(((K + 31) / 32) > 0 ? (K + 31) / 32 : 1, 4); }
@@ -64,6 +67,18 @@ mhs_status err(char *buf, size_t cap, mhs_status st, const char *msg) {
         buf[cap - 1] = '\0';
     }
     return st;
+}
+
+// True if p is device (or managed) memory that device `dev` can use; a
+// pointer of no kind CUDA knows (plain host memory) is rejected.
+bool on_device(const void *p, int dev) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();  // the failed query's error is not sticky: clear it
+        return false;
+    }
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 }  // namespace
@@ -86,23 +101,21 @@ extern "C" mhs_status mhs_kernelize_noalloc(int32_t n, int32_t m, const int32_t 
         return err(err_buf, err_cap, MHS_EINVAL, "NULL array");
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0)
         return err(err_buf, err_cap, MHS_ECUDA, "no current CUDA device");
+    if (!on_device(edge_ptr, dev) || (m > 0 && !on_device(demand, dev)) ||
+        (nnz > 0 && !on_device(edge_vtx, dev)) || (n > 0 && !on_device(alive_v, dev)) ||
+        (m > 0 && !on_device(alive_e, dev)))
+        return err(err_buf, err_cap, MHS_EINVAL,
+                   "an array is not device memory of the current device");
     void *base_v = nullptr;
-    {
-        std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_scratch_dev[dev]) {
-            void *p = nullptr;
-            cudaError_t e = cudaGetSymbolAddress(&p, kScratch);
-            if (e != cudaSuccess || !p)
-                return err(err_buf, err_cap, MHS_ECUDA, "cudaGetSymbolAddress(scratch) failed");
-            g_scratch_dev[dev] = p;
-        }
-        base_v = g_scratch_dev[dev];
-    }
+    if (cudaGetSymbolAddress(&base_v, kScratch) != cudaSuccess || !base_v)
+        return err(err_buf, err_cap, MHS_ECUDA, "cudaGetSymbolAddress(scratch) failed");
     uint8_t *base = static_cast<uint8_t *>(base_v);
     int sms = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        sms <= 0)
+        return err(err_buf, err_cap, MHS_ECUDA, "cannot read the SM count");
 
     // layout inside the scratch (same roles as the main path's arena)
     Take take;
@@ -181,6 +194,7 @@ extern "C" mhs_status mhs_kernelize_noalloc(int32_t n, int32_t m, const int32_t 
     if (e == cudaSuccess) e = launch_build(dst, 1, 0, nnz, m, n, s);
     if (e != cudaSuccess) return err(err_buf, err_cap, MHS_ECUDA, cudaGetErrorString(e));
     BatchCounters ctr;
+    std::memset(&ctr, 0, sizeof(ctr));
     int32_t kerr = 0;
     // every changing round deletes an item, so n + m + 1 rounds always suffice
     for (int32_t r = 0; r <= n + m + 1; ++r) {
@@ -198,6 +212,8 @@ extern "C" mhs_status mhs_kernelize_noalloc(int32_t n, int32_t m, const int32_t 
             return err(err_buf, err_cap, MHS_EDEVICE, "kernel reported an error status");
         if (ctr.active == 0) break;
     }
+    if (ctr.active != 0)  // unreachable with correct kernels: never report a partial result
+        return err(err_buf, err_cap, MHS_EDEVICE, "round cap reached before fixpoint");
     if (n > 0 || m > 0) {
         e = launch_alive_masks(dst, n > 0 ? alive_v : nullptr, m > 0 ? alive_e : nullptr, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);

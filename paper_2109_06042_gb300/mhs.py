@@ -510,6 +510,20 @@ def kernelize_noalloc(n, m, edge_ptr, edge_vtx, demand, nnz, alive_v, alive_e, s
     """mhs_kernelize_noalloc on CUDA tensors: no memory is allocated by the
     call; alive_v / alive_e (uint8 CUDA tensors) receive the surviving masks.
     Returns the round count."""
+    import torch
+    n, m, nnz = int(n), int(m), int(nnz)
+    dev = torch.cuda.current_device()
+    for name, t, dt, need in (("edge_ptr", edge_ptr, torch.int32, m + 1),
+                              ("edge_vtx", edge_vtx, torch.int32, nnz),
+                              ("demand", demand, torch.int32, m),
+                              ("alive_v", alive_v, torch.uint8, n),
+                              ("alive_e", alive_e, torch.uint8, m)):
+        if not (t.is_cuda and t.device.index == dev):
+            raise MhsError(MHS_EINVAL, f"{name} must be a CUDA tensor on device {dev}")
+        if t.dtype != dt or not t.is_contiguous():
+            raise MhsError(MHS_EINVAL, f"{name} must be a contiguous {dt} tensor")
+        if t.numel() < need:
+            raise MhsError(MHS_EINVAL, f"{name} holds {t.numel()} elements, needs {need}")
     rounds = ctypes.c_int32(0)
     buf = ctypes.create_string_buffer(256)
     st = lib().mhs_kernelize_noalloc(int(n), int(m), ctypes.c_void_p(edge_ptr.data_ptr()),

@@ -71,3 +71,29 @@ def test_bad_options_rejected_on_host(libpath):
                             ptr.ctypes.data_as(mhs._P32), 0, ctypes.byref(o), None,
                             ctypes.byref(h))
     assert st == mhs.MHS_EINVAL
+
+
+def test_noalloc_argument_errors_on_host(libpath):
+    """mhs_kernelize_noalloc maps bad sizes and missing arrays to MHS_EINVAL
+    with a message in the caller's buffer, before any CUDA call (so this runs
+    without a GPU)."""
+    import ctypes
+
+    from paper_2109_06042_gb300 import mhs
+    L = mhs.lib()
+    buf = ctypes.create_string_buffer(128)
+    dummy = ctypes.c_void_p(16)  # never dereferenced: the size checks come first
+    cases = [((-1, 4, 8), b">= 0"), ((4, -2, 8), b">= 0"), ((4, 4, -1), b">= 0"),
+             ((4097, 4, 8), b"too large"), ((4, 4097, 8), b"too large"),
+             ((4, 4, 65537), b"too large")]
+    for (n, m, nnz), msg in cases:
+        st = L.mhs_kernelize_noalloc(n, m, dummy, dummy, dummy, nnz, dummy, dummy, None, None,
+                                     buf, 128)
+        assert st == mhs.MHS_EINVAL and msg in buf.value, (n, m, nnz, buf.value)
+    st = L.mhs_kernelize_noalloc(4, 4, None, dummy, dummy, 8, dummy, dummy, None, None, buf, 128)
+    assert st == mhs.MHS_EINVAL and b"NULL" in buf.value
+    # a one-byte buffer still gets a terminated (empty) message
+    small = ctypes.create_string_buffer(1)
+    assert L.mhs_kernelize_noalloc(-1, 0, dummy, dummy, dummy, 0, dummy, dummy, None, None,
+                                   small, 1) == mhs.MHS_EINVAL
+    assert small.value == b""

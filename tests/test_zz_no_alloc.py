@@ -81,3 +81,79 @@ def test_noalloc_rejects_oversize(env):
         mhs.kernelize_noalloc(inst.n, inst.m, ptr, vtx, dem, inst.nnz, av, ae)
     assert ei.value.status == mhs.MHS_EINVAL
     assert "too large" in str(ei.value)
+
+
+def test_noalloc_malformed_then_valid(env):
+    """A vertex id out of range is caught by the device-side validation
+    (MHS_EINVAL); the next valid call still matches the allocating path."""
+    torch, mhs = env
+    inst = I.config_uniform(2)
+    ptr, vtx, dem = _dev(torch, inst)
+    bad = vtx.clone()
+    bad[5] = inst.n + 3
+    av = torch.zeros(inst.n, dtype=torch.uint8, device="cuda:0")
+    ae = torch.zeros(inst.m, dtype=torch.uint8, device="cuda:0")
+    with pytest.raises(mhs.MhsError) as ei:
+        mhs.kernelize_noalloc(inst.n, inst.m, ptr, bad, dem, inst.nnz, av, ae)
+    assert ei.value.status == mhs.MHS_EINVAL
+    ref = _allocating(torch, mhs, inst, ptr, vtx, dem)
+    got = _noalloc(torch, mhs, inst, ptr, vtx, dem)
+    assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
+    assert got[2] == ref[2]
+
+
+def test_noalloc_on_a_side_stream(env):
+    """The call runs on the stream it is given (a non-default torch stream)."""
+    torch, mhs = env
+    inst = I.config_batch_one(4011)
+    ptr, vtx, dem = _dev(torch, inst)
+    ref = _allocating(torch, mhs, inst, ptr, vtx, dem)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        av = torch.full((inst.n,), 7, dtype=torch.uint8, device="cuda:0")
+        ae = torch.full((inst.m,), 7, dtype=torch.uint8, device="cuda:0")
+    for _ in range(2):
+        rounds = mhs.kernelize_noalloc(inst.n, inst.m, ptr, vtx, dem, inst.nnz, av, ae,
+                                       stream=side)
+        side.synchronize()
+        assert np.array_equal(av.cpu().numpy(), ref[0])
+        assert np.array_equal(ae.cpu().numpy(), ref[1])
+        assert rounds == ref[2]
+
+
+def test_noalloc_empty_instances(env):
+    """No hyperedges (every vertex isolated, so deleted) and no vertices at
+    all: masks and round counts equal the allocating path's."""
+    torch, mhs = env
+    for inst in (I.from_edges(0, [], []), I.from_edges(6, [], [])):
+        ptr, vtx, dem = _dev(torch, inst)
+        ref = _allocating(torch, mhs, inst, ptr, vtx, dem)
+        for _ in range(2):
+            got = _noalloc(torch, mhs, inst, ptr, vtx, dem)
+            assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
+            assert got[2] == ref[2]
+
+
+def test_noalloc_rejects_host_memory(env):
+    """A CPU tensor is refused before any kernel runs (the binding checks,
+    and so does the library itself for a pointer it is handed directly)."""
+    torch, mhs = env
+    import ctypes
+    inst = I.config_uniform(3)
+    ptr, vtx, dem = _dev(torch, inst)
+    av_host = torch.zeros(inst.n, dtype=torch.uint8)
+    ae = torch.zeros(inst.m, dtype=torch.uint8, device="cuda:0")
+    with pytest.raises(mhs.MhsError) as ei:
+        mhs.kernelize_noalloc(inst.n, inst.m, ptr, vtx, dem, inst.nnz, av_host, ae)
+    assert ei.value.status == mhs.MHS_EINVAL
+    buf = ctypes.create_string_buffer(256)
+    st = mhs.lib().mhs_kernelize_noalloc(
+        inst.n, inst.m, ctypes.c_void_p(ptr.data_ptr()), ctypes.c_void_p(vtx.data_ptr()),
+        ctypes.c_void_p(dem.data_ptr()), inst.nnz, ctypes.c_void_p(av_host.data_ptr()),
+        ctypes.c_void_p(ae.data_ptr()), None, None, buf, 256)
+    assert st == mhs.MHS_EINVAL and b"device memory" in buf.value
+    # the context is unharmed: a valid call still matches
+    ref = _allocating(torch, mhs, inst, ptr, vtx, dem)
+    got = _noalloc(torch, mhs, inst, ptr, vtx, dem)
+    assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
