@@ -112,6 +112,14 @@ typedef struct {
     int32_t sparsity;    /* mhs_sparsity */
     int32_t edge_rule;   /* mhs_edge_rule */
     int32_t full_edges;  /* 1: alternate with rule FE (KernelGPU-FE); needs max_rounds = 0 */
+    /* Tile shape of the tcgen05 contraction (FP8).  Every shape gives the same
+     * result; 0 takes the autotuner's choice for the instance's size class
+     * (see mhs_tile_config). */
+    int32_t tile_m;      /* rows per tile: 0 or 128 */
+    int32_t tile_n;      /* columns per tile: 0, 128 (four TMEM accumulators) or 256 (two) */
+    int32_t group_rows;  /* row blocks per L2 group of the tile order: 0 or 1..4096 */
+    int32_t half_stages; /* 0; 1 = a K block shared in one 64-column half loads as that half;
+                            2 = whole K blocks only */
     int32_t reserved[1]; /* must be zero */
 } mhs_options;
 
@@ -283,11 +291,24 @@ mhs_status mhs_export(const mhs_instance *inst, int32_t index, int32_t *edge_ptr
  */
 mhs_status mhs_set_timing(mhs_instance *inst, int32_t enable);
 /*
- * Tensor-core work done since load (tcgen05 contraction): K steps of
- * 128 x 256 x 64 MACs issued and tiles contracted.  With block-sparse
+ * Tensor-core work done since load (tcgen05 contraction): MMA work in units
+ * of 128 x 128 x 32 MACs issued, and tiles contracted.  With block-sparse
  * skipping this is below the dense formulation's count.
  */
 mhs_status mhs_work_stats(const mhs_instance *inst, int64_t *mma_kblocks, int64_t *mma_tiles);
+
+/*
+ * The tile shape the instance's tcgen05 contraction uses (HOST outputs, any
+ * may be NULL): columns per tile (128 or 256), row blocks per L2 group,
+ * half stages (1 on, 0 off), and whether the autotuner's table gave it
+ * (*from_table = 1) rather than explicit options or the defaults.  The
+ * table is the file named by the environment variable MHS_TILE_TABLE, or
+ * tile_table.txt beside the library, written by the autotuner
+ * (paper_2109_06042_gb300/autotune.py), which times every shape on the GPU
+ * per size class.  The choice changes speed only, never a result.
+ */
+mhs_status mhs_tile_config(const mhs_instance *inst, int32_t *tile_n, int32_t *group_rows,
+                           int32_t *half_stages, int32_t *from_table);
 mhs_status mhs_last_timing(const mhs_instance *inst, float *ms4);
 
 /*

@@ -17,6 +17,18 @@ mhs_status set_error(mhs_status st, const char *fmt, ...);
 // kept for reuse, so load/free loops do not reach the driver).
 cudaError_t pool_for(int dev, cudaMemPool_t *out);
 
+// Tile shape of the tcgen05 contraction for a load: explicit options, else
+// the autotuner's table (tiles.cpp), else the defaults.
+struct TileChoice {
+    int32_t tile_n;       // 128 or 256 columns per tile
+    int32_t group_rows;   // row blocks per L2 group of the tile order
+    int32_t half_stages;  // 1: a K block shared in one half is loaded as that half
+    int32_t from_table;   // 1: the table gave the shape
+};
+// typical_rows: the larger of n and m (a batch: its mean over the instances).
+TileChoice choose_tiles(int32_t count, int64_t typical_rows, const mhs_options &opt);
+const char *tile_table_path();
+
 // InstState::layout_sorted for an mhs_layout option.
 inline int32_t layout_code(int32_t layout) {
     return layout == MHS_LAYOUT_INPUT ? 0 : layout == MHS_LAYOUT_SORTED ? 1 : 2;

@@ -322,7 +322,7 @@ __global__ void k_edge_rows(InstState *st, int count) {
 // ------------------------------------------------------------- planning --
 
 // phase 0: rows = current hyperedges (DP); phase 1: rows = current vertices (MD).
-// tc: 0 popcount tiles, 1 tcgen05 tiles.
+// tc: 0 popcount tiles, 1 tcgen05 tiles (128 x plan->tile_n).
 __global__ void k_plan(InstState *st, Plan *plan, int phase, int tc, BatchCounters *ctr) {
     __shared__ int32_t sh[33];
     __shared__ int64_t sh64[33];
@@ -346,7 +346,7 @@ __global__ void k_plan(InstState *st, Plan *plan, int phase, int tc, BatchCounte
                 // A^T for the ones DP kept)
                 rows = s.m;
                 const int32_t R = phase == 0 ? s.m : s.n;
-                tiles = tc ? tc_tiles(R) : pop_tiles(R);
+                tiles = tc ? tc_tiles(R, plan->tile_n) : pop_tiles(R);
                 act_any = 1;
             }
         }
@@ -1003,7 +1003,7 @@ cudaError_t launch_round_phase(InstState *st, Plan *plan, BatchCounters *ctr, in
                                int phase, int contraction, int sms, int32_t *kerr,
                                cudaStream_t s, cudaEvent_t ev_contract_begin,
                                cudaEvent_t ev_contract_end, int32_t *done_list,
-                               int compact_blocks) {
+                               int compact_blocks, int tile_n) {
     const bool tc = contraction == kFp8;
     k_plan<<<1, 1024, 0, s>>>(st, plan, phase, tc ? 1 : 0, ctr);
     const int grid = grid_for(sms, 8);
@@ -1013,14 +1013,23 @@ cudaError_t launch_round_phase(InstState *st, Plan *plan, BatchCounters *ctr, in
         cudaError_t e = launch_tc_tile_list(st, plan, phase, sms, s);
         if (e != cudaSuccess) return e;
     }
-    if (ev_contract_begin) cudaEventRecordWithFlags(ev_contract_begin, s, cudaEventRecordExternal);
+    // Timing events: external event nodes when the round is being captured
+    // into a graph, plain records when it is launched directly.
+    auto record = [s](cudaEvent_t ev) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+            cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal);
+        else
+            cudaEventRecord(ev, s);
+    };
+    if (ev_contract_begin) record(ev_contract_begin);
     if (tc) {
-        cudaError_t e = launch_tc_contract(st, plan, ctr, phase, sms, kerr, s);
+        cudaError_t e = launch_tc_contract(st, plan, ctr, phase, sms, tile_n, kerr, s);
         if (e != cudaSuccess) return e;
     } else {
         k_pop_contract<<<grid_for(sms, 6), 256, 0, s>>>(st, plan, phase);
     }
-    if (ev_contract_end) cudaEventRecordWithFlags(ev_contract_end, s, cudaEventRecordExternal);
+    if (ev_contract_end) record(ev_contract_end);
     // (the DP pass's clear of A runs inside the MD set pass, which walks the
     // same incidences)
     if (phase == 1) launch_scatter<1>(st, plan, false, tc, grid, s);

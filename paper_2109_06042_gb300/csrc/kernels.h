@@ -36,11 +36,12 @@ cudaError_t launch_build(InstState *st, int count, int32_t max_rounds, int64_t m
 // One phase of a round: phase 0 = DP (Algorithm 1), phase 1 = MD (Algorithm 2).
 // done_list (may be NULL): receives the index of every instance that stops
 // in this round (phase 1); ctr->n_done counts them.
+// tile_n: columns per tcgen05 tile (128 or 256; the value in plan->tile_n).
 cudaError_t launch_round_phase(InstState *st, Plan *plan, BatchCounters *ctr, int count,
                                int phase, int contraction, int sms, int32_t *kerr,
                                cudaStream_t s, cudaEvent_t ev_contract_begin,
                                cudaEvent_t ev_contract_end, int32_t *done_list = nullptr,
-                               int compact_blocks = 1);
+                               int compact_blocks = 1, int tile_n = kTcNDefault);
 // End of one round of the device-side fixpoint loop: keep looping while
 // some instance is active, no error was raised and fewer than round_cap
 // rounds ran (hitting the cap raises kErrRoundCap).
@@ -58,7 +59,7 @@ cudaError_t launch_alive_masks_batch(const InstState *st, int count, uint8_t *al
 
 // tcgen05 contraction (contract_tc.cu)
 cudaError_t launch_tc_contract(InstState *st, Plan *plan, BatchCounters *ctr, int phase, int sms,
-                               int32_t *kerr, cudaStream_t s);
+                               int tile_n, int32_t *kerr, cudaStream_t s);
 // The tiles of phase `phase` that hold nonzero counts (or, in a DP pass of
 // an instance with a hyperedge f > |e|, all tiles), into plan->tile_list.
 cudaError_t launch_tc_tile_list(InstState *st, Plan *plan, int phase, int sms, cudaStream_t s);

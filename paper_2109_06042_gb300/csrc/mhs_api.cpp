@@ -213,6 +213,7 @@ struct mhs_instance {
     int32_t *hkerr = nullptr;
     int64_t max_nnz = 0, max_m = 0, max_n = 0;
     int32_t compact_blocks = 1;  // compaction blocks per instance (> 1: chained scan)
+    TileChoice tiles{kTcNDefault, 16, 1, 0};  // tcgen05 tile shape of this load
     // arena offsets of the batch-wide input arrays
     int64_t in_eptr = 0, in_evtx = 0, in_f = 0;
     int64_t sum_m1 = 0, sum_nnz = 0, sum_m = 0;
@@ -276,6 +277,14 @@ mhs_status check_options(const mhs_options *opt, mhs_options *out) {
         return fail(MHS_EINVAL, "options.full_edges must be 0 or 1");
     if (out->full_edges && out->max_rounds)
         return fail(MHS_EINVAL, "options.full_edges needs max_rounds = 0");
+    if (out->tile_m != 0 && out->tile_m != kTcM)
+        return fail(MHS_EINVAL, "options.tile_m must be 0 (auto) or 128");
+    if (out->tile_n != 0 && out->tile_n != 128 && out->tile_n != 256)
+        return fail(MHS_EINVAL, "options.tile_n must be 0 (autotune), 128 or 256");
+    if (out->group_rows < 0 || out->group_rows > 4096)
+        return fail(MHS_EINVAL, "options.group_rows must be 0 (autotune) or 1..4096");
+    if (out->half_stages < 0 || out->half_stages > 2)
+        return fail(MHS_EINVAL, "options.half_stages must be 0 (autotune), 1 (on) or 2 (off)");
     if (out->reserved[0] != 0) return fail(MHS_EINVAL, "options.reserved must be zero");
     return MHS_OK;
 }
@@ -358,6 +367,11 @@ mhs_status create(int32_t count, const int32_t *n, const int32_t *m, const int64
     h->sum_m = sum_m;
     int64_t c_m1 = 0, c_z = 0, c_m = 0;
     int64_t tiles_dp = 0, tiles_md = 0;
+    if (dense) {  // the tile shape: options, else the autotuner's table for this size class
+        int64_t rows = 0;
+        for (int b = 0; b < count; ++b) rows += std::max<int64_t>(n[b], m[b]);
+        h->tiles = choose_tiles(count, rows / std::max(count, 1), opt);
+    }
     for (int b = 0; b < count; ++b) {
         Layout &L = lay[b];
         const int64_t n0 = n[b], m0 = m[b], z = nnz[b];
@@ -403,8 +417,8 @@ mhs_status create(int32_t count, const int32_t *n, const int32_t *m, const int64
         } else {
             L.occ0 = L.occ1 = -1;
         }
-        tiles_dp += tc_tiles((int32_t)m0);
-        tiles_md += tc_tiles((int32_t)n0);
+        tiles_dp += tc_tiles((int32_t)m0, h->tiles.tile_n);
+        tiles_md += tc_tiles((int32_t)n0, h->tiles.tile_n);
     }
     // the operands of all instances, contiguous in their own allocation,
     // all zero at load: the scatter/clear passes leave them all-zero between
@@ -549,7 +563,9 @@ mhs_status create(int32_t count, const int32_t *n, const int32_t *m, const int64
     p.tile_off = reinterpret_cast<int64_t *>(base + off_tileoff);
     p.tile_list = reinterpret_cast<int64_t *>(base + off_list);
     p.list_cap = (int32_t)std::min<int64_t>(list_cap, INT32_MAX);
-    p.group_rows = tile_group_rows();
+    p.group_rows = h->tiles.group_rows;
+    p.tile_n = h->tiles.tile_n;
+    p.half_stages = h->tiles.half_stages;
     std::memcpy(h->pin + 128, &p, sizeof(p));  // staged in pinned memory: no synchronisation
     ce = cudaMemcpyAsync(h->dplan, h->pin + 128, sizeof(p), cudaMemcpyHostToDevice, h->stream);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(h->dkerr, 0, 4, h->stream);
@@ -620,11 +636,12 @@ cudaError_t enqueue_round(mhs_instance *h, bool with_events) {
                                        h->sms, h->dkerr, h->stream,
                                        with_events ? h->ev[0] : nullptr,
                                        with_events ? h->ev[1] : nullptr, nullptr,
-                                       h->compact_blocks);
+                                       h->compact_blocks, h->tiles.tile_n);
     if (e != cudaSuccess) return e;
     e = launch_round_phase(h->dstate, h->dplan, h->dctr, h->count, 1, h->contraction, h->sms,
                            h->dkerr, h->stream, with_events ? h->ev[2] : nullptr,
-                           with_events ? h->ev[3] : nullptr, nullptr, h->compact_blocks);
+                           with_events ? h->ev[3] : nullptr, nullptr, h->compact_blocks,
+                           h->tiles.tile_n);
     if (e == cudaSuccess && h->opt.full_edges)
         e = launch_full_edges(h->dstate, h->count, h->dctr, nullptr, h->sms, h->stream);
     if (e != cudaSuccess) return e;
@@ -685,11 +702,11 @@ mhs_status build_loop_graph(mhs_instance *h) {
     if (e != cudaSuccess) return bail(e, "capture");
     cudaError_t e1 = launch_round_phase(h->dstate, h->dplan, h->dctr, h->count, 0, h->contraction,
                                         h->sms, h->dkerr, h->stream, nullptr, nullptr, nullptr,
-                                        h->compact_blocks);
+                                        h->compact_blocks, h->tiles.tile_n);
     if (e1 == cudaSuccess)
         e1 = launch_round_phase(h->dstate, h->dplan, h->dctr, h->count, 1, h->contraction, h->sms,
                                 h->dkerr, h->stream, nullptr, nullptr, nullptr,
-                                h->compact_blocks);
+                                h->compact_blocks, h->tiles.tile_n);
     if (e1 == cudaSuccess && h->opt.full_edges)
         e1 = launch_full_edges(h->dstate, h->count, h->dctr, nullptr, h->sms, h->stream);
     if (e1 == cudaSuccess)
@@ -1253,6 +1270,16 @@ mhs_status mhs_work_stats(const mhs_instance *inst, int64_t *mma_kblocks, int64_
     CUDA_TRY(cudaStreamSynchronize(inst->stream));
     if (mma_kblocks) *mma_kblocks = (int64_t)c.mma_kblocks;
     if (mma_tiles) *mma_tiles = (int64_t)c.mma_tiles;
+    return MHS_OK;
+}
+
+mhs_status mhs_tile_config(const mhs_instance *inst, int32_t *tile_n, int32_t *group_rows,
+                           int32_t *half_stages, int32_t *from_table) {
+    if (!inst) return fail(MHS_EINVAL, "instance is NULL");
+    if (tile_n) *tile_n = inst->tiles.tile_n;
+    if (group_rows) *group_rows = inst->tiles.group_rows;
+    if (half_stages) *half_stages = inst->tiles.half_stages;
+    if (from_table) *from_table = inst->tiles.from_table;
     return MHS_OK;
 }
 

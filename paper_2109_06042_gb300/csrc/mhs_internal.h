@@ -22,8 +22,8 @@ namespace mhs {
 
 // Tile shapes.
 constexpr int kPopTile = 64;     // popcount contraction: 64 x 64 pair tiles
-constexpr int kTcM = 128;        // tcgen05 contraction: 128 rows (i) ...
-constexpr int kTcN = 256;        // ... x 256 columns (j) per tile
+constexpr int kTcM = 128;        // tcgen05 contraction: 128 rows (i) x 128 or 256 columns (j)
+constexpr int kTcNDefault = 256; // per tile; the wider tile unless chosen otherwise
 constexpr int kTcK = 128;        // K bytes per pipeline stage (FP8)
 constexpr int kOccK = 64;        // K columns per occupancy bit (half a stage)
 constexpr int kRowAlign = 256;   // row capacity rounded to this
@@ -144,6 +144,8 @@ struct Plan {
     int32_t *row_off;       // [count+1] prefix of current hyperedges of active instances
     int64_t *tile_off;      // [count+1] prefix of tiles
     int32_t list_next;      // tcgen05: next tile_list entry to hand out (dynamic schedule)
+    int32_t tile_n;         // tcgen05: columns per tile, 128 or 256 (rows: kTcM)
+    int32_t half_stages;    // tcgen05: 1 = load a K block shared in one half as that half
     int32_t pad_;
 };
 
@@ -166,17 +168,22 @@ __host__ __device__ inline void unpack_tile(int64_t v, int *b, int32_t *bi, int3
     *bj = (int32_t)(v & 0xFFFFF);
 }
 
-// tcgen05 tiles: row blocks of kTcM, column blocks of kTcN; a tile is needed
-// if it holds some pair i < j (j < R).
-__host__ __device__ inline int32_t tc_col_blocks(int32_t R) { return (R + kTcN - 1) / kTcN; }
+// tcgen05 tiles: row blocks of kTcM, column blocks of tn = r * kTcM columns
+// (r = 1 or 2); tile (bi, bj) is needed iff it holds some pair i < j (j < R),
+// i.e. bj >= floor(bi / r).
+__host__ __device__ inline int32_t tc_col_blocks(int32_t R, int32_t tn) { return (R + tn - 1) / tn; }
 __host__ __device__ inline int32_t tc_row_blocks(int32_t R) { return (R + kTcM - 1) / kTcM; }
-// first column block holding a j > i for some i in row block bi
-__host__ __device__ inline int32_t tc_first_cb(int32_t bi) { return (bi * kTcM + 1) / kTcN; }
-__host__ __device__ inline int64_t tc_tiles(int32_t R) {
+// sum over b < bi of floor(b / r), for r = 1 or 2
+__host__ __device__ inline int64_t tc_floor_sum(int64_t bi, int32_t r) {
+    if (r == 1) return bi * (bi - 1) / 2;
+    return (bi / 2) * ((bi - 1) / 2 > 0 ? (bi - 1) / 2 : 0);
+}
+__host__ __device__ inline int64_t tc_tiles(int32_t R, int32_t tn) {
     if (R <= 1) return 0;
-    // sum over row blocks bi of (cb - floor(bi/2))
-    const int64_t rb = tc_row_blocks(R), cb = tc_col_blocks(R);
-    return rb * cb - (rb / 2) * ((rb - 1) / 2 > 0 ? (rb - 1) / 2 : 0);
+    // sum over row blocks bi of (cb - floor(bi / r))
+    const int32_t r = tn / kTcM;
+    const int64_t rb = tc_row_blocks(R), cb = tc_col_blocks(R, tn);
+    return rb * cb - tc_floor_sum(rb, r);
 }
 
 }  // namespace mhs

@@ -534,6 +534,8 @@ mhs_status setup_lane(mhs_server *S, Lane &Ln, int id, int32_t slots, int64_t li
     p.tile_list = reinterpret_cast<int64_t *>(Ln.ctl + o_list);
     p.list_cap = (int32_t)std::min<int64_t>(list_cap, INT32_MAX);
     p.group_rows = tile_group_rows();
+    p.tile_n = kTcNDefault;  // the server's lanes contract with the default tile shape
+    p.half_stages = 1;
     cudaError_t e = cudaMemsetAsync(Ln.ctl, 0, (size_t)o_list, Ln.stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(Ln.dplan, &p, sizeof(p), cudaMemcpyHostToDevice, Ln.stream);
@@ -677,7 +679,9 @@ mhs_status mhs_submit(mhs_server *S, int32_t n, int32_t m, const int32_t *edge_p
     r->dem.assign(demand, demand + m);
     r->footprint = plan_layout(n, m, nnz, S->contraction == kFp8, S->opt.full_edges != 0).bytes;
     // tile-list entries only matter for the tcgen05 contraction
-    r->tiles = S->contraction == kFp8 ? std::max(tc_tiles(m), tc_tiles(n)) : 0;
+    r->tiles = S->contraction == kFp8
+                   ? std::max(tc_tiles(m, kTcNDefault), tc_tiles(n, kTcNDefault))
+                   : 0;
     if (S->contraction == kFp8 && r->tiles > kServerListCap)
         return set_error(MHS_ENOMEM, "instance needs %lld tiles, over the server's %lld",
                          (long long)r->tiles, (long long)kServerListCap);

@@ -41,7 +41,9 @@ class Options(ctypes.Structure):
     _fields_ = [("contraction", ctypes.c_int32), ("max_rounds", ctypes.c_int32),
                 ("use_graphs", ctypes.c_int32), ("layout", ctypes.c_int32),
                 ("sparsity", ctypes.c_int32), ("edge_rule", ctypes.c_int32),
-                ("full_edges", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
+                ("full_edges", ctypes.c_int32), ("tile_m", ctypes.c_int32),
+                ("tile_n", ctypes.c_int32), ("group_rows", ctypes.c_int32),
+                ("half_stages", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
 
 
 class RoundStats(ctypes.Structure):
@@ -102,6 +104,7 @@ _SIGS = {
     "mhs_set_timing": (_i32, [_vp, _i32]),
     "mhs_work_stats": (_i32, [_vp, _P64, _P64]),
     "mhs_last_timing": (_i32, [_vp, ctypes.POINTER(ctypes.c_float)]),
+    "mhs_tile_config": (_i32, [_vp, _P32, _P32, _P32, _P32]),
     "mhs_kernelize_noalloc": (_i32, [_i32, _i32, _vp, _vp, _vp, _i32, _vp, _vp, _P32, _vp,
                                      ctypes.c_char_p, ctypes.c_size_t]),
     "mhs_server_default_options": (_i32, [ctypes.POINTER(ServerOptions)]),
@@ -172,8 +175,18 @@ def set_default_layout(layout: str):
     _DEFAULT_LAYOUT[0] = layout
 
 
+_DEFAULT_TILES = [None]
+
+
+def set_default_tiles(tiles):
+    """Tile shape used by the helpers below when none is given: None (the
+    autotuner's choice) or a dict with any of tile_n (128, 256), group_rows
+    and half_stages (True / False)."""
+    _DEFAULT_TILES[0] = tiles
+
+
 def make_options(contraction="auto", max_rounds=0, use_graphs=True, layout=None,
-                 sparsity=None, rule=None, full_edges=None) -> Options:
+                 sparsity=None, rule=None, full_edges=None, tiles=None) -> Options:
     o = Options()
     _check(lib().mhs_default_options(ctypes.byref(o)))
     o.contraction = CONTRACTIONS[contraction] if isinstance(contraction, str) else int(contraction)
@@ -187,6 +200,12 @@ def make_options(contraction="auto", max_rounds=0, use_graphs=True, layout=None,
     full_edges = _DEFAULT_VARIANT[1] if full_edges is None else full_edges
     o.edge_rule = RULES[rule] if isinstance(rule, str) else int(rule)
     o.full_edges = int(bool(full_edges))
+    tiles = _DEFAULT_TILES[0] if tiles is None else tiles
+    if tiles:
+        o.tile_n = int(tiles.get("tile_n", 0))
+        o.group_rows = int(tiles.get("group_rows", 0))
+        hs = tiles.get("half_stages")
+        o.half_stages = 0 if hs is None else (1 if hs else 2)
     return o
 
 
@@ -208,7 +227,7 @@ class Instance:
     # ---- loading ----
     @classmethod
     def load(cls, inst, contraction="auto", max_rounds=0, use_graphs=True, stream=None,
-             layout=None, sparsity=None, rule=None, full_edges=None):
+             layout=None, sparsity=None, rule=None, full_edges=None, tiles=None):
         """mhs_load from host arrays of an ``instances.Instance``-like object."""
         ptr = np.ascontiguousarray(inst.edge_ptr, dtype=np.int32)
         vtx = np.ascontiguousarray(inst.edge_vtx, dtype=np.int32)
@@ -217,7 +236,8 @@ class Instance:
             vtx = np.zeros(1, np.int32)
         if dem.size == 0:
             dem = np.zeros(1, np.int32)
-        opt = make_options(contraction, max_rounds, use_graphs, layout, sparsity, rule, full_edges)
+        opt = make_options(contraction, max_rounds, use_graphs, layout, sparsity, rule, full_edges,
+                           tiles)
         h = ctypes.c_void_p()
         _check(lib().mhs_load(int(inst.n), int(inst.m), _p32(ptr), _p32(vtx), _p32(dem),
                               int(inst.k), ctypes.byref(opt), _stream_ptr(stream),
@@ -227,9 +247,10 @@ class Instance:
     @classmethod
     def load_device(cls, n, m, edge_ptr, edge_vtx, demand, k, contraction="auto", max_rounds=0,
                     use_graphs=True, stream=None, layout=None, sparsity=None, rule=None,
-                    full_edges=None):
+                    full_edges=None, tiles=None):
         """mhs_load_device from CUDA tensors (int32, contiguous)."""
-        opt = make_options(contraction, max_rounds, use_graphs, layout, sparsity, rule, full_edges)
+        opt = make_options(contraction, max_rounds, use_graphs, layout, sparsity, rule, full_edges,
+                           tiles)
         h = ctypes.c_void_p()
         _check(lib().mhs_load_device(int(n), int(m), ctypes.c_void_p(edge_ptr.data_ptr()),
                                      ctypes.c_void_p(edge_vtx.data_ptr()),
@@ -239,7 +260,7 @@ class Instance:
 
     @classmethod
     def load_batch(cls, insts, contraction="auto", max_rounds=0, use_graphs=True, stream=None,
-                   rule=None, full_edges=None):
+                   rule=None, full_edges=None, tiles=None):
         """mhs_load_batch from a list of host instances."""
         count = len(insts)
         n = np.array([i.n for i in insts], dtype=np.int32)
@@ -255,13 +276,15 @@ class Instance:
         vtx = np.concatenate([np.asarray(i.edge_vtx, np.int32) for i in insts] + [np.zeros(1, np.int32)])
         dem = np.concatenate([np.asarray(i.demand, np.int32) for i in insts] + [np.zeros(1, np.int32)])
         return cls.load_batch_arrays(count, n, m, ptr, vtx, dem, k, contraction, max_rounds,
-                                     use_graphs, stream, rule=rule, full_edges=full_edges)
+                                     use_graphs, stream, rule=rule, full_edges=full_edges,
+                                     tiles=tiles)
 
     @classmethod
     def load_batch_arrays(cls, count, n, m, ptr, vtx, dem, k, contraction="auto", max_rounds=0,
                           use_graphs=True, stream=None, layout=None, sparsity=None, rule=None,
-                          full_edges=None):
-        opt = make_options(contraction, max_rounds, use_graphs, layout, sparsity, rule, full_edges)
+                          full_edges=None, tiles=None):
+        opt = make_options(contraction, max_rounds, use_graphs, layout, sparsity, rule, full_edges,
+                           tiles)
         h = ctypes.c_void_p()
         _check(lib().mhs_load_batch(int(count), _p32(n), _p32(m), ptr.ctypes.data_as(_P64),
                                     _p32(vtx), _p32(dem), k.ctypes.data_as(_P64),
@@ -271,13 +294,14 @@ class Instance:
     @classmethod
     def load_batch_device(cls, n, m, k, edge_ptr, edge_vtx, demand, contraction="auto",
                           max_rounds=0, use_graphs=True, stream=None, layout=None, sparsity=None,
-                          rule=None, full_edges=None):
+                          rule=None, full_edges=None, tiles=None):
         """mhs_load_batch_device: n, m, k host numpy arrays; edge_ptr (int64),
         edge_vtx, demand (int32) CUDA tensors over the concatenated instances."""
         n = np.ascontiguousarray(n, dtype=np.int32)
         m = np.ascontiguousarray(m, dtype=np.int32)
         k = np.ascontiguousarray(k, dtype=np.int64)
-        opt = make_options(contraction, max_rounds, use_graphs, layout, sparsity, rule, full_edges)
+        opt = make_options(contraction, max_rounds, use_graphs, layout, sparsity, rule, full_edges,
+                           tiles)
         h = ctypes.c_void_p()
         _check(lib().mhs_load_batch_device(int(n.size), _p32(n), _p32(m),
                                            ctypes.c_void_p(edge_ptr.data_ptr()),
@@ -306,8 +330,15 @@ class Instance:
         _check(lib().mhs_last_timing(self._h, a))
         return {"dp_ms": a[0], "md_ms": a[1], "other_ms": a[2], "total_ms": a[3]}
 
+    def tile_config(self) -> dict:
+        """The tcgen05 tile shape of this load (options, table or defaults)."""
+        v = [ctypes.c_int32() for _ in range(4)]
+        _check(lib().mhs_tile_config(self._h, *[ctypes.byref(x) for x in v]))
+        return {"tile_n": v[0].value, "group_rows": v[1].value,
+                "half_stages": bool(v[2].value), "from_table": bool(v[3].value)}
+
     def work_stats(self):
-        """(K steps of 128x256x64 MACs issued, tiles contracted) since load."""
+        """(MMA work in units of 128x128x32 MACs, tiles contracted) since load."""
         kb = ctypes.c_int64()
         tl = ctypes.c_int64()
         _check(lib().mhs_work_stats(self._h, ctypes.byref(kb), ctypes.byref(tl)))
@@ -394,11 +425,11 @@ class Instance:
 
 
 def kernelize(inst, contraction="auto", max_rounds=0, use_graphs=True, layout=None,
-              sparsity=None, rule=None, full_edges=None) -> dict:
+              sparsity=None, rule=None, full_edges=None, tiles=None) -> dict:
     """Load, reduce to the fixpoint and return the result of one host instance
     (with ``full_edges`` also 'forced' and 'fe_passes')."""
     with Instance.load(inst, contraction, max_rounds, use_graphs, layout=layout,
-                       sparsity=sparsity, rule=rule, full_edges=full_edges) as h:
+                       sparsity=sparsity, rule=rule, full_edges=full_edges, tiles=tiles) as h:
         h.kernelize()
         res = h.result()
         if (_DEFAULT_VARIANT[1] if full_edges is None else full_edges):

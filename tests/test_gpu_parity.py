@@ -405,3 +405,18 @@ def test_reused_operand_regions(mhs):
             with mhs.Instance.load(inst, contraction="fp8", full_edges=True) as h:
                 h.kernelize()
             _same(mhs.kernelize(inst, contraction="popcount"), ref, f"rep {rep} popcount")
+
+
+@pytest.mark.parametrize("graphs", [True, False])
+@pytest.mark.parametrize("mode", MODES)
+def test_timing_mode(mhs, graphs, mode):
+    """Per-phase CUDA-event timing (mhs_set_timing) works with captured
+    per-round graphs and with direct launches, and does not change results."""
+    inst = I.config_powerlaw(3, n=3000, m=6000)
+    with mhs.Instance.load(inst, contraction=mode, use_graphs=graphs) as h:
+        h.set_timing(True)
+        h.kernelize()
+        t = h.last_timing()
+        _same(h.result(), O.reduce(inst), f"graphs={graphs}")
+    assert t["dp_ms"] > 0 and t["md_ms"] > 0 and t["other_ms"] >= 0
+    assert t["total_ms"] >= t["dp_ms"] + t["md_ms"] - 1e-3
