@@ -1,29 +1,37 @@
 #!/usr/bin/env python
 """Throughput of the exhaustive DP + MD kernelization (Algorithm 3) on GB300.
 
-A step is the complete kernelization of one instance, or of one batch of
-instances, with the inputs (CSR arrays) already resident in HBM:
+A step is the complete kernelization of one instance (repeated --reps
+times, so that the timed region is long enough to sample the clocks), or
+of one batch of instances, with the inputs (CSR arrays) already resident
+in HBM:
 
 * load from device arrays;
 * every round of DP (Algorithm 1) and MD (Algorithm 2), with their
   contractions and compaction;
 * the result masks written to device memory.
 
-``value`` is reduced instances per second over all GPUs.  The line also
-carries:
+``value`` is reduced instances per second over all GPUs, on the power-law
+20,000 x 40,000 instance (the headline).  The line also carries:
 
 * pair tests per second;
-* the roofline of the dominant kernel (the contraction), from its CUDA-event
-  times in the timed region and the algorithmic work the library's own
-  per-round trace gives;
+* the roofline of the dominant kernel (the tcgen05 contraction): the
+  tensor work it issues over its CUDA-event time, against the FP8 peak;
+  beside it the dense formulation's ratio and the sparse intrinsic work;
 * the CPU oracle timed on the host (bounded sample);
 * an end-to-end figure through host buffers;
-* the SM clocks seen.
+* the SM clocks seen;
+* ``configs``: the other workloads on the same GPU -- uniform 200 x 400,
+  interval 50,000 x 100,000, the batch of 4,096 uneven instances (with its
+  autotuned and fixed tile shapes and the one-instance-per-launch loop),
+  and a short serving sweep with measured latencies of the served and the
+  plain one-at-a-time form under the same Poisson arrivals.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-       [--workload powerlaw|uniform|interval|batch] [--contraction fp8|popcount]
+       [--workload all|powerlaw|uniform|interval|batch|stream] [--contraction fp8|popcount]
 N > 1 runs under torchrun; each rank reduces its own instances, with no
-data-path collective (weak scaling).
+data-path collective (weak scaling); the other workloads are measured at
+N = 1 only.
 """
 from __future__ import annotations
 
@@ -45,16 +53,20 @@ sys.path.insert(0, ROOT)
 METRIC = "reduced instances/s (exhaustive DP+MD kernelization)"
 UNIT = "instances/s"
 DATA = "synthetic (seeded generators with the shapes of the paper's workloads)"
+DEFAULT_TILES = dict(tile_n=256, group_rows=16, half_stages=True)
+# kernelizations per timed step of a single-instance workload
+REPS = {"powerlaw": 16, "uniform": 64, "interval": 2, "batch": 1}
 
 
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", choices=["powerlaw", "uniform", "interval", "batch", "stream"],
-                   default="powerlaw")
+    p.add_argument("--workload", choices=["all", "powerlaw", "uniform", "interval", "batch",
+                                          "stream"], default="all",
+                   help="all: the power-law headline plus the other workloads as sub-records")
     p.add_argument("--contraction", choices=["fp8", "popcount"], default="fp8")
     p.add_argument("--sparsity", choices=["skip", "dense"], default="skip",
                    help="tcgen05 block-sparse skipping (exact) or the dense formulation")
@@ -63,9 +75,12 @@ def parse():
     p.add_argument("--full-edges", action="store_true",
                    help="alternate with rule FE at every fixpoint (KernelGPU-FE variant)")
     p.add_argument("--seed", type=int, default=0)
+    p.add_argument("--reps", type=int, default=0,
+                   help="kernelizations per timed step (0: per workload, see REPS)")
     p.add_argument("--batch-count", type=int, default=4096)
     p.add_argument("--cpu-seconds", type=float, default=15.0,
                    help="bound on the CPU oracle sample")
+    p.add_argument("--sub-steps", type=int, default=10, help="timed steps of each sub-record")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-loop", action="store_true", help="batch: skip the per-instance loop")
@@ -73,13 +88,22 @@ def parse():
     p.add_argument("--pool", type=int, default=300, help="stream: distinct request instances")
     p.add_argument("--rates", type=str, default="0.25,0.5,1,1.5,2",
                    help="stream: arrival rates as multiples of the saturating rate")
+    p.add_argument("--sub-requests", type=int, default=300,
+                   help="all: requests per rate of the short serving sweep")
+    p.add_argument("--sub-rates", type=str, default="0.5,1,2",
+                   help="all: rates of the short serving sweep")
     return p.parse_args()
 
 
-def make_instances(args, rank):
+def headline_workload(args):
+    return "powerlaw" if args.workload == "all" else args.workload
+
+
+def make_instances(args, rank, workload=None):
     from paper_2109_06042_gb300 import instances as I
-    if args.workload == "batch":
-        seed0 = shard_seed0(args, rank)
+    workload = workload or headline_workload(args)
+    if workload == "batch":
+        seed0 = shard_seed0(args, rank, workload)
         insts = I.config_batch(args.batch_count, seed0)
         nn = sum(i.n for i in insts)
         mm = sum(i.m for i in insts)
@@ -87,17 +111,17 @@ def make_instances(args, rank):
         desc = (f"batch of {len(insts)} uneven instances (n~U[50,2000], m~U[n,2n], "
                 f"|e|~U[2,16]), sum n={nn} sum m={mm} nnz={zz} seeds {seed0}..{seed0 + len(insts) - 1}")
         return insts, desc
-    seed = shard_seed0(args, rank)
+    seed = shard_seed0(args, rank, workload)
     f = {"powerlaw": I.config_powerlaw, "uniform": I.config_uniform,
-         "interval": I.config_interval}[args.workload]
+         "interval": I.config_interval}[workload]
     inst = f(seed)
-    desc = f"{args.workload} n={inst.n} m={inst.m} nnz={inst.nnz} seed={seed}"
+    desc = f"{workload} n={inst.n} m={inst.m} nnz={inst.nnz} seed={seed}"
     return [inst], desc
 
 
-def shard_seed0(args, rank):
+def shard_seed0(args, rank, workload=None):
     """First seed of this rank's instances: ranks reduce disjoint instances."""
-    if args.workload == "batch":
+    if (workload or headline_workload(args)) == "batch":
         return 4000 + rank * args.batch_count
     return args.seed + rank
 
@@ -276,6 +300,101 @@ class DeviceInputs:
         self.ae = torch.empty(int(self.m.sum()) + 1, dtype=torch.uint8, device=dev)
 
 
+class Runner:
+    """One workload on the library's stream: load from device arrays,
+    kernelize, write the result masks; `reps` kernelizations per step."""
+
+    def __init__(self, torch, mhs, stream, insts, args, tiles=None, reps=1):
+        self.torch, self.mhs, self.stream = torch, mhs, stream
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.D = DeviceInputs(torch, dev, insts)
+        self.insts = insts
+        self.batch = len(insts) > 1
+        self.args = args
+        self.tiles = tiles
+        self.reps = reps
+
+    def load(self):
+        D, a = self.D, self.args
+        if self.batch:
+            return self.mhs.Instance.load_batch_device(D.n, D.m, D.k, D.ptr64, D.vtx, D.dem,
+                                                       contraction=a.contraction,
+                                                       stream=self.stream, tiles=self.tiles)
+        i = self.insts[0]
+        return self.mhs.Instance.load_device(i.n, i.m, D.ptr32, D.vtx, D.dem, i.k,
+                                             contraction=a.contraction, stream=self.stream,
+                                             tiles=self.tiles)
+
+    def one(self, timing=False):
+        """One kernelization; with timing, the contraction's event times and
+        the tensor work counter."""
+        h = self.load()
+        if timing:
+            h.set_timing(True)  # per-round graphs with event nodes around the contractions
+        h.kernelize()           # default: the whole fixpoint as one graph launch
+        if self.batch:
+            h.result_batch_device(self.D.av, self.D.ae)
+        else:
+            h.result_device(self.D.av, self.D.ae)
+        t = None
+        if timing:
+            t = h.last_timing()
+            if self.args.contraction == "fp8":
+                t["kblocks"], t["tiles"] = h.work_stats()
+        self.cfg = h.tile_config() if self.args.contraction == "fp8" else None
+        h.free()
+        return t
+
+    def step(self):
+        for _ in range(self.reps):
+            self.one()
+
+    def traces(self):
+        h = self.load()
+        st = h.kernelize()
+        tr = [h.trace(b)[0] for b in range(self.D.count)]
+        h.free()
+        return tr, int(st["rounds"])
+
+    def timed(self, steps, warmup):
+        """(ms of `steps` steps on the library's stream, CUDA events; then
+        the contraction's ms and work counter summed over as many timed
+        kernelizations)."""
+        torch = self.torch
+        for _ in range(warmup):
+            self.step()
+            self.one(timing=True)
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(self.stream)
+        for _ in range(steps):
+            self.step()
+        ev1.record(self.stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        contract_ms, kblocks = 0.0, 0
+        for _ in range(steps):
+            t = self.one(timing=True)
+            contract_ms += t["dp_ms"] + t["md_ms"]
+            kblocks += t.get("kblocks", 0)
+        torch.cuda.synchronize()
+        return ms, contract_ms, kblocks
+
+
+def contraction_roofline(args, peaks, kind, flops_per_k, contract_ms, kblocks, steps):
+    """issued tensor TFLOP/s and fractions (per timed kernelization)."""
+    s_per_k = contract_ms / steps / 1e3
+    dense_equiv = flops_per_k / s_per_k / 1e12 if s_per_k > 0 else 0.0
+    if args.contraction == "fp8":
+        peak = 2.0 * peaks["bf16_tflops"]
+        issued = kblocks * 2.0 * 128 * 128 * 32 / (contract_ms / 1e3) / 1e12 if contract_ms else 0
+        return {"issued_tflops": round(issued, 2), "frac": round(issued / peak, 4),
+                "dense_equiv_frac": round(dense_equiv / peak, 4),
+                "contract_ms_per_kernelization": round(contract_ms / steps, 4)}
+    return {"contract_ms_per_kernelization": round(contract_ms / steps, 4)}
+
+
 def run_ours(args, rank, world, dist):
     import torch
     from paper_2109_06042_gb300 import build as B
@@ -286,44 +405,18 @@ def run_ours(args, rank, world, dist):
     from paper_2109_06042_gb300 import mhs
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.Stream(device=dev)  # the library runs all its work on this stream
+    workload = headline_workload(args)
     insts, desc = make_instances(args, rank)
-    D = DeviceInputs(torch, dev, insts)
-    batch = args.workload == "batch"
+    reps = args.reps or REPS.get(workload, 1)
+    R = Runner(torch, mhs, stream, insts, args, reps=reps)
+    D = R.D
+    batch = R.batch
 
     mhs.set_default_sparsity(args.sparsity)
     mhs.set_default_variant(args.rule, args.full_edges)
 
-    def load():
-        if batch:
-            return mhs.Instance.load_batch_device(D.n, D.m, D.k, D.ptr64, D.vtx, D.dem,
-                                                  contraction=args.contraction, stream=stream)
-        i = insts[0]
-        return mhs.Instance.load_device(i.n, i.m, D.ptr32, D.vtx, D.dem, i.k,
-                                        contraction=args.contraction, stream=stream)
-
-    def step(timing=False):
-        h = load()
-        if timing:
-            h.set_timing(True)  # per-round graphs with event nodes around the contractions
-        h.kernelize()           # default: the whole fixpoint as one graph launch
-        if batch:
-            h.result_batch_device(D.av, D.ae)
-        else:
-            h.result_device(D.av, D.ae)
-        t = None
-        if timing:
-            t = h.last_timing()
-            if args.contraction == "fp8":
-                t["kblocks"], t["tiles"] = h.work_stats()
-        h.free()
-        return t
-
     # untimed: the library's per-round trace of every instance -> algorithmic work
-    h = load()
-    st = h.kernelize()
-    traces = [h.trace(b)[0] for b in range(D.count)]
-    rounds = int(st["rounds"])
-    h.free()
+    traces, rounds = R.traces()
     flops, pairs, bits_bytes = algorithmic_work(traces)
     # untimed: round by round through the public API, the alive sets entering
     # each round (single instance) -> the sparse intrinsic work
@@ -350,36 +443,22 @@ def run_ours(args, rank, world, dist):
     clocks = ClockSampler(gpu_index)
     clocks.start()  # running before the timed region starts
     for _ in range(args.warmup):
-        step()
-        step(timing=True)
+        R.step()
+        R.one(timing=True)
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
     t_window0 = time.time()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for _ in range(args.steps):
-        step()
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    # second timed region of the same length: CUDA events on the library's
-    # stream around every contraction launch give the kernel's durations
-    contract_ms = 0.0
-    kblocks = 0
-    for _ in range(args.steps):
-        t = step(timing=True)
-        contract_ms += t["dp_ms"] + t["md_ms"]
-        kblocks += t.get("kblocks", 0)
-    torch.cuda.synchronize()
+    ms, contract_ms, kblocks = R.timed(args.steps, 0)
     clocks.mark(t_window0, time.time())
     if dist is not None:
         dist.barrier()
     clk = clocks.stop()
-    ms = max_over_ranks(ev0.elapsed_time(ev1), dist, dev)
+    ms = max_over_ranks(ms, dist, dev)
     ms_per_step = ms / args.steps
-    value = job_throughput(world, D.count, args.steps, ms)
+    units_per_step = D.count * reps
+    value = job_throughput(world, units_per_step, args.steps, ms)
 
     # end to end through host buffers: load from host arrays, result masks back to host
     e2e = None
@@ -404,45 +483,23 @@ def run_ours(args, rank, world, dist):
         for _ in range(max(1, args.warmup // 2)):
             e2e_step()
         torch.cuda.synchronize()
+        n_e2e = args.steps * (reps if not batch else 1)
         t0 = time.perf_counter()
-        for _ in range(args.steps):
+        for _ in range(n_e2e):
             e2e_step()
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
         h2d = 8 * ptr.size + 4 * (vtx.size + dem.size) if batch else \
             4 * (insts[0].m + 1 + insts[0].nnz + insts[0].m)
-        e2e = {"value": round(world * D.count * args.steps / e2e_s, 4), "unit": UNIT,
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(D.av.numel() + D.ae.numel())}
-
-    # the plain one-instance-per-call form on the same GPU (batch only)
-    loop = None
-    if batch and not args.no_loop:
-        singles = []
-        for i in insts:
-            singles.append((i, torch.from_numpy(i.edge_ptr.astype(np.int32)).to(dev),
-                            torch.from_numpy(i.edge_vtx if i.nnz else np.zeros(1, np.int32)).to(dev),
-                            torch.from_numpy(i.demand if i.m else np.zeros(1, np.int32)).to(dev)))
-        for i, p_, v_, d_ in singles[:8]:
-            hh = mhs.Instance.load_device(i.n, i.m, p_, v_, d_, i.k, contraction=args.contraction,
-                                          stream=stream)
-            hh.kernelize()
-            hh.free()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for i, p_, v_, d_ in singles:
-            hh = mhs.Instance.load_device(i.n, i.m, p_, v_, d_, i.k, contraction=args.contraction,
-                                          stream=stream)
-            hh.kernelize()
-            hh.result_device(D.av, D.ae)
-            hh.free()
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        loop = {"value": round(D.count / dt, 2), "unit": UNIT,
-                "form": "mhs_load_device + mhs_kernelize + mhs_result_device per instance"}
+        e2e = {"value": round(world * D.count * n_e2e / e2e_s, 4), "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(D.av.numel() + D.ae.numel()),
+               "form": "mhs_load (host CSR) + mhs_kernelize + result masks to host, per instance"
+                       if not batch else "mhs_load_batch (host CSR) + mhs_kernelize + masks to host"}
 
     peaks, kind = load_peaks()
-    per_launch = contract_ms / args.steps / (2 * rounds)
-    contract_s_per_step = contract_ms / args.steps / 1e3
+    launches = 2 * rounds
+    per_launch = contract_ms / args.steps / launches
+    contract_s_per_step = contract_ms / args.steps / 1e3  # per timed kernelization
     dense_equiv = flops / contract_s_per_step / 1e12
     prof = kernel_profile(args)
     if args.contraction == "fp8":
@@ -457,15 +514,16 @@ def run_ours(args, rank, world, dist):
                 "unit": "TFLOP/s", "frac": round(issued / peak, 4),
                 "traffic": prof.get("traffic_bytes_per_launch"),
                 "kernel": "k_tc_contract", "peak_source": f"{kind}: 2 x bf16_tflops (burst)",
-                "launches_per_step": 2 * rounds, "avg_launch_ms": round(per_launch, 4),
+                "launches_per_kernelization": launches, "avg_launch_ms": round(per_launch, 4),
                 "achieved_basis": "tensor MACs issued x 2 (kernel counter)",
-                "issued_flops_per_step": kblocks * 2.0 * 128 * 128 * 32 / args.steps,
+                "issued_flops_per_kernelization": kblocks * 2.0 * 128 * 128 * 32 / args.steps,
                 "dense_equiv_tflops": round(dense_equiv, 2),
                 "dense_equiv_frac": round(dense_equiv / peak, 4),
-                "dense_formulation_flops_per_step": flops,
-                "sparse_intrinsic_macs_per_step": intrinsic,
+                "dense_formulation_flops_per_kernelization": flops,
+                "sparse_intrinsic_macs_per_kernelization": intrinsic,
                 "ncu_tensor_active_pct": prof.get("tensor_active_pct"),
                 "ncu_profile": prof.get("file"),
+                "tile_shape": R.cfg,
                 "sparsity": args.sparsity}
     else:
         sm_mhz = peaks.get("sm_max_mhz", 2070.0)
@@ -475,10 +533,10 @@ def run_ours(args, rank, world, dist):
         roof = {"bound": "alu", "achieved": round(dense_equiv, 2), "peak": round(peak, 1),
                 "unit": "TOP/s", "frac": round(dense_equiv / peak, 4), "traffic": None,
                 "kernel": "k_pop_contract", "peak_source": "derived: 16 POPC/clk/SM nominal",
-                "launches_per_step": 2 * rounds, "avg_launch_ms": round(per_launch, 4),
+                "launches_per_kernelization": launches, "avg_launch_ms": round(per_launch, 4),
                 "achieved_basis": "bit-MACs of the dense formulation x 2 (every 64 x 64 "
                                   "tile of the upper triangle is contracted)",
-                "sparse_intrinsic_macs_per_step": intrinsic,
+                "sparse_intrinsic_macs_per_kernelization": intrinsic,
                 "hbm": {"achieved": round(hbm, 2), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                         "frac": round(hbm / peaks["hbm_gbs"], 4),
                         "basis": "bit-packed operand bytes per pass, (m n + n m') / 8"}}
@@ -489,7 +547,7 @@ def run_ours(args, rank, world, dist):
         seq = cpu_sequential(insts, desc, args.cpu_seconds) if variant_name(args) == "DP+MD" \
             else None
 
-    # Kernels of one step.  Load: k_validate, k_init, k_vertex_degrees,
+    # Kernels of one kernelization.  Load: k_validate, k_init, k_vertex_degrees,
     # k_vertex_layout, k_layout_keys, k_layout_scan, k_layout_place,
     # k_edge_rows (a batch adds k_gather_bounds and k_localize_ptr), then the
     # result-mask kernel.  Per round: k_plan, the A set scatter, [k_tile_list],
@@ -507,59 +565,121 @@ def run_ours(args, rank, world, dist):
         "data": DATA,
         "config": {"workload": desc, "contraction": args.contraction, "rounds": rounds,
                    "sparsity": args.sparsity, "rules": variant_name(args),
-                   "instances_per_step": D.count,
+                   "instances_per_step": units_per_step,
+                   "kernelizations_per_step": reps,
                    "l2": "inputs larger than L2: dense operands "
                          f"{sum(i.m * i.n for i in insts) / 1e9:.2f} GB per product",
                    "parallelism": f"{world} GPU(s), independent instances per GPU"},
-        "pair_tests_per_s": round(world * pairs * args.steps / (ms / 1e3), 1),
+        "pair_tests_per_s": round(world * pairs * reps * args.steps / (ms / 1e3), 1),
         "roofline": roof,
         "cpu_baseline": cpu,
         "cpu_sequential": seq,
         "e2e": e2e,
-        "gpu_launches": args.steps * (load_kernels + per_round * rounds),
+        "gpu_launches": args.steps * reps * (load_kernels + per_round * rounds),
         "clocks": clk,
     }
-    if loop is not None:
-        line["per_instance_loop"] = loop
+    if batch and not args.no_loop:
+        line["per_instance_loop"] = per_instance_loop(torch, mhs, stream, insts, args, D)
+    if args.workload == "all" and world == 1:
+        line["configs"] = sub_records(torch, mhs, stream, args, peaks, kind)
     return line
 
 
-def run_stream(args, rank, world):
-    """Serving: Poisson arrivals of stream-shaped requests through the
-    continuous-batching server, against the plain one-instance-at-a-time form
-    (mhs_load + mhs_kernelize + mhs_result) on the same GPU."""
-    import torch
-    from paper_2109_06042_gb300 import build as B
-    B.build()
-    from paper_2109_06042_gb300 import instances as I
-    from paper_2109_06042_gb300 import mhs
-    mhs.set_default_variant(args.rule, args.full_edges)
-    rng = np.random.Generator(np.random.PCG64(777 + rank))
-    pool = [I.config_stream_one(50_000 + rank * 100_000 + i) for i in range(args.pool)]
-    order = rng.integers(0, len(pool), size=args.requests)
-    reqs = [pool[i] for i in order]
-    desc = (f"stream of {args.requests} requests per rate from {len(pool)} seeded instances "
-            f"(n log-uniform [100,20000], m~U[n,3n], |e|~U[2,16], f<=3)")
-    # plain form: service time of every request, back to back
-    for i in reqs[:3]:
-        mhs.kernelize(i, contraction=args.contraction)
+def per_instance_loop(torch, mhs, stream, insts, args, D):
+    """The plain one-instance-per-call form of a batch on the same GPU."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    singles = []
+    for i in insts:
+        singles.append((i, torch.from_numpy(i.edge_ptr.astype(np.int32)).to(dev),
+                        torch.from_numpy(i.edge_vtx if i.nnz else np.zeros(1, np.int32)).to(dev),
+                        torch.from_numpy(i.demand if i.m else np.zeros(1, np.int32)).to(dev)))
+    for i, p_, v_, d_ in singles[:8]:
+        hh = mhs.Instance.load_device(i.n, i.m, p_, v_, d_, i.k, contraction=args.contraction,
+                                      stream=stream)
+        hh.kernelize()
+        hh.free()
     torch.cuda.synchronize()
-    svc = np.zeros(len(reqs))
-    for j, i in enumerate(reqs):
-        t0 = time.perf_counter()
-        mhs.kernelize(i, contraction=args.contraction)
-        svc[j] = time.perf_counter() - t0
-    plain_rate = len(reqs) / svc.sum()
+    t0 = time.perf_counter()
+    for i, p_, v_, d_ in singles:
+        hh = mhs.Instance.load_device(i.n, i.m, p_, v_, d_, i.k, contraction=args.contraction,
+                                      stream=stream)
+        hh.kernelize()
+        hh.result_device(D.av, D.ae)
+        hh.free()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    return {"value": round(len(insts) / dt, 2), "unit": UNIT,
+            "form": "mhs_load_device + mhs_kernelize + mhs_result_device per instance"}
+
+
+def sub_records(torch, mhs, stream, args, peaks, kind):
+    """The other workloads on the same GPU (N = 1): instances/s with inputs in
+    HBM (CUDA events), the contraction's issued tensor fraction, the tile
+    shape; the batch with autotuned and fixed shapes and its one-instance
+    loop; a short serving sweep."""
+    out = {}
+    steps, warmup = args.sub_steps, 3
+    for wl in ("uniform", "interval", "batch"):
+        insts, desc = make_instances(args, 0, wl)
+        reps = REPS[wl]
+        R = Runner(torch, mhs, stream, insts, args, reps=reps)
+        traces, rounds = R.traces()
+        flops, pairs, _ = algorithmic_work(traces)
+        ms, cms, kb = R.timed(steps, warmup)
+        rec = {"workload": desc, "rounds": rounds,
+               "value": round(len(insts) * reps * steps / (ms / 1e3), 3), "unit": UNIT,
+               "ms_per_kernelization": round(ms / steps / reps, 4),
+               "pair_tests_per_s": round(pairs * reps * steps / (ms / 1e3), 1),
+               "tile_shape": R.cfg}
+        rec.update(contraction_roofline(args, peaks, kind, flops, cms, kb, steps))
+        if wl == "batch":
+            F = Runner(torch, mhs, stream, insts, args, tiles=DEFAULT_TILES, reps=1)
+            ms_f, _, _ = F.timed(steps, warmup)
+            rec["fixed_shape"] = {"tile_shape": DEFAULT_TILES,
+                                  "value": round(len(insts) * steps / (ms_f / 1e3), 3)}
+            if not args.no_loop:
+                rec["per_instance_loop"] = per_instance_loop(torch, mhs, stream, insts, args, R.D)
+            del F
+        out[wl] = rec
+        del R
+        torch.cuda.empty_cache()
+    out["stream"] = serve_sweep(mhs, torch, args, args.sub_requests, min(args.pool, 150),
+                                args.sub_rates, rank=0)
+    return out
+
+
+def serve_sweep(mhs, torch, args, requests, pool_size, rates, rank=0):
+    """Poisson arrivals of stream-shaped requests, at several rates, through
+    the continuous-batching server and through the plain one-at-a-time form
+    (mhs_load + mhs_kernelize + mhs_result per request, in arrival order),
+    both measured under the same arrival times on the same GPU."""
+    from paper_2109_06042_gb300 import instances as I
+    rng = np.random.Generator(np.random.PCG64(777 + rank))
+    pool = [I.config_stream_one(50_000 + rank * 100_000 + i) for i in range(pool_size)]
+    order = rng.integers(0, len(pool), size=requests)
+    reqs = [pool[i] for i in order]
+    contraction = args.contraction
+    for i in reqs[:3]:
+        mhs.kernelize(i, contraction=contraction)
+    torch.cuda.synchronize()
+    # the plain form back to back: its saturating rate
+    t0 = time.perf_counter()
+    for i in reqs:
+        mhs.kernelize(i, contraction=contraction)
+    plain_rate = len(reqs) / (time.perf_counter() - t0)
+
+    def pace(arrivals, t0, a):
+        now = time.perf_counter() - t0
+        if a > now:
+            time.sleep(a - now)
 
     def serve(arrivals):
-        """Submit at the given arrival offsets (s); returns (latencies s, makespan s)."""
-        with mhs.Server(contraction=args.contraction) as srv:
+        """Server: (latencies s, makespan s)."""
+        with mhs.Server(contraction=contraction) as srv:
             t0 = time.perf_counter()
             tickets = []
             for a, inst in zip(arrivals, reqs):
-                now = time.perf_counter() - t0
-                if a > now:
-                    time.sleep(a - now)
+                pace(arrivals, t0, a)
                 tickets.append(srv.submit(inst))
             lat = []
             for t in tickets:
@@ -568,52 +688,65 @@ def run_stream(args, rank, world):
             makespan = time.perf_counter() - t0
         return np.array(lat), makespan
 
-    # saturating rate: everything at once (closed loop)
+    def plain(arrivals):
+        """One request at a time, in arrival order, each started at its
+        arrival or when the previous one finished: (latencies s, makespan s)."""
+        t0 = time.perf_counter()
+        lat = []
+        for a, inst in zip(arrivals, reqs):
+            pace(arrivals, t0, a)
+            mhs.kernelize(inst, contraction=contraction)
+            lat.append(time.perf_counter() - t0 - a)
+        return np.array(lat), time.perf_counter() - t0
+
     serve(np.zeros(min(len(reqs), 64)))  # warm-up
-    lat0, mk0 = serve(np.zeros(len(reqs)))
+    lat0, mk0 = serve(np.zeros(len(reqs)))  # everything at once: the saturating rate
     sat = len(reqs) / mk0
+    pct = lambda x, q: round(1e3 * float(np.percentile(x, q)), 3)
     sweep = []
-    for mult in [float(x) for x in args.rates.split(",")]:
+    for mult in [float(x) for x in rates.split(",")]:
         rate = mult * sat
         arr = np.cumsum(rng.exponential(1.0 / rate, size=len(reqs)))
         lat, mk = serve(arr)
-        # plain form under the same arrivals: single FIFO server with the measured times
-        fin = np.zeros(len(reqs))
-        t = 0.0
-        for j in range(len(reqs)):
-            t = max(t, arr[j]) + svc[j]
-            fin[j] = t
-        plat = fin - arr
+        plat, pmk = plain(arr)
         sweep.append({
             "rate_per_s": round(rate, 2), "x_saturating": mult,
-            "served": {"p50_ms": round(1e3 * float(np.percentile(lat, 50)), 3),
-                       "p99_ms": round(1e3 * float(np.percentile(lat, 99)), 3),
+            "served": {"p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99),
                        "instances_per_s": round(len(reqs) / mk, 2)},
-            "plain": {"p50_ms": round(1e3 * float(np.percentile(plat, 50)), 3),
-                      "p99_ms": round(1e3 * float(np.percentile(plat, 99)), 3),
-                      "instances_per_s": round(len(reqs) / fin[-1], 2)},
+            "plain": {"p50_ms": pct(plat, 50), "p99_ms": pct(plat, 99),
+                      "instances_per_s": round(len(reqs) / pmk, 2)},
         })
-    best = max(sweep, key=lambda r: r["served"]["instances_per_s"])
+    return {"workload": f"{requests} requests per rate from {len(pool)} seeded instances "
+                        "(n log-uniform [100,20000], m~U[n,3n], |e|~U[2,16], f<=3), "
+                        "Poisson arrivals",
+            "closed_loop_rate_per_s": round(sat, 2),
+            "closed_loop_p50_ms": pct(lat0, 50), "closed_loop_p99_ms": pct(lat0, 99),
+            "plain_rate_per_s": round(plain_rate, 2),
+            "speedup_vs_plain": round(sat / plain_rate, 3),
+            "server": "max_slots 256, budget 3/4 of free HBM",
+            "plain_form": "mhs_load + mhs_kernelize + mhs_result per request, measured "
+                          "under the same arrival times",
+            "sweep": sweep}
+
+
+def run_stream(args, rank, world):
+    """Serving: the sweep of serve_sweep at --requests per rate."""
+    import torch
+    from paper_2109_06042_gb300 import build as B
+    B.build()
+    from paper_2109_06042_gb300 import mhs
+    mhs.set_default_variant(args.rule, args.full_edges)
+    sv = serve_sweep(mhs, torch, args, args.requests, args.pool, args.rates, rank)
+    best = max(sv["sweep"], key=lambda r: r["served"]["instances_per_s"])
     return {
         "metric": "served instances/s (continuous batching) with p50/p99 latency",
         "value": best["served"]["instances_per_s"], "unit": UNIT, "n_gpus": world,
-        "steps": len(sweep),
-        "warmup": 1, "ms_per_step": round(1e3 * mk0, 3), "higher_is_better": True,
+        "steps": len(sv["sweep"]), "warmup": 1, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "e4m3" if args.contraction == "fp8" else "u32-popcount", "data": DATA,
-        "config": {"workload": desc, "contraction": args.contraction,
-                   "server": "max_slots 256, budget 3/4 of free HBM"},
-        "serving": {"at_value": {"offered_rate_per_s": best["rate_per_s"],
-                                 "served_p50_ms": best["served"]["p50_ms"],
-                                 "served_p99_ms": best["served"]["p99_ms"],
-                                 "plain_instances_per_s": best["plain"]["instances_per_s"],
-                                 "plain_p99_ms": best["plain"]["p99_ms"]},
-                    "closed_loop_rate_per_s": round(sat, 2),
-                    "plain_rate_per_s": round(plain_rate, 2),
-                    "speedup_vs_plain": round(best["served"]["instances_per_s"] / plain_rate, 3),
-                    "closed_loop_p50_ms": round(1e3 * float(np.percentile(lat0, 50)), 3),
-                    "closed_loop_p99_ms": round(1e3 * float(np.percentile(lat0, 99)), 3),
-                    "sweep": sweep},
+        "config": {"workload": sv["workload"], "contraction": args.contraction,
+                   "server": sv["server"]},
+        "serving": sv,
     }
 
 
@@ -637,7 +770,8 @@ def kernel_profile(args):
     dram__bytes_write.sum, averaged over one kernelization's launches) and
     the tensor pipe's active share; empty when the workload or options
     differ or the kernel sources changed since the capture."""
-    default = (args.workload == "powerlaw" and args.seed == 0 and args.sparsity == "skip" and
+    default = (headline_workload(args) == "powerlaw" and args.seed == 0 and
+               args.sparsity == "skip" and
                args.rule == "dp" and not args.full_edges and args.contraction == "fp8")
     if not default or not os.path.exists(PROFILE):
         return {}

@@ -420,3 +420,64 @@ def test_timing_mode(mhs, graphs, mode):
         _same(h.result(), O.reduce(inst), f"graphs={graphs}")
     assert t["dp_ms"] > 0 and t["md_ms"] > 0 and t["other_ms"] >= 0
     assert t["total_ms"] >= t["dp_ms"] + t["md_ms"] - 1e-3
+
+
+def _oracle_alive(seed):
+    """Worker: the oracle's result of batch instance `seed` as alive masks
+    over its input ids, with k and the round count."""
+    from oracle import oracle as O2
+    from paper_2109_06042_gb300 import instances as I2
+    inst = I2.config_batch_one(seed)
+    r = O2.reduce(inst)
+    av = np.zeros(inst.n, np.uint8)
+    ae = np.zeros(inst.m, np.uint8)
+    av[r["vertices"]] = 1
+    ae[r["edges"]] = 1
+    return av, ae, r["rounds"]
+
+
+def test_full_batch_4096_every_instance(mhs):
+    """The whole 4,096-instance batch the benchmark times (seeds 4000..4095),
+    loaded the same way (device CSR arrays, one batch), reduced in one
+    fixpoint launch; every instance's surviving vertex and hyperedge sets and
+    round count equal the oracle's.  The oracle runs in a pool of spawned
+    processes."""
+    import multiprocessing as mp
+    import os
+    import torch
+    count, seed0 = 4096, 4000
+    insts = I.config_batch(count, seed0)
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        ref_async = pool.map_async(_oracle_alive, [seed0 + b for b in range(count)], chunksize=16)
+        dev = torch.device("cuda", 0)
+        n = np.array([i.n for i in insts], np.int32)
+        m = np.array([i.m for i in insts], np.int32)
+        k = np.array([i.k for i in insts], np.int64)
+        nnz = np.array([i.nnz for i in insts], np.int64)
+        base = np.concatenate([[0], np.cumsum(nnz)])
+        ptr = np.zeros(int(m.sum()) + 1, np.int64)
+        e0 = 0
+        for b, i in enumerate(insts):
+            ptr[e0:e0 + i.m + 1] = i.edge_ptr.astype(np.int64) + base[b]
+            e0 += i.m
+        vtx = np.concatenate([i.edge_vtx for i in insts] + [np.zeros(1, np.int32)])
+        dem = np.concatenate([i.demand for i in insts] + [np.zeros(1, np.int32)])
+        av = torch.zeros(int(n.sum()) + 1, dtype=torch.uint8, device=dev)
+        ae = torch.zeros(int(m.sum()) + 1, dtype=torch.uint8, device=dev)
+        with mhs.Instance.load_batch_device(n, m, k, torch.from_numpy(ptr).to(dev),
+                                            torch.from_numpy(vtx).to(dev),
+                                            torch.from_numpy(dem).to(dev),
+                                            contraction="fp8") as h:
+            h.kernelize()
+            h.result_batch_device(av, ae)
+            torch.cuda.synchronize()
+            rounds = [h.trace(b)[1] for b in range(count)]
+        av = av.cpu().numpy()
+        ae = ae.cpu().numpy()
+        refs = ref_async.get(timeout=1800)
+    vb = np.concatenate([[0], np.cumsum(n)])
+    eb = np.concatenate([[0], np.cumsum(m)])
+    for b, (rav, rae, rr) in enumerate(refs):
+        assert np.array_equal(av[vb[b]:vb[b + 1]], rav), f"instance {b}: vertices"
+        assert np.array_equal(ae[eb[b]:eb[b + 1]], rae), f"instance {b}: hyperedges"
+        assert rounds[b] == rr, f"instance {b}: rounds {rounds[b]} != {rr}"
