@@ -549,13 +549,14 @@ def run_ours(args, rank, world, dist):
 
     # Kernels of one kernelization.  Load: k_validate, k_init, k_vertex_degrees,
     # k_vertex_layout, k_layout_keys, k_layout_scan, k_layout_place,
-    # k_edge_rows (a batch adds k_gather_bounds and k_localize_ptr), then the
+    # k_layout_rank, k_layout_commit, k_edge_rows (a batch adds
+    # k_gather_bounds and k_localize_ptr), then the
     # result-mask kernel.  Per round: k_plan, the A set scatter, [k_tile_list],
     # the DP contraction, k_compact_edges, k_plan, the fused A clear / A^T set
     # scatter, [k_tile_list], the MD contraction, the A^T clear scatter,
     # k_compact_vertices and the loop-condition kernel ([] tcgen05 only), plus
     # the three FE kernels with --full-edges.
-    load_kernels = 9 + (2 if batch else 0)
+    load_kernels = 11 + (2 if batch else 0)
     per_round = (12 if args.contraction == "fp8" else 10) + (3 if args.full_edges else 0)
     line = {
         "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,

@@ -130,6 +130,7 @@ typedef struct {
     int32_t changed;    /* 1 if the last executed round deleted something */
     int32_t dp_deleted; /* hyperedges deleted by the last round's DP pass */
     int32_t md_deleted; /* vertices deleted by the last round's MD pass */
+    int32_t active;     /* instances not yet at their fixpoint (0: nothing more to do) */
 } mhs_round_stats;
 
 typedef struct mhs_instance mhs_instance;
@@ -210,6 +211,44 @@ mhs_status mhs_reduce_round(mhs_instance *inst, mhs_round_stats *stats);
 
 /* Algorithm 3 to the fixpoint (or opt.max_rounds rounds).  stats may be NULL. */
 mhs_status mhs_kernelize(mhs_instance *inst, mhs_round_stats *stats);
+
+/*
+ * Sharded rounds: one pass of Algorithm 3 split over several replicas of
+ * one instance (Section 4.1 computes every pair of a pass independently,
+ * so the pairs can be split; the only exchange is the pass's output).
+ * Every replica loads the same instance (count 1, same options) and runs,
+ * per round and per phase (0: the DP or SE pass, 1: the MD pass):
+ *   mhs_pass_begin      plan and encode (identical on every replica);
+ *   mhs_pass_contract   its share `shard` of `nshards`: the tile rows of
+ *                       the 128-row blocks b with b % nshards == shard
+ *                       (may be called for several shares in a row);
+ *   mhs_pass_partial    copies this replica's partial result to a DEVICE
+ *                       buffer indexed by INPUT id (replicas may lay rows
+ *                       out differently): phase 0 the deletion flags
+ *                       uint8[m] (1 = superseded, 0 for ids no longer
+ *                       alive), phase 1 the dominator counts int32[n] of
+ *                       the input's m hyperedges / n vertices
+ *                       (*elems_out = m or n);
+ *   (the caller combines the replicas' buffers: element-wise maximum of
+ *    the flags, sum of the counts -- e.g. one all-reduce each)
+ *   mhs_pass_merge      copies the combined buffer back (DEVICE);
+ *   mhs_pass_end        the decision and order-preserving compaction
+ *                       (identical on every replica); after phase 1 also
+ *                       rule FE if enabled, and *stats (may be NULL) as for
+ *                       mhs_reduce_round.
+ * mhs_pass_partial and mhs_pass_merge run on the instance's stream and
+ * return when their copy is done; a buffer written by other streams must
+ * be complete before it is passed in.
+ * Passes must come in this order; mhs_kernelize / mhs_reduce_round are
+ * refused while a sharded round is in progress.  A replica that runs every
+ * share itself needs no partial/merge.  Results equal mhs_kernelize's.
+ */
+mhs_status mhs_pass_begin(mhs_instance *inst, int32_t phase);
+mhs_status mhs_pass_contract(mhs_instance *inst, int32_t phase, int32_t shard, int32_t nshards);
+mhs_status mhs_pass_partial(const mhs_instance *inst, int32_t phase, void *dev_out,
+                            int64_t *elems_out);
+mhs_status mhs_pass_merge(mhs_instance *inst, int32_t phase, const void *dev_in);
+mhs_status mhs_pass_end(mhs_instance *inst, int32_t phase, mhs_round_stats *stats);
 
 /*
  * Copy the current result of instance `index` to HOST buffers (any may be

@@ -327,7 +327,7 @@ __device__ __forceinline__ int32_t kit_next(KIter &k) {
 // f > |e|, and in MD a zero count only adds dominators of a vertex in no
 // hyperedge, which is deleted anyway (its maximum demand is 0).
 // Warp-aggregated appends keep runs of 32 consecutive tiles together.
-__global__ void k_tile_list(InstState *st, Plan *plan, int phase) {
+__global__ void k_tile_list(InstState *st, Plan *plan, int phase, int shard, int nshards) {
     const int lane = threadIdx.x & 31;
     const int64_t total = plan->total_tiles;
     const int32_t G = plan->group_rows > 0 ? plan->group_rows : kGroupRows;
@@ -352,7 +352,9 @@ __global__ void k_tile_list(InstState *st, Plan *plan, int phase) {
             ti.nk = ((K > 0 ? K : 1) + kTcK - 1) / kTcK;
             tc_tile_coords(t - plan->tile_off[lo], ti.R, G, r, &ti.bi, &ti.bj);
             bool has_k = true;
-            if (s.no_skip) {
+            if (nshards > 1 && ti.bi % nshards != shard) {
+                keep = false;  // another share's row block
+            } else if (s.no_skip) {
                 keep = true;  // the dense formulation: every tile, every round
             } else {
                 // only tiles that hold a candidate row (incremental rounds) ...
@@ -1203,8 +1205,9 @@ int32_t tile_group_rows() {
     return g;
 }
 
-cudaError_t launch_tc_tile_list(InstState *st, Plan *plan, int phase, int sms, cudaStream_t s) {
-    k_tile_list<<<sms * 4, 256, 0, s>>>(st, plan, phase);
+cudaError_t launch_tc_tile_list(InstState *st, Plan *plan, int phase, int sms, cudaStream_t s,
+                                int shard, int nshards) {
+    k_tile_list<<<sms * 4, 256, 0, s>>>(st, plan, phase, shard, nshards);
     return cudaGetLastError();
 }
 

@@ -290,8 +290,9 @@ __global__ void k_layout_scan(InstState *st, int count) {
 }
 
 // Sorted layout, step 3: place every hyperedge at the next slot of its
-// bucket (the order inside a bucket is arbitrary; results do not depend
-// on it, since ties compare original ids).
+// bucket, in arbitrary order (steps 4 and 5 sort each bucket by input id,
+// so that every load of an instance gets the same layout: sharded passes
+// split the tile rows of replicas that must agree on it).
 __global__ void k_layout_place(InstState *st, int count) {
     const int b = blockIdx.y;
     if (b >= count) return;
@@ -303,6 +304,37 @@ __global__ void k_layout_place(InstState *st, int count) {
         s.e_c2o[pos] = (int32_t)e;
         s.e_o2c[e] = pos;
     }
+}
+
+// Sorted layout, step 4: each hyperedge's final position is its bucket's
+// start plus the number of hyperedges of the bucket with a smaller input id
+// (after step 3, v_deg[key] is the bucket's end and v_cnt[key] its size).
+// The cost is the sum of the squared bucket sizes; buckets hold the
+// hyperedges sharing their smallest vertex (id or position).
+__global__ void k_layout_rank(InstState *st, int count) {
+    const int b = blockIdx.y;
+    if (b >= count) return;
+    InstState &s = st[b];
+    if (!s.layout_sorted || s.status) return;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < s.m0;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t key = s.e_s[e];
+        const int32_t hi = s.v_deg[key], lo = hi - s.v_cnt[key];
+        int32_t rank = 0;
+        for (int32_t p = lo; p < hi; ++p) rank += s.e_c2o[p] < (int32_t)e;
+        s.e_o2c[e] = lo + rank;
+    }
+}
+
+// Sorted layout, step 5: the position -> id map from the final positions.
+__global__ void k_layout_commit(InstState *st, int count) {
+    const int b = blockIdx.y;
+    if (b >= count) return;
+    InstState &s = st[b];
+    if (!s.layout_sorted || s.status) return;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < s.m0;
+         e += (int64_t)gridDim.x * blockDim.x)
+        s.e_c2o[s.e_o2c[e]] = (int32_t)e;
 }
 
 // Hyperedge rows of round 1, by position.
@@ -785,7 +817,10 @@ __device__ __forceinline__ void tri_tile(int64_t t, int32_t nt, int32_t *ti, int
 constexpr int kPopKW = 32;  // K words staged per step
 
 // phase 0: DP on Ab (rows = hyperedges); phase 1: MD on Atb (rows = vertices).
-__global__ void __launch_bounds__(256) k_pop_contract(InstState *st, const Plan *plan, int phase) {
+// With nshards > 1 only the tiles whose rows lie in a 128-row block b with
+// b % nshards == shard are contracted (one share of a sharded pass).
+__global__ void __launch_bounds__(256) k_pop_contract(InstState *st, const Plan *plan, int phase,
+                                                      int shard, int nshards) {
     __shared__ uint32_t As[kPopTile][kPopKW + 1];
     __shared__ uint32_t Bs[kPopTile][kPopKW + 1];
     __shared__ int32_t rcnt[kPopTile], ccnt[kPopTile];
@@ -803,6 +838,7 @@ __global__ void __launch_bounds__(256) k_pop_contract(InstState *st, const Plan 
         int32_t ti, tj;
         tri_tile(local, nt, &ti, &tj);
         const int32_t i0 = ti * kPopTile, j0 = tj * kPopTile;
+        if (nshards > 1 && (i0 / kTcM) % nshards != shard) continue;  // another share's tile
         {  // incremental rounds: only tiles that hold a candidate row or column
             const uint8_t *drb = phase == 0 ? s.e_dirty_rb : s.v_dirty_rb;
             if (drb && !(phase == 1 && s.md_full) && !drb[i0 >> 7] && !drb[j0 >> 7]) continue;
@@ -983,6 +1019,8 @@ cudaError_t launch_build(InstState *st, int count, int32_t max_rounds, int64_t m
     k_layout_keys<<<dim3(gx, count), 256, 0, s>>>(st, count);
     k_layout_scan<<<count, 1024, 0, s>>>(st, count);
     k_layout_place<<<dim3(gx, count), 256, 0, s>>>(st, count);
+    k_layout_rank<<<dim3(gx, count), 256, 0, s>>>(st, count);
+    k_layout_commit<<<dim3(gx, count), 256, 0, s>>>(st, count);
     k_edge_rows<<<dim3(gx, count), 256, 0, s>>>(st, count);
     return cudaGetLastError();
 }
@@ -999,18 +1037,89 @@ static void launch_scatter(InstState *st, const Plan *plan, bool set, bool dense
     }
 }
 
+cudaError_t launch_phase_prologue(InstState *st, Plan *plan, BatchCounters *ctr, int phase,
+                                  int contraction, int sms, cudaStream_t s) {
+    const bool tc = contraction == kFp8;
+    k_plan<<<1, 1024, 0, s>>>(st, plan, phase, tc ? 1 : 0, ctr);
+    const int grid = grid_for(sms, 8);
+    if (phase == 0) launch_scatter<0>(st, plan, true, tc, grid, s);
+    else launch_scatter<1>(st, plan, true, tc, grid, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_phase_contract(InstState *st, Plan *plan, BatchCounters *ctr, int phase,
+                                  int contraction, int sms, int32_t *kerr, cudaStream_t s,
+                                  int tile_n, int shard, int nshards) {
+    const bool tc = contraction == kFp8;
+    if (tc) {
+        // each share builds its own list and hands it out from its start
+        cudaError_t e = cudaMemsetAsync(&plan->list_count, 0, sizeof(int32_t), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(&plan->list_next, 0, sizeof(int32_t), s);
+        if (e == cudaSuccess) e = launch_tc_tile_list(st, plan, phase, sms, s, shard, nshards);
+        if (e != cudaSuccess) return e;
+        return launch_tc_contract(st, plan, ctr, phase, sms, tile_n, kerr, s);
+    }
+    k_pop_contract<<<grid_for(sms, 6), 256, 0, s>>>(st, plan, phase, shard, nshards);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_phase_epilogue(InstState *st, Plan *plan, BatchCounters *ctr, int count,
+                                  int phase, int contraction, int sms, cudaStream_t s,
+                                  int32_t *done_list, int compact_blocks) {
+    const bool tc = contraction == kFp8;
+    const int grid = grid_for(sms, 8);
+    // (the DP pass's clear of A runs inside the MD set pass, which walks the
+    // same incidences)
+    if (phase == 1) launch_scatter<1>(st, plan, false, tc, grid, s);
+    // compact_blocks > 1: a single instance, one block per chunk of 1024 ids
+    const dim3 cgrid(compact_blocks > 1 ? compact_blocks : 1, count);
+    if (phase == 0) k_compact_edges<<<cgrid, 1024, 0, s>>>(st, count);
+    else k_compact_vertices<<<cgrid, 1024, 0, s>>>(st, count, ctr, done_list);
+    return cudaGetLastError();
+}
+
+// A sharded pass's partial output over INPUT ids (the replicas' layouts may
+// order rows differently): phase 0 the DP/SE deletion flag of every
+// hyperedge (0 if not alive), phase 1 the dominator count of every vertex.
+// export: out[id] = value at the id's current position; import: the value at
+// each alive id's position = in[id].
+__global__ void k_pass_exchange(InstState *st, int phase, int import, void *buf) {
+    InstState &s = st[0];
+    const int32_t ids = phase == 0 ? s.m0 : s.n0;
+    const int32_t rows = phase == 0 ? s.m : s.n;  // this pass's rows
+    const int32_t *o2c = phase == 0 ? s.e_o2c : s.v_o2c;
+    for (int32_t id = blockIdx.x * blockDim.x + threadIdx.x; id < ids;
+         id += gridDim.x * blockDim.x) {
+        const int32_t pos = o2c[id];
+        const bool alive = pos >= 0 && pos < rows;
+        if (phase == 0) {
+            uint8_t *b = static_cast<uint8_t *>(buf);
+            if (!import) b[id] = alive ? s.e_del[pos] : 0;
+            else if (alive) s.e_del[pos] = b[id] ? 1 : 0;
+        } else {
+            int32_t *b = static_cast<int32_t *>(buf);
+            if (!import) b[id] = alive ? s.v_cnt[pos] : 0;
+            else if (alive) s.v_cnt[pos] = b[id];
+        }
+    }
+}
+
+cudaError_t launch_pass_exchange(InstState *st, int phase, int import, void *buf, int sms,
+                                 cudaStream_t s) {
+    k_pass_exchange<<<grid_for(sms, 2), 256, 0, s>>>(st, phase, import, buf);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_round_phase(InstState *st, Plan *plan, BatchCounters *ctr, int count,
                                int phase, int contraction, int sms, int32_t *kerr,
                                cudaStream_t s, cudaEvent_t ev_contract_begin,
                                cudaEvent_t ev_contract_end, int32_t *done_list,
                                int compact_blocks, int tile_n) {
     const bool tc = contraction == kFp8;
-    k_plan<<<1, 1024, 0, s>>>(st, plan, phase, tc ? 1 : 0, ctr);
-    const int grid = grid_for(sms, 8);
-    if (phase == 0) launch_scatter<0>(st, plan, true, tc, grid, s);
-    else launch_scatter<1>(st, plan, true, tc, grid, s);
+    cudaError_t e0 = launch_phase_prologue(st, plan, ctr, phase, contraction, sms, s);
+    if (e0 != cudaSuccess) return e0;
     if (tc) {
-        cudaError_t e = launch_tc_tile_list(st, plan, phase, sms, s);
+        cudaError_t e = launch_tc_tile_list(st, plan, phase, sms, s, 0, 1);
         if (e != cudaSuccess) return e;
     }
     // Timing events: external event nodes when the round is being captured
@@ -1027,17 +1136,11 @@ cudaError_t launch_round_phase(InstState *st, Plan *plan, BatchCounters *ctr, in
         cudaError_t e = launch_tc_contract(st, plan, ctr, phase, sms, tile_n, kerr, s);
         if (e != cudaSuccess) return e;
     } else {
-        k_pop_contract<<<grid_for(sms, 6), 256, 0, s>>>(st, plan, phase);
+        k_pop_contract<<<grid_for(sms, 6), 256, 0, s>>>(st, plan, phase, 0, 1);
     }
     if (ev_contract_end) record(ev_contract_end);
-    // (the DP pass's clear of A runs inside the MD set pass, which walks the
-    // same incidences)
-    if (phase == 1) launch_scatter<1>(st, plan, false, tc, grid, s);
-    // compact_blocks > 1: a single instance, one block per chunk of 1024 ids
-    const dim3 cgrid(compact_blocks > 1 ? compact_blocks : 1, count);
-    if (phase == 0) k_compact_edges<<<cgrid, 1024, 0, s>>>(st, count);
-    else k_compact_vertices<<<cgrid, 1024, 0, s>>>(st, count, ctr, done_list);
-    return cudaGetLastError();
+    return launch_phase_epilogue(st, plan, ctr, count, phase, contraction, sms, s, done_list,
+                                 compact_blocks);
 }
 
 cudaError_t launch_alive_masks(const InstState *st, uint8_t *alive_v, uint8_t *alive_e,

@@ -42,6 +42,23 @@ cudaError_t launch_round_phase(InstState *st, Plan *plan, BatchCounters *ctr, in
                                cudaStream_t s, cudaEvent_t ev_contract_begin,
                                cudaEvent_t ev_contract_end, int32_t *done_list = nullptr,
                                int compact_blocks = 1, int tile_n = kTcNDefault);
+// The three parts of launch_round_phase, for a pass split into shares
+// (mhs_pass_*): plan and set scatter; the contraction of share `shard` of
+// `nshards` (the tile rows of 128-row blocks b with b % nshards == shard);
+// the clear scatter (MD) and the compaction.
+cudaError_t launch_phase_prologue(InstState *st, Plan *plan, BatchCounters *ctr, int phase,
+                                  int contraction, int sms, cudaStream_t s);
+cudaError_t launch_phase_contract(InstState *st, Plan *plan, BatchCounters *ctr, int phase,
+                                  int contraction, int sms, int32_t *kerr, cudaStream_t s,
+                                  int tile_n, int shard, int nshards);
+cudaError_t launch_phase_epilogue(InstState *st, Plan *plan, BatchCounters *ctr, int count,
+                                  int phase, int contraction, int sms, cudaStream_t s,
+                                  int32_t *done_list, int compact_blocks);
+// Copy a single instance's partial pass output to (import = 0) or from
+// (import = 1) a buffer indexed by input id: uint8[m0] deletion flags
+// (phase 0) or int32[n0] dominator counts (phase 1).
+cudaError_t launch_pass_exchange(InstState *st, int phase, int import, void *buf, int sms,
+                                 cudaStream_t s);
 // End of one round of the device-side fixpoint loop: keep looping while
 // some instance is active, no error was raised and fewer than round_cap
 // rounds ran (hitting the cap raises kErrRoundCap).
@@ -62,7 +79,9 @@ cudaError_t launch_tc_contract(InstState *st, Plan *plan, BatchCounters *ctr, in
                                int tile_n, int32_t *kerr, cudaStream_t s);
 // The tiles of phase `phase` that hold nonzero counts (or, in a DP pass of
 // an instance with a hyperedge f > |e|, all tiles), into plan->tile_list.
-cudaError_t launch_tc_tile_list(InstState *st, Plan *plan, int phase, int sms, cudaStream_t s);
+// With nshards > 1 only the tiles of row blocks b with b % nshards == shard.
+cudaError_t launch_tc_tile_list(InstState *st, Plan *plan, int phase, int sms, cudaStream_t s,
+                                int shard = 0, int nshards = 1);
 cudaError_t prepare_tc_contract();  // once per process, before any capture
 // Row blocks per L2 group of the tile order (environment MHS_TILE_GROUP_ROWS,
 // default 16); stored in Plan::group_rows.

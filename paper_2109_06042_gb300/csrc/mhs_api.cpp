@@ -232,6 +232,9 @@ struct mhs_instance {
     cudaEvent_t ev[6] = {};
     float last_ms[4] = {0, 0, 0, 0};
     int32_t rounds_done = 0;
+    // sharded passes (mhs_pass_*): 0 between rounds, 1 DP pass open,
+    // 2 DP pass ended, 3 MD pass open
+    int32_t pass_state = 0;
 };
 
 namespace {
@@ -729,6 +732,8 @@ mhs_status build_loop_graph(mhs_instance *h) {
 }
 
 mhs_status run_rounds(mhs_instance *h, int32_t limit, mhs_round_stats *stats) {
+    if (h->pass_state != 0)
+        return fail(MHS_EINVAL, "a sharded round is in progress (finish it with mhs_pass_end)");
     if (limit <= 0 && h->opt.use_graphs && !h->timing) {
         if (!h->loop_graph) {
             mhs_status st = build_loop_graph(h);
@@ -747,6 +752,7 @@ mhs_status run_rounds(mhs_instance *h, int32_t limit, mhs_round_stats *stats) {
             stats->changed = h->hctr->changed_any;
             stats->dp_deleted = h->hctr->dp_deleted;
             stats->md_deleted = h->hctr->md_deleted;
+            stats->active = h->hctr->active;
         }
         return MHS_OK;
     }
@@ -792,6 +798,7 @@ mhs_status run_rounds(mhs_instance *h, int32_t limit, mhs_round_stats *stats) {
             stats->changed = h->hctr->changed_any;
             stats->dp_deleted = h->hctr->dp_deleted;
             stats->md_deleted = h->hctr->md_deleted;
+            stats->active = h->hctr->active;
         } else {
             std::memset(stats, 0, sizeof(*stats));
         }
@@ -1098,6 +1105,109 @@ mhs_status mhs_kernelize(mhs_instance *inst, mhs_round_stats *stats) {
     const mhs_status st = run_rounds(inst, 0, stats);
     if (st) inst->faulted = true;
     return st;
+}
+
+// ---- sharded passes ------------------------------------------------------
+
+namespace {
+mhs_status pass_check(const mhs_instance *h, int32_t phase, bool open) {
+    if (!h) return fail(MHS_EINVAL, "instance is NULL");
+    if (h->count != 1) return fail(MHS_EINVAL, "sharded passes take a single instance");
+    if (phase != 0 && phase != 1) return fail(MHS_EINVAL, "phase must be 0 (DP/SE) or 1 (MD)");
+    const int32_t want = open ? (phase == 0 ? 1 : 3) : (phase == 0 ? 0 : 2);
+    if (h->pass_state != want)
+        return fail(MHS_EINVAL,
+                    "passes run in order: begin(0), contract(0)..., end(0), begin(1), "
+                    "contract(1)..., end(1) (state %d, phase %d)",
+                    h->pass_state, phase);
+    return MHS_OK;
+}
+}  // namespace
+
+mhs_status mhs_pass_begin(mhs_instance *inst, int32_t phase) {
+    mhs_status st = pass_check(inst, phase, false);
+    if (st) return st;
+    if (inst->opt.full_edges && inst->opt.max_rounds)
+        return fail(MHS_EINVAL, "full_edges needs max_rounds = 0");
+    CUDA_TRY(launch_phase_prologue(inst->dstate, inst->dplan, inst->dctr, phase, inst->contraction,
+                                   inst->sms, inst->stream));
+    inst->pass_state = phase == 0 ? 1 : 3;
+    return MHS_OK;
+}
+
+mhs_status mhs_pass_contract(mhs_instance *inst, int32_t phase, int32_t shard, int32_t nshards) {
+    mhs_status st = pass_check(inst, phase, true);
+    if (st) return st;
+    if (nshards < 1 || nshards > 4096 || shard < 0 || shard >= nshards)
+        return fail(MHS_EINVAL, "need 1 <= nshards <= 4096 and 0 <= shard < nshards");
+    CUDA_TRY(launch_phase_contract(inst->dstate, inst->dplan, inst->dctr, phase,
+                                   inst->contraction, inst->sms, inst->dkerr, inst->stream,
+                                   inst->tiles.tile_n, shard, nshards));
+    return MHS_OK;
+}
+
+mhs_status mhs_pass_partial(const mhs_instance *inst, int32_t phase, void *dev_out,
+                            int64_t *elems_out) {
+    mhs_status st = pass_check(inst, phase, true);
+    if (st) return st;
+    const InstState &s = inst->hstate[0];
+    const int64_t elems = phase == 0 ? s.m0 : s.n0;
+    if (elems_out) *elems_out = elems;
+    if (dev_out && elems > 0) {
+        CUDA_TRY(launch_pass_exchange(inst->dstate, phase, 0, dev_out, inst->sms, inst->stream));
+        CUDA_TRY(cudaStreamSynchronize(inst->stream));
+    }
+    return MHS_OK;
+}
+
+mhs_status mhs_pass_merge(mhs_instance *inst, int32_t phase, const void *dev_in) {
+    mhs_status st = pass_check(inst, phase, true);
+    if (st) return st;
+    if (!dev_in) return fail(MHS_EINVAL, "dev_in is NULL");
+    const InstState &s = inst->hstate[0];
+    const int64_t elems = phase == 0 ? s.m0 : s.n0;
+    if (elems > 0) {
+        CUDA_TRY(launch_pass_exchange(inst->dstate, phase, 1, const_cast<void *>(dev_in),
+                                      inst->sms, inst->stream));
+        CUDA_TRY(cudaStreamSynchronize(inst->stream));
+    }
+    return MHS_OK;
+}
+
+mhs_status mhs_pass_end(mhs_instance *inst, int32_t phase, mhs_round_stats *stats) {
+    mhs_status st = pass_check(inst, phase, true);
+    if (st) return st;
+    cudaError_t e = launch_phase_epilogue(inst->dstate, inst->dplan, inst->dctr, 1, phase,
+                                          inst->contraction, inst->sms, inst->stream, nullptr,
+                                          inst->compact_blocks);
+    if (e == cudaSuccess && phase == 1 && inst->opt.full_edges)
+        e = launch_full_edges(inst->dstate, 1, inst->dctr, nullptr, inst->sms, inst->stream);
+    if (e != cudaSuccess) {
+        inst->faulted = true;
+        return fail(MHS_ECUDA, "pass end: %s", cudaGetErrorString(e));
+    }
+    inst->pass_state = phase == 0 ? 2 : 0;
+    if (phase == 0) {
+        if (stats) std::memset(stats, 0, sizeof(*stats));
+        return MHS_OK;
+    }
+    CUDA_TRY(cudaMemcpyAsync(inst->hctr, inst->dctr, sizeof(BatchCounters), cudaMemcpyDeviceToHost,
+                             inst->stream));
+    CUDA_TRY(cudaMemcpyAsync(inst->hkerr, inst->dkerr, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                             inst->stream));
+    CUDA_TRY(cudaStreamSynchronize(inst->stream));
+    st = check_device_status(inst);
+    if (st) return st;
+    if (stats) {
+        stats->n_alive = inst->hctr->n_alive;
+        stats->m_alive = inst->hctr->m_alive;
+        stats->rounds = inst->hctr->max_rounds_seen;
+        stats->changed = inst->hctr->changed_any;
+        stats->dp_deleted = inst->hctr->dp_deleted;
+        stats->md_deleted = inst->hctr->md_deleted;
+        stats->active = inst->hctr->active;
+    }
+    return MHS_OK;
 }
 
 mhs_status mhs_result_at(const mhs_instance *inst, int32_t index, int32_t *vtx_out,

@@ -49,7 +49,8 @@ class Options(ctypes.Structure):
 class RoundStats(ctypes.Structure):
     _fields_ = [("n_alive", ctypes.c_int32), ("m_alive", ctypes.c_int32),
                 ("rounds", ctypes.c_int32), ("changed", ctypes.c_int32),
-                ("dp_deleted", ctypes.c_int32), ("md_deleted", ctypes.c_int32)]
+                ("dp_deleted", ctypes.c_int32), ("md_deleted", ctypes.c_int32),
+                ("active", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: int(getattr(self, f)) for f, _ in self._fields_}
@@ -94,6 +95,11 @@ _SIGS = {
     "mhs_count": (_i32, [_vp]),
     "mhs_reduce_round": (_i32, [_vp, ctypes.POINTER(RoundStats)]),
     "mhs_kernelize": (_i32, [_vp, ctypes.POINTER(RoundStats)]),
+    "mhs_pass_begin": (_i32, [_vp, _i32]),
+    "mhs_pass_contract": (_i32, [_vp, _i32, _i32, _i32]),
+    "mhs_pass_partial": (_i32, [_vp, _i32, _vp, _P64]),
+    "mhs_pass_merge": (_i32, [_vp, _i32, _vp]),
+    "mhs_pass_end": (_i32, [_vp, _i32, ctypes.POINTER(RoundStats)]),
     "mhs_result_at": (_i32, [_vp, _i32, _P32, _i32, _P32, _P32, _P32, _i32, _P32, _P64, _P32]),
     "mhs_result": (_i32, [_vp, _P32, _i32, _P32, _P32, _P32, _i32, _P32, _P64, _P32]),
     "mhs_forced_at": (_i32, [_vp, _i32, _P32, _i32, _P32, _P32]),
@@ -320,6 +326,34 @@ class Instance:
     def kernelize(self) -> dict:
         st = RoundStats()
         _check(lib().mhs_kernelize(self._h, ctypes.byref(st)))
+        return st.as_dict()
+
+    # ---- sharded passes (see paper_2109_06042_gb300/shard.py) ----
+    def pass_begin(self, phase: int):
+        _check(lib().mhs_pass_begin(self._h, int(phase)))
+
+    def pass_contract(self, phase: int, shard: int, nshards: int):
+        _check(lib().mhs_pass_contract(self._h, int(phase), int(shard), int(nshards)))
+
+    def pass_elems(self, phase: int) -> int:
+        """Elements of the phase's partial buffer (m flags or n counts)."""
+        e = ctypes.c_int64()
+        _check(lib().mhs_pass_partial(self._h, int(phase), None, ctypes.byref(e)))
+        return int(e.value)
+
+    def pass_partial(self, phase: int, out):
+        """Copy the partial flags (uint8) / counts (int32) into a CUDA tensor."""
+        e = ctypes.c_int64()
+        _check(lib().mhs_pass_partial(self._h, int(phase), ctypes.c_void_p(out.data_ptr()),
+                                      ctypes.byref(e)))
+        return int(e.value)
+
+    def pass_merge(self, phase: int, buf):
+        _check(lib().mhs_pass_merge(self._h, int(phase), ctypes.c_void_p(buf.data_ptr())))
+
+    def pass_end(self, phase: int) -> dict:
+        st = RoundStats()
+        _check(lib().mhs_pass_end(self._h, int(phase), ctypes.byref(st)))
         return st.as_dict()
 
     def set_timing(self, enable=True):
