@@ -99,10 +99,12 @@ TileChoice choose_tiles(int32_t count, int64_t typical_rows, const mhs_options &
         c.half_stages = best->half_stages == 1 ? 1 : 0;
         c.from_table = 1;
     }
-    // explicit options win over the table
+    // explicit options win over the table; from_table says whether the table
+    // gave any of the three
     if (opt.tile_n) c.tile_n = opt.tile_n;
     if (opt.group_rows) c.group_rows = opt.group_rows;
     if (opt.half_stages) c.half_stages = opt.half_stages == 1 ? 1 : 0;
+    if (opt.tile_n && opt.group_rows && opt.half_stages) c.from_table = 0;
     return c;
 }
 
