@@ -42,4 +42,11 @@ constexpr size_t kPinnedBlock = 1024;
 void *pinned_block();  // nullptr if page-locked memory is unavailable
 void pinned_release(void *p);
 
+// Larger page-locked staging buffers (a batch's instance states and tensor
+// maps), from a process-wide pool in size classes of powers of two from
+// 64 KB; a buffer goes back to the pool, never to the system.  *cls receives
+// the class to give back; nullptr if page-locked memory is unavailable.
+void *pinned_take(size_t bytes, size_t *cls);
+void pinned_give(void *p, size_t cls);
+
 }  // namespace mhs

@@ -67,15 +67,6 @@ __device__ __forceinline__ int find_owner(const T *off, int count, T g) {
     return lo;
 }
 
-__device__ __forceinline__ int64_t kpad_bytes(int32_t K) {
-    int32_t k = K > 0 ? K : 1;
-    return (int64_t)((k + kTcK - 1) / kTcK) * kTcK;
-}
-__device__ __forceinline__ int32_t kpad_words(int32_t K) {
-    int32_t w = (K + 31) / 32;
-    return ((w > 0 ? w : 1) + 3) & ~3;
-}
-
 // ---------------------------------------------------------------- setup --
 
 // Structural checks of device-resident inputs (blockIdx.y = instance):
@@ -100,6 +91,16 @@ __global__ void k_validate(InstState *st, int count) {
     }
 }
 
+// OR of the instances' status words, so that a batch load reads back one
+// word instead of every instance's state.
+__global__ void k_status_or(const InstState *st, int count, int32_t *out) {
+    int32_t x = 0;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < count; b += gridDim.x * blockDim.x)
+        x |= st[b].status;
+    x = __reduce_or_sync(0xffffffffu, x);
+    if ((threadIdx.x & 31) == 0 && x) atomicOr(out, x);
+}
+
 // Batch inputs from device arrays: convert the global int64 CSR offsets of
 // instance b (hyperedges [e0[b], e0[b] + m0)) to its local int32 offsets.
 __global__ void k_localize_ptr(InstState *st, int count, const int64_t *gptr, const int64_t *e0) {
@@ -121,21 +122,18 @@ __global__ void k_gather_bounds(const int64_t *gptr, const int64_t *e0, int64_t 
         out[b] = gptr[e0[b]];
 }
 
-// Zero the occupancy bits of phase p's operand for its first R rows (all
-// row blocks a tile over R rows can touch).  Block-cooperative.
 // Chained-scan compaction of a single instance (see k_compact_edges): status
 // word epochs (30 bits) and the time limit of a wait on a predecessor chunk.
 constexpr uint32_t kEpochMask = (1u << 30) - 1;
 constexpr uint64_t kChainWaitNs = 2000000000ull;  // 2 s
 
+// Zero the occupancy bits of phase p's operand for its first R rows (all
+// row blocks a tile over R rows can touch).  Block-cooperative.
 __device__ __forceinline__ void zero_occupancy(InstState &s, int p, int32_t R, int64_t first,
                                                int64_t stride) {
     if (!s.occ[p]) return;
     const int64_t words = (int64_t)((R + 255) / 256) * 2 * s.occ_words[p];
     for (int64_t w = first; w < words; w += stride) s.occ[p][w] = 0;
-}
-__device__ __forceinline__ void zero_occupancy(InstState &s, int p, int32_t R) {
-    zero_occupancy(s, p, R, threadIdx.x, blockDim.x);
 }
 
 // Round state and vertex id maps (one block per instance).  In input
@@ -376,7 +374,10 @@ __global__ void k_plan(InstState *st, Plan *plan, int phase, int tc, BatchCounte
                 // hyperedges to scatter: phase 0 the current ones; phase 1 the
                 // rows DP saw (the fused pass clears A at those rows and sets
                 // A^T for the ones DP kept)
-                rows = s.m;
+                // (tcgen05 path: rounded up to a multiple of 32, so a warp's
+                // group of 32 rows lies in one instance and starts at a
+                // 32-aligned position: k_set_a_tc, k_set_md_tc, k_clear_at_tc)
+                rows = tc ? (s.m + 31) & ~31 : s.m;
                 const int32_t R = phase == 0 ? s.m : s.n;
                 tiles = tc ? tc_tiles(R, plan->tile_n) : pop_tiles(R);
                 act_any = 1;
@@ -410,19 +411,19 @@ __global__ void k_plan(InstState *st, Plan *plan, int phase, int tc, BatchCounte
 
 // --------------------------------------------------------------- encode --
 
-// One hyperedge row per lane, a warp walking the original vertex lists of
-// its 32 hyperedges together.  Phase 0 (rows = current hyperedges) sets
-// A[e'][v'] (K = current vertices) and counts |e| (= I^E_ii).  Phase 1 walks
-// the rows the DP pass saw (e_prev): its set pass clears their entries of A
-// (the DP pass's clear, fused in since it walks the same incidences), marks
-// the vertices of the hyperedges DP deleted as MD candidates, and for the
-// kept ones sets At[v'][e''] (rows = current vertices, K = the hyperedges'
-// positions after DP) and counts deg(v) (= I^V_jj) and the maximum demand;
-// its clear pass clears At after the MD contraction.  So the operands are
-// all-zero between rounds, and A^T between phases.  A set counts only
-// incidences that were not already set, so a repeated id inside one
-// hyperedge counts once.
-template <int kPhase, bool kSet, bool kDense>
+// Bit-packed operands (popcount path).  One hyperedge row per lane, a warp
+// walking the original vertex lists of its 32 hyperedges together.  Phase 0
+// (rows = current hyperedges) sets A[e'][v'] (K = current vertices) and
+// counts |e| (= I^E_ii).  Phase 1 walks the rows the DP pass saw (e_prev):
+// its set pass clears their entries of A (the DP pass's clear, fused in since
+// it walks the same incidences), marks the vertices of the hyperedges DP
+// deleted as MD candidates, and for the kept ones sets At[v'][e''] (rows =
+// current vertices, K = the hyperedges' positions after DP) and counts deg(v)
+// (= I^V_jj) and the maximum demand; its clear pass clears At after the MD
+// contraction.  So the operands are all-zero between rounds, and A^T between
+// phases.  A set counts only incidences that were not already set, so a
+// repeated id inside one hyperedge counts once.
+template <int kPhase, bool kSet>
 __global__ void __launch_bounds__(256) k_scatter(InstState *st, const Plan *plan) {
     // Each warp takes 32 consecutive rows and walks the incidences of all of
     // them together, 32 at a time, so a hyperedge of 64 vertices does not
@@ -486,8 +487,7 @@ __global__ void __launch_bounds__(256) k_scatter(InstState *st, const Plan *plan
                 s.v_dirty_rb[cv >> 7] = 1;
             }
             if (kPhase == 1 && kSet) {  // the DP pass's clear of A, fused in
-                if (kDense) s.A[(int64_t)rce * s.A_pitch + cv] = 0;
-                else s.Ab[(int64_t)rce * s.Ab_pitch + (cv >> 5)] = 0;
+                s.Ab[(int64_t)rce * s.Ab_pitch + (cv >> 5)] = 0;
                 if (rnew < 0) continue;  // deleted by DP: nothing in A^T
             }
             const int32_t R = kPhase == 0 ? s.m : s.n;
@@ -496,32 +496,13 @@ __global__ void __launch_bounds__(256) k_scatter(InstState *st, const Plan *plan
             const int32_t cc = kPhase == 0 ? cv : rnew;
             if (rr >= R || cc >= K) { atomicOr(&s.status, kErrCapacity); continue; }
             bool fresh = false;
-            if (kDense) {
-                uint8_t *row = (kPhase == 0 ? s.A : s.At) +
-                               (int64_t)rr * (kPhase == 0 ? s.A_pitch : s.At_pitch);
-                if (kSet) {
-                    uint32_t *w = reinterpret_cast<uint32_t *>(row + (cc & ~3));
-                    const uint32_t sh = 8u * (cc & 3);
-                    const uint32_t old = atomicOr(w, (uint32_t)kFp8One << sh);
-                    fresh = ((old >> sh) & 0xffu) == 0;
-                    // occupancy of (row block rr/128, K block cc/kOccK)
-                    const int32_t kblk = cc / kOccK;
-                    uint32_t *ow = s.occ[kPhase] + (int64_t)(rr >> 7) * s.occ_words[kPhase] +
-                                   (kblk >> 5);
-                    const uint32_t ob = 1u << (kblk & 31);
-                    if (!(*reinterpret_cast<volatile uint32_t *>(ow) & ob)) atomicOr(ow, ob);
-                } else {
-                    row[cc] = 0;
-                }
+            uint32_t *row = (kPhase == 0 ? s.Ab : s.Atb) +
+                            (int64_t)rr * (kPhase == 0 ? s.Ab_pitch : s.Atb_pitch);
+            if (kSet) {
+                const uint32_t bit = 1u << (cc & 31);
+                fresh = (atomicOr(&row[cc >> 5], bit) & bit) == 0;
             } else {
-                uint32_t *row = (kPhase == 0 ? s.Ab : s.Atb) +
-                                (int64_t)rr * (kPhase == 0 ? s.Ab_pitch : s.Atb_pitch);
-                if (kSet) {
-                    const uint32_t bit = 1u << (cc & 31);
-                    fresh = (atomicOr(&row[cc >> 5], bit) & bit) == 0;
-                } else {
-                    row[cc >> 5] = 0;  // every set bit of this word is cleared by some thread
-                }
+                row[cc >> 5] = 0;  // every set bit of this word is cleared by some thread
             }
             if (kSet && fresh) {
                 if (kPhase == 0) {
@@ -545,13 +526,381 @@ __global__ void __launch_bounds__(256) k_scatter(InstState *st, const Plan *plan
                     const int32_t fe = s.e_f[ce];
                     s.e_rec[ce] = make_int4(fe, s.edge_rule ? fresh_cnt : fe - fresh_cnt, e, 0);
                 }
-                // a count of 0 decides a pair only from a hyperedge with f > |e|
-                // (DP) or an empty one (SE)
-                if (kDense && (s.edge_rule ? fresh_cnt == 0 : s.e_f[ce] > fresh_cnt))
-                    s.has_loose = 1;
             }
             __syncwarp();  // wfresh is reused by the next group of rows
         }
+    }
+}
+
+// ------------------------------------------ dense operands (tcgen05) --
+//
+// The FP8 operands hold one byte per incidence, and DRAM and L2 move them in
+// 32-byte sectors.  A byte store or a byte atomic into a sector L2 does not
+// hold makes L2 read the sector from DRAM first; a store that covers the
+// whole sector does not.  So the set and clear passes of the dense operands
+// write whole sectors, and each sector has one writer:
+//  * A (rows = hyperedges): a sector lies in one row; the warp that owns the
+//    row builds the sector's byte mask in a shared-memory table from the
+//    row's incidences and writes the sector once.
+//  * A^T (rows = vertices, K = hyperedge positions after DP): the warp that
+//    owns positions [32w, 32w + 32) owns sector w of every vertex row, so it
+//    builds those sectors from its hyperedges' incidences.
+//  * A clear writes the zero sector: every nonzero byte in it belongs to the
+//    row being cleared (A) or to the same all-clearing pass (A^T).
+// Warps take groups of 32 rows; the plan rounds every instance's rows up to
+// a multiple of 32, so a group lies in one instance at a 32-aligned
+// position.  A group whose incidences exceed its table sets its bytes with
+// atomics instead, for all of its sectors, so no sector is written both
+// ways.  The table also deduplicates: a vertex listed twice in a hyperedge
+// sets one bit, so sizes and degrees count it once.
+
+constexpr int kSecWarps = 4;          // warps per block
+constexpr int kSecTab = 512;          // table entries per warp (a power of two)
+constexpr int kSecTabLog = 9;
+constexpr uint32_t kSecEmpty = 0xffffffffu;
+
+struct SecTable {
+    uint32_t key[kSecTab];
+    uint32_t mask[kSecTab];  // bit b: byte b of the sector is 1.0
+    int32_t aux[kSecTab];    // A^T: maximum demand over the sector's hyperedges
+};
+
+// Slot of `key` in the table, inserting it if absent; kSecTab if the table
+// is full (callers insert at most kSecTab keys, so it never is).
+__device__ __forceinline__ int sec_slot(SecTable &t, uint32_t key) {
+    uint32_t h = (key * 2654435761u) >> (32 - kSecTabLog);
+    for (int p = 0; p < kSecTab; ++p) {
+        const uint32_t old = atomicCAS(&t.key[h], kSecEmpty, key);
+        if (old == kSecEmpty || old == key) return (int)h;
+        h = (h + 1) & (kSecTab - 1);
+    }
+    return kSecTab;
+}
+
+// Four mask bits -> four bytes of 0 or 1.0 (bit i -> byte i).
+__device__ __forceinline__ uint32_t fp8_bytes(uint32_t nib) {
+    return ((nib * 0x00204081u) & 0x01010101u) * kFp8One;
+}
+
+__device__ __forceinline__ void store_sector(uint8_t *p, uint32_t m) {
+    uint4 *q = reinterpret_cast<uint4 *>(p);
+    q[0] = make_uint4(fp8_bytes(m & 15u), fp8_bytes((m >> 4) & 15u), fp8_bytes((m >> 8) & 15u),
+                      fp8_bytes((m >> 12) & 15u));
+    q[1] = make_uint4(fp8_bytes((m >> 16) & 15u), fp8_bytes((m >> 20) & 15u),
+                      fp8_bytes((m >> 24) & 15u), fp8_bytes(m >> 28));
+}
+
+__device__ __forceinline__ void zero_sector(uint8_t *p) {
+    uint4 *q = reinterpret_cast<uint4 *>(p);
+    q[0] = make_uint4(0u, 0u, 0u, 0u);
+    q[1] = make_uint4(0u, 0u, 0u, 0u);
+}
+
+// Occupancy bit of (row block rr / 128, K block cc / kOccK) of phase p's operand.
+__device__ __forceinline__ void set_occupancy(InstState &s, int p, int32_t rr, int32_t cc) {
+    const int32_t kblk = cc / kOccK;
+    uint32_t *ow = s.occ[p] + (int64_t)(rr >> 7) * s.occ_words[p] + (kblk >> 5);
+    const uint32_t ob = 1u << (kblk & 31);
+    if (!(*reinterpret_cast<volatile uint32_t *>(ow) & ob)) atomicOr(ow, ob);
+}
+
+// Byte atomic (groups whose incidences exceed the table); true if the byte was 0.
+__device__ __forceinline__ bool set_byte(uint8_t *row, int32_t cc) {
+    uint32_t *w = reinterpret_cast<uint32_t *>(row + (cc & ~3));
+    const uint32_t sh = 8u * (cc & 3);
+    const uint32_t old = atomicOr(w, (uint32_t)kFp8One << sh);
+    return ((old >> sh) & 0xffu) == 0;
+}
+
+// The incidences of a warp's 32 rows (lane l: row l, its list at p0, len
+// entries), flattened: *start = the lane's first flat index, returns the total.
+__device__ __forceinline__ int32_t rows_prefix(int lane, int32_t len, int32_t *start) {
+    int32_t incl = len;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    *start = incl - len;
+    return __shfl_sync(0xffffffffu, incl, 31);
+}
+
+// Flat index f -> its row (the last lane whose run starts at or before f).
+__device__ __forceinline__ int flat_owner(int32_t start, int32_t f) {
+    int r = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+        const int c = r + step;
+        const int32_t sc = __shfl_sync(0xffffffffu, start, c & 31);
+        if (c < 32 && sc <= f) r = c;
+    }
+    return r;
+}
+
+// Walks the incidences of a warp's 32 rows whose vertices are alive (lane l:
+// row l, its vertex list at p0, flattened from *start, tot in all), calling
+// fn(r, cv, x_r) with the row r, the vertex's current position cv and row
+// r's payload x.  The loads of kWalkU chunks of 32 incidences are issued
+// before any is used, so a warp has that many dependent pairs in flight.
+constexpr int kWalkU = 4;
+template <typename F>
+__device__ __forceinline__ void walk_live(const InstState &s, int lane, int32_t p0,
+                                          int32_t start, int32_t tot, int32_t x, F &&fn) {
+    const int32_t *evtx = s.evtx;
+    const int32_t *o2c = s.v_o2c;
+    for (int32_t f0 = 0; f0 < tot; f0 += 32 * kWalkU) {
+        int r[kWalkU];
+        int32_t v[kWalkU], xr[kWalkU];
+#pragma unroll
+        for (int u = 0; u < kWalkU; ++u) {
+            const int32_t f = f0 + 32 * u + lane;
+            r[u] = flat_owner(start, f);
+            const int32_t rp = __shfl_sync(0xffffffffu, p0, r[u]) + f -
+                               __shfl_sync(0xffffffffu, start, r[u]);
+            xr[u] = __shfl_sync(0xffffffffu, x, r[u]);
+            v[u] = f < tot ? __ldg(evtx + rp) : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < kWalkU; ++u) v[u] = v[u] >= 0 ? __ldg(o2c + v[u]) : -1;
+#pragma unroll
+        for (int u = 0; u < kWalkU; ++u)
+            if (v[u] >= 0) fn(r[u], v[u], xr[u]);
+    }
+}
+
+// Empties the table entries the warp has written: fn(key, mask, aux) writes
+// an entry's sector and returns, through *ow / *ob, the occupancy word and
+// bit it sets.  The lanes of one pass over 32 slots set each distinct word
+// with one atomic.
+template <typename F>
+__device__ __forceinline__ void drain_table(SecTable &t, int lane, F &&fn) {
+    __syncwarp();
+    for (int base = 0; base < kSecTab; base += 32) {
+        const int i = base + lane;
+        const uint32_t key = t.key[i];
+        uint32_t *ow = nullptr;
+        uint32_t ob = 0;
+        if (key != kSecEmpty) {
+            const uint32_t m = t.mask[i];
+            const int32_t aux = t.aux[i];
+            t.key[i] = kSecEmpty;
+            t.mask[i] = 0;
+            t.aux[i] = 0;
+            fn(key, m, aux, &ow, &ob);
+        }
+        const unsigned grp = __match_any_sync(0xffffffffu, (unsigned long long)(uintptr_t)ow);
+        const uint32_t bits = __reduce_or_sync(grp, ob);
+        if (ow && lane == __ffs(grp) - 1) atomicOr(ow, bits);
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ void init_table(SecTable &t, int lane) {
+    for (int i = lane; i < kSecTab; i += 32) {
+        t.key[i] = kSecEmpty;
+        t.mask[i] = 0;
+        t.aux[i] = 0;
+    }
+    __syncwarp();
+}
+
+// Occupancy word and bit of (row block rr / 128, K block cc / kOccK) of
+// phase p's operand.
+__device__ __forceinline__ uint32_t *occ_word(InstState &s, int p, int32_t rr, int32_t cc,
+                                              uint32_t *ob) {
+    const int32_t kblk = cc / kOccK;
+    *ob = 1u << (kblk & 31);
+    return s.occ[p] + (int64_t)(rr >> 7) * s.occ_words[p] + (kblk >> 5);
+}
+
+// Phase 0 set: A[e'][v'] = 1.0 for the current hyperedges' live incidences,
+// |e| (= I^E_ii), the epilogue's row records and the occupancy bits of A.
+__global__ void __launch_bounds__(32 * kSecWarps) k_set_a_tc(InstState *st, const Plan *plan) {
+    __shared__ SecTable tab[kSecWarps];
+    __shared__ int32_t wfresh[kSecWarps][32];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    SecTable &t = tab[wib];
+    init_table(t, lane);
+    const int32_t total = plan->total_rows;
+    const int32_t nw = gridDim.x * kSecWarps;
+    for (int32_t g0 = (blockIdx.x * kSecWarps + wib) * 32; g0 < total; g0 += nw * 32) {
+        const int b = find_owner(plan->row_off, plan->count, g0);
+        InstState &s = st[b];
+        const int32_t ce0 = g0 - plan->row_off[b];
+        const int32_t ce = ce0 + lane;
+        const bool row = ce < s.m;
+        int32_t e = 0, p0 = 0, len = 0;
+        if (row) {
+            e = __ldg(s.e_c2o + ce);
+            p0 = __ldg(s.eptr + e);
+            len = __ldg(s.eptr + e + 1) - p0;
+        }
+        int32_t start;
+        const int32_t tot = rows_prefix(lane, len, &start);
+        const bool table = tot <= kSecTab;
+        const int32_t K = s.n;
+        uint8_t *const A = s.A;
+        const int64_t pitch = s.A_pitch;
+        wfresh[wib][lane] = 0;
+        __syncwarp();
+        walk_live(s, lane, p0, start, tot, 0, [&](int r, int32_t cv, int32_t) {
+            if (cv >= K) { atomicOr(&s.status, kErrCapacity); return; }
+            if (table) {
+                const int slot = sec_slot(t, ((uint32_t)r << 26) | (uint32_t)(cv >> 5));
+                if (slot < kSecTab) atomicOr(&t.mask[slot], 1u << (cv & 31));
+                else atomicOr(&s.status, kErrCapacity);
+            } else {
+                const int32_t rr = ce0 + r;
+                if (set_byte(A + (int64_t)rr * pitch, cv)) atomicAdd(&wfresh[wib][r], 1);
+                set_occupancy(s, 0, rr, cv);
+            }
+        });
+        if (table) {
+            drain_table(t, lane, [&](uint32_t key, uint32_t m, int32_t, uint32_t **ow,
+                                     uint32_t *ob) {
+                const int r = (int)(key >> 26);
+                const int32_t c0 = (int32_t)(key & 0x3ffffffu) * 32;
+                const int32_t rr = ce0 + r;
+                store_sector(A + (int64_t)rr * pitch + c0, m);
+                atomicAdd(&wfresh[wib][r], __popc(m));
+                *ow = occ_word(s, 0, rr, c0, ob);
+            });
+        } else {
+            __syncwarp();
+        }
+        if (row) {
+            const int32_t size = wfresh[wib][lane];
+            // a hyperedge whose size changed since the previous DP pass (or
+            // never tested) makes its row block a DP candidate
+            if (s.e_dirty_rb && s.e_s[ce] != size) s.e_dirty_rb[ce >> 7] = 1;
+            s.e_s[ce] = size;
+            const int32_t fe = s.e_f[ce];
+            if (s.e_rec) s.e_rec[ce] = make_int4(fe, s.edge_rule ? size : fe - size, e, 0);
+            // a count of 0 decides a pair only from a hyperedge with f > |e|
+            // (DP) or an empty one (SE)
+            if (s.edge_rule ? size == 0 : fe > size) s.has_loose = 1;
+        }
+        __syncwarp();  // wfresh is reused by the next group
+    }
+}
+
+// Phase 1 set, two walks per group of 32 positions [c0, c0 + 32):
+//  (a) the rows the DP pass saw there (e_prev): zero their sectors of A (the
+//      DP pass's clear), and mark the vertices of the hyperedges DP deleted
+//      as MD candidates;
+//  (b) the hyperedges DP kept there (e_c2o after DP): sector c0 / 32 of
+//      A^T's vertex rows, deg(v) (= I^V_jj), the maximum demand over E(v),
+//      and the occupancy bits of A^T.
+__global__ void __launch_bounds__(32 * kSecWarps) k_set_md_tc(InstState *st, const Plan *plan) {
+    __shared__ SecTable tab[kSecWarps];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    SecTable &t = tab[wib];
+    init_table(t, lane);
+    const int32_t total = plan->total_rows;
+    const int32_t nw = gridDim.x * kSecWarps;
+    for (int32_t g0 = (blockIdx.x * kSecWarps + wib) * 32; g0 < total; g0 += nw * 32) {
+        const int b = find_owner(plan->row_off, plan->count, g0);
+        InstState &s = st[b];
+        const int32_t c0 = g0 - plan->row_off[b];
+        const int32_t n = s.n;
+        {  // (a)
+            const int32_t ce = c0 + lane;
+            int32_t p0 = 0, len = 0, mark = 0;
+            if (ce < s.m) {
+                const int32_t e = __ldg(s.e_prev + ce);
+                p0 = __ldg(s.eptr + e);
+                len = __ldg(s.eptr + e + 1) - p0;
+                mark = s.v_dirty && __ldg(s.e_o2c + e) < 0;
+            }
+            int32_t start;
+            const int32_t tot = rows_prefix(lane, len, &start);
+            uint8_t *const A = s.A;
+            const int64_t pitch = s.A_pitch;
+            uint8_t *const vd = s.v_dirty;
+            uint8_t *const vdrb = s.v_dirty_rb;
+            walk_live(s, lane, p0, start, tot, mark, [&](int r, int32_t cv, int32_t rmark) {
+                if (rmark && cv < n) {
+                    vd[cv] = 1;
+                    vdrb[cv >> 7] = 1;
+                }
+                zero_sector(A + (int64_t)(c0 + r) * pitch + (cv & ~31));
+            });
+        }
+        {  // (b)
+            const int32_t cn = c0 + lane;
+            int32_t p0 = 0, len = 0, fe = 0;
+            if (cn < s.m_dp) {
+                const int32_t e = __ldg(s.e_c2o + cn);
+                p0 = __ldg(s.eptr + e);
+                len = __ldg(s.eptr + e + 1) - p0;
+                fe = __ldg(s.f + e);
+            }
+            int32_t start;
+            const int32_t tot = rows_prefix(lane, len, &start);
+            const bool table = tot <= kSecTab;
+            uint8_t *const At = s.At;
+            const int64_t pitch = s.At_pitch;
+            int32_t *const deg = s.v_deg;
+            int32_t *const maxf = s.v_maxf;
+            walk_live(s, lane, p0, start, tot, fe, [&](int r, int32_t cv, int32_t rfe) {
+                if (cv >= n) { atomicOr(&s.status, kErrCapacity); return; }
+                if (table) {
+                    const int slot = sec_slot(t, (uint32_t)cv);
+                    if (slot < kSecTab) {
+                        atomicOr(&t.mask[slot], 1u << r);
+                        atomicMax(&t.aux[slot], rfe);
+                    } else {
+                        atomicOr(&s.status, kErrCapacity);
+                    }
+                } else {
+                    if (set_byte(At + (int64_t)cv * pitch, c0 + r)) {
+                        atomicAdd(&deg[cv], 1);
+                        atomicMax(&maxf[cv], rfe);
+                    }
+                    set_occupancy(s, 1, cv, c0);
+                }
+            });
+            if (table) {
+                drain_table(t, lane, [&](uint32_t cv, uint32_t m, int32_t mf, uint32_t **ow,
+                                         uint32_t *ob) {
+                    store_sector(At + (int64_t)cv * pitch + c0, m);
+                    atomicAdd(&deg[cv], __popc(m));
+                    atomicMax(&maxf[cv], mf);
+                    *ow = occ_word(s, 1, (int32_t)cv, c0, ob);
+                });
+            } else {
+                __syncwarp();
+            }
+        }
+    }
+}
+
+// Phase 1 clear, after the MD contraction: zero the sectors of A^T that the
+// set pass wrote (group [c0, c0 + 32): sector c0 / 32 of its vertices' rows).
+__global__ void __launch_bounds__(32 * kSecWarps) k_clear_at_tc(InstState *st,
+                                                              const Plan *plan) {
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int32_t total = plan->total_rows;
+    const int32_t nw = gridDim.x * kSecWarps;
+    for (int32_t g0 = (blockIdx.x * kSecWarps + wib) * 32; g0 < total; g0 += nw * 32) {
+        const int b = find_owner(plan->row_off, plan->count, g0);
+        InstState &s = st[b];
+        const int32_t c0 = g0 - plan->row_off[b];
+        const int32_t cn = c0 + lane;
+        int32_t p0 = 0, len = 0;
+        if (cn < s.m_dp) {
+            const int32_t e = __ldg(s.e_c2o + cn);
+            p0 = __ldg(s.eptr + e);
+            len = __ldg(s.eptr + e + 1) - p0;
+        }
+        int32_t start;
+        const int32_t tot = rows_prefix(lane, len, &start);
+        uint8_t *const At = s.At;
+        const int64_t pitch = s.At_pitch;
+        const int32_t n = s.n;
+        walk_live(s, lane, p0, start, tot, 0, [&](int, int32_t cv, int32_t) {
+            if (cv < n) zero_sector(At + (int64_t)cv * pitch + c0);
+        });
     }
 }
 
@@ -995,6 +1344,11 @@ cudaError_t launch_validate(InstState *st, int count, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+cudaError_t launch_status_or(const InstState *st, int count, int32_t *out, cudaStream_t s) {
+    k_status_or<<<(count + 255) / 256 < 64 ? (count + 255) / 256 : 64, 256, 0, s>>>(st, count, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_localize_ptr(InstState *st, int count, const int64_t *gptr, const int64_t *e0,
                                 cudaStream_t s) {
     k_localize_ptr<<<dim3(16, count), 256, 0, s>>>(st, count, gptr, e0);
@@ -1025,25 +1379,29 @@ cudaError_t launch_build(InstState *st, int count, int32_t max_rounds, int64_t m
     return cudaGetLastError();
 }
 
+// Set (or, phase 1, clear) pass of the operands: dense FP8 (tcgen05 path,
+// sector writes) or bit-packed (popcount path).
 template <int kPhase>
-static void launch_scatter(InstState *st, const Plan *plan, bool set, bool dense, int grid,
+static void launch_scatter(InstState *st, const Plan *plan, bool set, bool dense, int sms,
                            cudaStream_t s) {
-    if (set) {
-        if (dense) k_scatter<kPhase, true, true><<<grid, 256, 0, s>>>(st, plan);
-        else k_scatter<kPhase, true, false><<<grid, 256, 0, s>>>(st, plan);
-    } else {
-        if (dense) k_scatter<kPhase, false, true><<<grid, 256, 0, s>>>(st, plan);
-        else k_scatter<kPhase, false, false><<<grid, 256, 0, s>>>(st, plan);
+    if (dense) {
+        const int grid = grid_for(sms, 8);
+        if (kPhase == 0) k_set_a_tc<<<grid, 32 * kSecWarps, 0, s>>>(st, plan);
+        else if (set) k_set_md_tc<<<grid, 32 * kSecWarps, 0, s>>>(st, plan);
+        else k_clear_at_tc<<<2 * grid, 32 * kSecWarps, 0, s>>>(st, plan);
+        return;
     }
+    const int grid = grid_for(sms, 8);
+    if (set) k_scatter<kPhase, true><<<grid, 256, 0, s>>>(st, plan);
+    else k_scatter<kPhase, false><<<grid, 256, 0, s>>>(st, plan);
 }
 
 cudaError_t launch_phase_prologue(InstState *st, Plan *plan, BatchCounters *ctr, int phase,
                                   int contraction, int sms, cudaStream_t s) {
     const bool tc = contraction == kFp8;
     k_plan<<<1, 1024, 0, s>>>(st, plan, phase, tc ? 1 : 0, ctr);
-    const int grid = grid_for(sms, 8);
-    if (phase == 0) launch_scatter<0>(st, plan, true, tc, grid, s);
-    else launch_scatter<1>(st, plan, true, tc, grid, s);
+    if (phase == 0) launch_scatter<0>(st, plan, true, tc, sms, s);
+    else launch_scatter<1>(st, plan, true, tc, sms, s);
     return cudaGetLastError();
 }
 
@@ -1067,10 +1425,9 @@ cudaError_t launch_phase_epilogue(InstState *st, Plan *plan, BatchCounters *ctr,
                                   int phase, int contraction, int sms, cudaStream_t s,
                                   int32_t *done_list, int compact_blocks) {
     const bool tc = contraction == kFp8;
-    const int grid = grid_for(sms, 8);
     // (the DP pass's clear of A runs inside the MD set pass, which walks the
     // same incidences)
-    if (phase == 1) launch_scatter<1>(st, plan, false, tc, grid, s);
+    if (phase == 1) launch_scatter<1>(st, plan, false, tc, sms, s);
     // compact_blocks > 1: a single instance, one block per chunk of 1024 ids
     const dim3 cgrid(compact_blocks > 1 ? compact_blocks : 1, count);
     if (phase == 0) k_compact_edges<<<cgrid, 1024, 0, s>>>(st, count);

@@ -27,6 +27,8 @@ struct BatchCounters {
 };
 
 cudaError_t launch_validate(InstState *st, int count, cudaStream_t s);
+// *out |= the OR of the instances' status words (the caller zeroes *out).
+cudaError_t launch_status_or(const InstState *st, int count, int32_t *out, cudaStream_t s);
 cudaError_t launch_localize_ptr(InstState *st, int count, const int64_t *gptr, const int64_t *e0,
                                 cudaStream_t s);
 cudaError_t launch_gather_bounds(const int64_t *gptr, const int64_t *e0, int64_t *out, int count,

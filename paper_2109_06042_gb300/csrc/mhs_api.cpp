@@ -109,6 +109,37 @@ void mhs::pinned_release(void *p) {
 }
 
 namespace {
+std::vector<std::pair<size_t, void *>> g_stage_free;  // (class, buffer), under g_pin_mu
+}  // namespace
+
+void *mhs::pinned_take(size_t bytes, size_t *cls) {
+    size_t c = (size_t)64 << 10;
+    while (c < bytes) c <<= 1;
+    *cls = c;
+    {
+        std::lock_guard<std::mutex> lk(g_pin_mu);
+        for (size_t i = 0; i < g_stage_free.size(); ++i)
+            if (g_stage_free[i].first == c) {
+                void *p = g_stage_free[i].second;
+                g_stage_free.erase(g_stage_free.begin() + (long)i);
+                return p;
+            }
+    }
+    void *p = nullptr;
+    if (cudaMallocHost(&p, c) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void mhs::pinned_give(void *p, size_t cls) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    g_stage_free.push_back({cls, p});
+}
+
+namespace {
 // Dense operand regions that are known to be all zero, kept for reuse by
 // later loads of similar size.  Every phase clears exactly the incidences it
 // set, so an instance that finished without a device error leaves its
@@ -121,7 +152,10 @@ struct ZeroBlock {
 };
 std::mutex g_zero_mu;
 std::vector<ZeroBlock> g_zero;
-constexpr int64_t kZeroCacheBytes = 16ll << 30;
+// Budget of the cache (a batch of 4,096 instances of up to 2,000 x 4,000
+// holds 16.7 GB of operands).  A load whose allocation fails empties the
+// cache and retries.
+constexpr int64_t kZeroCacheBytes = 32ll << 30;
 
 uint8_t *zero_take(int dev, int64_t bytes) {
     std::lock_guard<std::mutex> lk(g_zero_mu);
@@ -201,6 +235,10 @@ struct mhs_instance {
     int32_t count = 0;
     std::vector<HostInst> hinst;
     std::vector<InstState> hstate;  // host mirror: pointers and static fields
+    // a batch's page-locked staging: its states, then its tensor maps
+    uint8_t *stage = nullptr;
+    size_t stage_cls = 0;
+    int64_t stage_tmaps = 0;        // offset of the tensor maps in `stage`
     uint8_t *arena = nullptr;       // all device memory of the instance
     InstState *dstate = nullptr;
     Plan *dplan = nullptr;
@@ -258,6 +296,7 @@ void destroy(mhs_instance *h) {
         else cudaFreeAsync(h->dense, h->stream);
     }
     pinned_release(h->pin);
+    pinned_give(h->stage, h->stage_cls);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
 }
@@ -491,6 +530,12 @@ mhs_status create(int32_t count, const int32_t *n, const int32_t *m, const int64
     h->hctr = reinterpret_cast<BatchCounters *>(h->pin);
     h->hkerr = reinterpret_cast<int32_t *>(h->pin + 64);
     h->hstate.resize(count);
+    if (count > 1) {  // without it the copies stage through pageable memory
+        h->stage_tmaps = round_up((int64_t)sizeof(InstState) * count, 128);
+        h->stage = static_cast<uint8_t *>(pinned_take(
+            (size_t)(h->stage_tmaps + (dense ? (int64_t)tmap_bytes() * 2 * count : 0)),
+            &h->stage_cls));
+    }
     int64_t vbase = 0, ebase = 0;
     for (int b = 0; b < count; ++b) {
         const Layout &L = lay[b];
@@ -583,15 +628,28 @@ mhs_status create(int32_t count, const int32_t *n, const int32_t *m, const int64
 
 // Tensor maps (host encode, one copy to the device), state upload, and the
 // device-side build of the vertex -> hyperedge lists and id maps.
+// The instance states to the device (through the batch's pinned staging).
+cudaError_t upload_states(mhs_instance *h) {
+    const size_t sb = sizeof(InstState) * (size_t)h->count;
+    const void *src = h->hstate.data();
+    if (h->stage) {  // no copy from it is in flight: every load step before synchronised
+        std::memcpy(h->stage, src, sb);
+        src = h->stage;
+    }
+    return cudaMemcpyAsync(h->dstate, src, sb, cudaMemcpyHostToDevice, h->stream);
+}
+
 mhs_status finish_load(mhs_instance *h, int64_t tmap_off) {
     const bool dense = h->contraction == kFp8;
     if (dense) {
         CUDA_TRY(prepare_tc_contract());
         const size_t mb = tmap_bytes() * 2 * h->count;
-        // one instance: staged in its pinned block; a batch: a local vector
-        const bool pinned = mb <= kPinnedBlock - 256;
+        // one instance: its pinned block; a batch: its pinned staging, else a local vector
+        const bool pinned = mb <= kPinnedBlock - 256 || h->stage;
         std::vector<uint8_t> local(pinned ? 0 : mb);
-        uint8_t *maps = pinned ? h->pin + 256 : local.data();
+        uint8_t *maps = mb <= kPinnedBlock - 256 ? h->pin + 256
+                        : h->stage              ? h->stage + h->stage_tmaps
+                                                : local.data();
         for (int b = 0; b < h->count; ++b) {
             const InstState &s = h->hstate[b];
             if (!make_operand_tmap(maps + tmap_bytes() * 2 * b, s.A, s.A_pitch, s.A_rows) ||
@@ -601,8 +659,7 @@ mhs_status finish_load(mhs_instance *h, int64_t tmap_off) {
         CUDA_TRY(cudaMemcpyAsync(h->arena + tmap_off, maps, mb, cudaMemcpyHostToDevice, h->stream));
         if (!pinned) CUDA_TRY(cudaStreamSynchronize(h->stream));  // `local` goes out of scope
     }
-    CUDA_TRY(cudaMemcpyAsync(h->dstate, h->hstate.data(), sizeof(InstState) * h->count,
-                             cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(upload_states(h));
     if (!h->dense_zeroed) {
         CUDA_TRY(cudaMemsetAsync(h->dense, 0, (size_t)h->dense_bytes, h->stream));
         h->dense_zeroed = true;
@@ -1011,8 +1068,10 @@ mhs_status mhs_load_batch_device(int32_t count, const int32_t *n, const int32_t 
     cudaMemPool_t pool;
     CUDA_TRY(pool_for(dev, &pool));
     int64_t *tmp = nullptr;
+    // [0, count]: hyperedge offsets; [count + 1, 2 count + 1]: their CSR
+    // positions; then the OR of the validation statuses
     CUDA_TRY(cudaMallocFromPoolAsync(reinterpret_cast<void **>(&tmp),
-                                     sizeof(int64_t) * 2 * ((size_t)count + 1), pool, cs));
+                                     sizeof(int64_t) * (2 * ((size_t)count + 1) + 1), pool, cs));
     std::vector<int64_t> bounds(count + 1);
     cudaError_t e = cudaMemcpyAsync(tmp, eoff.data(), sizeof(int64_t) * (count + 1),
                                     cudaMemcpyHostToDevice, cs);
@@ -1058,28 +1117,38 @@ mhs_status mhs_load_batch_device(int32_t count, const int32_t *n, const int32_t 
     if (e == cudaSuccess && h->sum_m > 0)
         e = cudaMemcpyAsync(h->arena + h->in_f, demand, 4 * (size_t)h->sum_m,
                             cudaMemcpyDeviceToDevice, h->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(h->dstate, h->hstate.data(), sizeof(InstState) * count,
-                            cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = upload_states(h);
     if (e == cudaSuccess) e = launch_localize_ptr(h->dstate, count, edge_ptr, tmp, h->stream);
     if (e == cudaSuccess) e = launch_validate(h->dstate, count, h->stream);
-    std::vector<InstState> chk(count);
+    int32_t *any_status = reinterpret_cast<int32_t *>(tmp + 2 * ((int64_t)count + 1));
+    int32_t hany = 0;
+    if (e == cudaSuccess) e = cudaMemsetAsync(any_status, 0, sizeof(int32_t), h->stream);
+    if (e == cudaSuccess) e = launch_status_or(h->dstate, count, any_status, h->stream);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(chk.data(), h->dstate, sizeof(InstState) * count,
-                            cudaMemcpyDeviceToHost, h->stream);
+        e = cudaMemcpyAsync(&hany, any_status, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                            h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     cudaFreeAsync(tmp, h->stream);
     if (e != cudaSuccess) {
         destroy(h);
         return fail(MHS_ECUDA, "batch device load: %s", cudaGetErrorString(e));
     }
-    for (int b = 0; b < count; ++b)
-        if (chk[b].status) {
-            const int32_t sv = chk[b].status;
-            destroy(h);
-            return fail(MHS_EINVAL, "instance %d malformed (status 0x%x: %s)", b, sv,
-                        status_text(sv));
-        }
+    if (hany) {  // some instance is malformed: read the states to name the first
+        std::vector<InstState> chk(count);
+        e = cudaMemcpyAsync(chk.data(), h->dstate, sizeof(InstState) * count,
+                            cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        for (int b = 0; e == cudaSuccess && b < count; ++b)
+            if (chk[b].status) {
+                const int32_t sv = chk[b].status;
+                destroy(h);
+                return fail(MHS_EINVAL, "instance %d malformed (status 0x%x: %s)", b, sv,
+                            status_text(sv));
+            }
+        destroy(h);
+        return fail(MHS_ECUDA, "batch device load: %s",
+                    e != cudaSuccess ? cudaGetErrorString(e) : "status read back inconsistent");
+    }
     st = finish_load(h, tmoff);
     if (st == MHS_OK && cudaStreamSynchronize(h->stream) != cudaSuccess)
         st = fail(MHS_ECUDA, "load failed");
