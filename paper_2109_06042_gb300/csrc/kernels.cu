@@ -169,7 +169,7 @@ __global__ void k_init(InstState *st, int count, int32_t max_rounds) {
         s.n = s.n0; s.m = s.m0; s.m_dp = s.m0; s.n_next = s.n0;
         s.rounds = 0; s.active = s.status == 0; s.max_rounds = max_rounds; s.changed = 0;
         s.dp_deleted = 0; s.md_deleted = 0; s.has_loose = 0;
-        s.fe_stage = 0; s.fe_passes = 0; s.md_full = 1;
+        s.fe_stage = 0; s.fe_passes = 0; s.md_full = 1; s.skip_a = 0; s.skip_at = 0;
     }
 }
 
@@ -371,13 +371,26 @@ __global__ void k_plan(InstState *st, Plan *plan, int phase, int tc, BatchCounte
                 st[b].scan_epoch = (s.scan_epoch + 1) & kEpochMask;
             }
             if (s.active && s.status == 0) {
+                // Incremental rounds (tcgen05 path): a pass without candidates
+                // deletes nothing, so its operand is not needed.  DP: no
+                // hyperedge lost a vertex since the previous DP pass, i.e. the
+                // previous MD pass deleted none (FE sets md_full).  MD: this
+                // round's DP pass deleted no hyperedge.
+                int32_t skip = 0;
+                if (tc && !s.no_skip && !s.md_full) {
+                    if (phase == 0) skip = s.e_dirty_rb && s.md_deleted == 0;
+                    else skip = s.v_dirty && s.dp_deleted == 0;
+                }
+                if (phase == 0) st[b].skip_a = skip;
+                else st[b].skip_at = skip;
                 // hyperedges to scatter: phase 0 the current ones; phase 1 the
                 // rows DP saw (the fused pass clears A at those rows and sets
                 // A^T for the ones DP kept)
                 // (tcgen05 path: rounded up to a multiple of 32, so a warp's
                 // group of 32 rows lies in one instance and starts at a
                 // 32-aligned position: k_set_a_tc, k_set_md_tc, k_clear_at_tc)
-                rows = tc ? (s.m + 31) & ~31 : s.m;
+                const bool none = phase == 0 ? skip : skip && s.skip_a;
+                rows = !tc ? s.m : none ? 0 : (s.m + 31) & ~31;
                 const int32_t R = phase == 0 ? s.m : s.n;
                 tiles = tc ? tc_tiles(R, plan->tile_n) : pop_tiles(R);
                 act_any = 1;
@@ -803,7 +816,7 @@ __global__ void __launch_bounds__(32 * kSecWarps) k_set_md_tc(InstState *st, con
         InstState &s = st[b];
         const int32_t c0 = g0 - plan->row_off[b];
         const int32_t n = s.n;
-        {  // (a)
+        if (!s.skip_a) {  // (a)
             const int32_t ce = c0 + lane;
             int32_t p0 = 0, len = 0, mark = 0;
             if (ce < s.m) {
@@ -826,7 +839,7 @@ __global__ void __launch_bounds__(32 * kSecWarps) k_set_md_tc(InstState *st, con
                 zero_sector(A + (int64_t)(c0 + r) * pitch + (cv & ~31));
             });
         }
-        {  // (b)
+        if (!s.skip_at) {  // (b)
             const int32_t cn = c0 + lane;
             int32_t p0 = 0, len = 0, fe = 0;
             if (cn < s.m_dp) {
@@ -886,6 +899,7 @@ __global__ void __launch_bounds__(32 * kSecWarps) k_clear_at_tc(InstState *st,
         const int b = find_owner(plan->row_off, plan->count, g0);
         InstState &s = st[b];
         const int32_t c0 = g0 - plan->row_off[b];
+        if (s.skip_at) continue;
         const int32_t cn = c0 + lane;
         int32_t p0 = 0, len = 0;
         if (cn < s.m_dp) {

@@ -8,7 +8,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <mutex>
+#include <thread>
 #include <string>
 #include <vector>
 
@@ -650,12 +652,48 @@ mhs_status finish_load(mhs_instance *h, int64_t tmap_off) {
         uint8_t *maps = mb <= kPinnedBlock - 256 ? h->pin + 256
                         : h->stage              ? h->stage + h->stage_tmaps
                                                 : local.data();
-        for (int b = 0; b < h->count; ++b) {
+        const int count = h->count;
+        auto enc = [&](int b) {
             const InstState &s = h->hstate[b];
-            if (!make_operand_tmap(maps + tmap_bytes() * 2 * b, s.A, s.A_pitch, s.A_rows) ||
-                !make_operand_tmap(maps + tmap_bytes() * (2 * b + 1), s.At, s.At_pitch, s.At_rows))
-                return fail(MHS_ECUDA, "cuTensorMapEncodeTiled failed for instance %d", b);
+            return make_operand_tmap(maps + tmap_bytes() * 2 * b, s.A, s.A_pitch, s.A_rows) &&
+                   make_operand_tmap(maps + tmap_bytes() * (2 * b + 1), s.At, s.At_pitch,
+                                     s.At_rows);
+        };
+        // Four maps per instance: a large batch encodes them on several
+        // threads.  Instance 0 goes first on this thread, which resolves the
+        // driver's encoder before any other thread calls it.
+        if (!enc(0)) return fail(MHS_ECUDA, "cuTensorMapEncodeTiled failed for instance 0");
+        const int nt = count >= 512 ? 4 : 1;
+        std::atomic<int> bad{count};  // lowest instance whose encoding failed
+        auto share = [&](int t) {
+            for (int b = 1 + t; b < count; b += nt)
+                if (!enc(b)) {
+                    int cur = bad.load();
+                    while (b < cur && !bad.compare_exchange_weak(cur, b)) {
+                    }
+                }
+        };
+        // a new thread has no current context, which the encoder needs
+        auto worker = [&](int t) {
+            if (cudaSetDevice(h->device) != cudaSuccess) {
+                int cur = bad.load();
+                while (1 + t < cur && !bad.compare_exchange_weak(cur, 1 + t)) {
+                }
+                return;
+            }
+            share(t);
+        };
+        std::vector<std::thread> threads;
+        int started = 1;
+        try {
+            for (; started < nt; ++started) threads.emplace_back(worker, started);
+        } catch (...) {  // a thread that cannot start: its share runs here
         }
+        for (int t = started; t < nt; ++t) share(t);
+        share(0);
+        for (std::thread &x : threads) x.join();
+        if (bad.load() < count)
+            return fail(MHS_ECUDA, "cuTensorMapEncodeTiled failed for instance %d", bad.load());
         CUDA_TRY(cudaMemcpyAsync(h->arena + tmap_off, maps, mb, cudaMemcpyHostToDevice, h->stream));
         if (!pinned) CUDA_TRY(cudaStreamSynchronize(h->stream));  // `local` goes out of scope
     }

@@ -104,6 +104,11 @@ struct InstState {
     uint8_t *v_dirty;      // per current vertex: lost a hyperedge in this round's DP
     uint8_t *v_dirty_rb;   // per 128 vertex rows: some v_dirty set
     int32_t md_full;       // 1: every vertex is an MD candidate (first round, after FE)
+    // tcgen05 path, set by the plan of each phase: no candidate can exist in
+    // this round's DP pass (the previous MD pass deleted no vertex) or MD pass
+    // (this round's DP pass deleted no hyperedge), so its operand is neither
+    // written nor cleared and its tile list is empty
+    int32_t skip_a, skip_at;
 
     // dense FP8 operands: rows x pitch bytes (0x38 = 1.0 in E4M3)
     uint8_t *A;            // rows = current hyperedges, K = current vertices
