@@ -241,6 +241,9 @@ struct mhs_instance {
     uint8_t *stage = nullptr;
     size_t stage_cls = 0;
     int64_t stage_tmaps = 0;        // offset of the tensor maps in `stage`
+    // a single instance's host inputs, staged page-locked for their copies
+    uint8_t *in_stage = nullptr;
+    size_t in_stage_cls = 0;
     uint8_t *arena = nullptr;       // all device memory of the instance
     InstState *dstate = nullptr;
     Plan *dplan = nullptr;
@@ -299,6 +302,7 @@ void destroy(mhs_instance *h) {
     }
     pinned_release(h->pin);
     pinned_give(h->stage, h->stage_cls);
+    pinned_give(h->in_stage, h->in_stage_cls);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
 }
@@ -334,30 +338,65 @@ mhs_status check_options(const mhs_options *opt, mhs_options *out) {
 }
 
 // Host-side structural validation of one instance's CSR.
+// Checks of one instance's host CSR.  quiet: report only the status (safe
+// on several threads at once: the error text is not touched).
 mhs_status validate_host(int32_t n, int32_t m, const int64_t *eptr64, const int32_t *eptr32,
                          const int32_t *evtx, const int32_t *demand, std::vector<int32_t> &mark,
-                         int32_t tag_base, const char *what) {
-    if (n < 0 || m < 0) return fail(MHS_EINVAL, "%s: n and m must be >= 0", what);
+                         int32_t tag_base, const char *what, bool quiet = false) {
+    auto bad = [quiet](mhs_status st, const char *fmt, auto... args) {
+        return quiet ? st : mhs::set_error(st, fmt, args...);
+    };
+    if (n < 0 || m < 0) return bad(MHS_EINVAL, "%s: n and m must be >= 0", what);
     if (n >= (1 << 24) || m >= (1 << 24))
-        return fail(MHS_EINVAL, "%s: n and m must be < 2^24 (exact FP32 counts)", what);
+        return bad(MHS_EINVAL, "%s: n and m must be < 2^24 (exact FP32 counts)", what);
     auto ptr = [&](int64_t i) -> int64_t { return eptr64 ? eptr64[i] : eptr32[i]; };
     if ((size_t)n > mark.size()) mark.assign((size_t)n, -1);
     for (int32_t e = 0; e < m; ++e) {
         int64_t a = ptr(e), b = ptr(e + 1);
-        if (b < a) return fail(MHS_EINVAL, "%s: edge_ptr decreases at hyperedge %d", what, e);
-        if (b - a > (1ll << 24)) return fail(MHS_EINVAL, "%s: hyperedge %d too large", what, e);
-        if (demand[e] < 1) return fail(MHS_EINVAL, "%s: demand of hyperedge %d is < 1", what, e);
+        if (b < a) return bad(MHS_EINVAL, "%s: edge_ptr decreases at hyperedge %d", what, e);
+        if (b - a > (1ll << 24)) return bad(MHS_EINVAL, "%s: hyperedge %d too large", what, e);
+        if (demand[e] < 1) return bad(MHS_EINVAL, "%s: demand of hyperedge %d is < 1", what, e);
         for (int64_t p = a; p < b; ++p) {
             int32_t v = evtx[p];
             if (v < 0 || v >= n)
-                return fail(MHS_EINVAL, "%s: hyperedge %d has vertex id %d outside [0,%d)", what,
+                return bad(MHS_EINVAL, "%s: hyperedge %d has vertex id %d outside [0,%d)", what,
                             e, v, n);
             if (mark[v] == tag_base + e)
-                return fail(MHS_EINVAL, "%s: hyperedge %d lists vertex %d twice", what, e, v);
+                return bad(MHS_EINVAL, "%s: hyperedge %d lists vertex %d twice", what, e, v);
             mark[v] = tag_base + e;
         }
     }
     return MHS_OK;
+}
+
+// validate_host over hyperedge ranges on several threads for a large
+// instance; a failure is validated again on this thread for its message.
+mhs_status validate_host_parallel(int32_t n, int32_t m, const int32_t *eptr32,
+                                  const int32_t *evtx, const int32_t *demand, int64_t nnz,
+                                  const char *what) {
+    std::vector<int32_t> mark;
+    const int nt = nnz >= (1 << 17) ? (int)std::min<int64_t>(8, nnz >> 16) : 1;
+    if (nt <= 1) return validate_host(n, m, nullptr, eptr32, evtx, demand, mark, 0, what);
+    std::atomic<bool> bad{false};
+    auto part = [&](int t) {
+        const int32_t e0 = (int32_t)((int64_t)m * t / nt);
+        const int32_t e1 = (int32_t)((int64_t)m * (t + 1) / nt);
+        std::vector<int32_t> mk;
+        if (validate_host(n, e1 - e0, nullptr, eptr32 + e0, evtx, demand + e0, mk, 0, what,
+                          /*quiet=*/true))
+            bad = true;
+    };
+    std::vector<std::thread> threads;
+    int started = 1;
+    try {
+        for (; started < nt; ++started) threads.emplace_back(part, started);
+    } catch (...) {  // a thread that cannot start: its part runs here
+    }
+    for (int t = started; t < nt; ++t) part(t);
+    part(0);
+    for (std::thread &x : threads) x.join();
+    if (!bad) return MHS_OK;
+    return validate_host(n, m, nullptr, eptr32, evtx, demand, mark, 0, what);
 }
 
 struct Layout {  // byte offsets inside the arena for one instance
@@ -920,29 +959,58 @@ mhs_status mhs_load(int32_t n, int32_t m, const int32_t *edge_ptr, const int32_t
     if (!out) return fail(MHS_EINVAL, "out is NULL");
     *out = nullptr;
     if (!edge_ptr || (m > 0 && !demand)) return fail(MHS_EINVAL, "NULL input array");
-    if (m >= 0 && edge_ptr[0] != 0) return fail(MHS_EINVAL, "edge_ptr[0] must be 0");
-    std::vector<int32_t> mark;
+    if (n < 0 || m < 0) return fail(MHS_EINVAL, "instance: n and m must be >= 0");
+    if (n >= (1 << 24) || m >= (1 << 24))
+        return fail(MHS_EINVAL, "instance: n and m must be < 2^24 (exact FP32 counts)");
+    if (edge_ptr[0] != 0) return fail(MHS_EINVAL, "edge_ptr[0] must be 0");
+    // The pointer array first (O(m)): the copies below read edge_ptr[m]
+    // vertex ids, which a monotone array with edge_ptr[0] = 0 bounds.
+    for (int32_t e = 0; e < m; ++e)
+        if (edge_ptr[e + 1] < edge_ptr[e] || edge_ptr[e + 1] - edge_ptr[e] > (1 << 24)) {
+            std::vector<int32_t> mk;  // the standard message
+            mhs_status st = validate_host(n, m, nullptr, edge_ptr, edge_vtx, demand, mk, 0,
+                                          "instance");
+            return st ? st : fail(MHS_EINVAL, "instance: bad edge_ptr");
+        }
     if (m > 0 && edge_ptr[m] > 0 && !edge_vtx) return fail(MHS_EINVAL, "edge_vtx is NULL");
-    mhs_status st = validate_host(n, m, nullptr, edge_ptr, edge_vtx, demand, mark, 0, "instance");
-    if (st) return st;
     int64_t nnz = edge_ptr[m];
     std::vector<Layout> lay;
     int64_t tmoff = 0;
     mhs_instance *h = nullptr;
-    st = create(1, &n, &m, &nnz, &k, opt, cuda_stream, &h, lay, tmoff);
+    mhs_status st = create(1, &n, &m, &nnz, &k, opt, cuda_stream, &h, lay, tmoff);
     if (st) return st;
+    // The inputs go to the device (through pinned staging when it is
+    // available) while the host validates them; no kernel reads them before
+    // the validation has passed.
     const InstState &s = h->hstate[0];
-    cudaError_t e = cudaMemcpyAsync(const_cast<int32_t *>(s.eptr), edge_ptr, 4 * ((size_t)m + 1),
+    const size_t b_ptr = 4 * ((size_t)m + 1), b_vtx = 4 * (size_t)nnz, b_f = 4 * (size_t)m;
+    // (a buffer of its own: nothing else writes it while the copies run)
+    h->in_stage = static_cast<uint8_t *>(pinned_take(b_ptr + b_vtx + b_f, &h->in_stage_cls));
+    const void *src_ptr = edge_ptr, *src_vtx = edge_vtx, *src_f = demand;
+    if (uint8_t *in = h->in_stage) {
+        std::memcpy(in, edge_ptr, b_ptr);
+        if (b_vtx) std::memcpy(in + b_ptr, edge_vtx, b_vtx);
+        if (b_f) std::memcpy(in + b_ptr + b_vtx, demand, b_f);
+        src_ptr = in;
+        src_vtx = in + b_ptr;
+        src_f = in + b_ptr + b_vtx;
+    }
+    cudaError_t e = cudaMemcpyAsync(const_cast<int32_t *>(s.eptr), src_ptr, b_ptr,
                                     cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess && nnz > 0)
-        e = cudaMemcpyAsync(const_cast<int32_t *>(s.evtx), edge_vtx, 4 * (size_t)nnz,
-                            cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess && m > 0)
-        e = cudaMemcpyAsync(const_cast<int32_t *>(s.f), demand, 4 * (size_t)m,
-                            cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess && b_vtx)
+        e = cudaMemcpyAsync(const_cast<int32_t *>(s.evtx), src_vtx, b_vtx, cudaMemcpyHostToDevice,
+                            h->stream);
+    if (e == cudaSuccess && b_f)
+        e = cudaMemcpyAsync(const_cast<int32_t *>(s.f), src_f, b_f, cudaMemcpyHostToDevice,
+                            h->stream);
     if (e != cudaSuccess) {
         destroy(h);
         return fail(MHS_ECUDA, "input copy failed: %s", cudaGetErrorString(e));
+    }
+    st = validate_host_parallel(n, m, edge_ptr, edge_vtx, demand, nnz, "instance");
+    if (st) {
+        destroy(h);  // (waits for the copies)
+        return st;
     }
     st = finish_load(h, tmoff);
     if (st == MHS_OK && cudaStreamSynchronize(h->stream) != cudaSuccess)
@@ -1026,28 +1094,71 @@ mhs_status mhs_load_batch(int32_t count, const int32_t *n, const int32_t *m,
     }
     if (edge_ptr[0] != 0) return fail(MHS_EINVAL, "edge_ptr[0] must be 0");
     if (eoff[count] > 0 && !demand) return fail(MHS_EINVAL, "demand is NULL");
-    std::vector<int32_t> mark;
-    int32_t tag = 0;
     for (int b = 0; b < count; ++b) {
         const int64_t e0 = eoff[b];
         nnz[b] = edge_ptr[e0 + m[b]] - edge_ptr[e0];
         if (nnz[b] > 0 && !edge_vtx) return fail(MHS_EINVAL, "edge_vtx is NULL");
+        if (n[b] < 0) return fail(MHS_EINVAL, "instance %d: n < 0", b);
+        if (n[b] >= (1 << 24) || m[b] >= (1 << 24))
+            return fail(MHS_EINVAL, "instance %d: n and m must be < 2^24 (exact FP32 counts)", b);
+        if (nnz[b] < 0 || nnz[b] >= (1ll << 31))
+            return fail(MHS_EINVAL, "instance %d: bad edge_ptr range", b);
+    }
+    // Every instance is validated against the global pointer array (vertex
+    // ids local) on several threads for a large batch, while this thread
+    // allocates and copies the inputs; no kernel reads them before the
+    // validation has passed.  The lowest failing instance is validated again
+    // here for its message.
+    auto check = [&](int b, std::vector<int32_t> &mark) {
         char what[64];
         std::snprintf(what, sizeof(what), "instance %d", b);
-        // validate against the global pointer array, vertex ids local
-        if (n[b] < 0) return fail(MHS_EINVAL, "%s: n < 0", what);
         if ((size_t)n[b] > mark.size()) mark.resize((size_t)n[b], -1);
         std::fill(mark.begin(), mark.begin() + n[b], -1);
-        mhs_status st = validate_host(n[b], m[b], edge_ptr + e0, nullptr, edge_vtx, demand + e0,
-                                      mark, tag, what);
-        if (st) return st;
-        if (nnz[b] >= (1ll << 31)) return fail(MHS_EINVAL, "%s: too many incidences", what);
+        return validate_host(n[b], m[b], edge_ptr + eoff[b], nullptr, edge_vtx, demand + eoff[b],
+                             mark, 0, what, /*quiet=*/true);
+    };
+    const int nt = count >= 64 ? 8 : 1;
+    std::atomic<int> first_bad{count};
+    auto share = [&](int t) {
+        std::vector<int32_t> mark;
+        for (int b = t; b < count && b < first_bad.load(); b += nt)
+            if (check(b, mark)) {
+                int cur = first_bad.load();
+                while (b < cur && !first_bad.compare_exchange_weak(cur, b)) {
+                }
+            }
+    };
+    std::vector<std::thread> threads;
+    int started = 1;
+    try {
+        for (; started < nt; ++started) threads.emplace_back(share, started);
+    } catch (...) {  // a thread that cannot start: its share runs here, below
     }
+    // joins the checks; the lowest malformed instance's message, else MHS_OK
+    auto finish_checks = [&]() {
+        for (int t = started; t < nt; ++t) share(t);
+        share(0);
+        for (std::thread &x : threads) x.join();
+        threads.clear();
+        const int bad = first_bad.load();
+        if (bad >= count) return MHS_OK;
+        std::vector<int32_t> mark((size_t)std::max(n[bad], 1), -1);
+        char what[64];
+        std::snprintf(what, sizeof(what), "instance %d", bad);
+        mhs_status st = validate_host(n[bad], m[bad], edge_ptr + eoff[bad], nullptr, edge_vtx,
+                                      demand + eoff[bad], mark, 0, what);
+        return st ? st : fail(MHS_EINVAL, "%s: malformed", what);
+    };
     std::vector<Layout> lay;
     int64_t tmoff = 0;
     mhs_instance *h = nullptr;
     mhs_status st = create(count, n, m, nnz.data(), k, opt, cuda_stream, &h, lay, tmoff);
-    if (st) return st;
+    if (st) {  // a malformed input is reported first, as a check before the allocation would
+        const std::string msg = g_err;
+        const mhs_status vst = finish_checks();
+        if (vst) return vst;
+        return fail(st, "%s", msg.c_str());
+    }
     // one copy per input array: local int32 offsets, vertex ids, demands
     std::vector<int32_t> local_ptr((size_t)h->sum_m1);
     {
@@ -1067,6 +1178,11 @@ mhs_status mhs_load_batch(int32_t count, const int32_t *n, const int32_t *m,
         e = cudaMemcpyAsync(h->arena + h->in_f, demand, 4 * (size_t)h->sum_m,
                             cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);  // local_ptr is pageable
+    st = finish_checks();
+    if (st) {
+        destroy(h);
+        return st;
+    }
     if (e != cudaSuccess) {
         destroy(h);
         return fail(MHS_ECUDA, "input copy failed: %s", cudaGetErrorString(e));

@@ -97,3 +97,40 @@ def test_noalloc_argument_errors_on_host(libpath):
     assert L.mhs_kernelize_noalloc(-1, 0, dummy, dummy, dummy, 0, dummy, dummy, None, None,
                                    small, 1) == mhs.MHS_EINVAL
     assert small.value == b""
+
+
+def test_batch_host_validation_names_the_lowest_bad_instance(libpath):
+    """mhs_load_batch validates a large batch on several host threads before
+    any CUDA call; the error names the lowest malformed instance, with the
+    same message a single-threaded check gives."""
+    import numpy as np
+
+    from paper_2109_06042_gb300 import instances as I
+    from paper_2109_06042_gb300 import mhs
+
+    insts = [I.tiny_random(9000 + i, nmax=24, mmax=16) for i in range(100)]
+
+    def first_pair_edge(inst):  # a hyperedge of at least two vertices
+        for e in range(inst.m):
+            if inst.edge_ptr[e + 1] - inst.edge_ptr[e] >= 2:
+                return e
+        raise AssertionError("no hyperedge of two vertices")
+
+    def expect(fragments):
+        with pytest.raises(mhs.MhsError) as ei:
+            mhs.Instance.load_batch(insts)
+        assert ei.value.status == mhs.MHS_EINVAL
+        for frag in fragments:
+            assert frag in str(ei.value), str(ei.value)
+
+    e70 = first_pair_edge(insts[70])
+    p = int(insts[70].edge_ptr[e70])
+    kept = insts[70].edge_vtx.copy()
+    insts[70].edge_vtx[p + 1] = insts[70].edge_vtx[p]  # a vertex listed twice
+    insts[90].edge_vtx[0] = insts[90].n  # a vertex id out of range
+    expect(["instance 70:", "twice"])
+    insts[70].edge_vtx[:] = kept
+    expect(["instance 90:", "outside"])
+    insts[5].demand[0] = 0
+    expect(["instance 5:", "demand"])
+    assert np.all(insts[5].demand[1:] >= 1)

@@ -237,6 +237,40 @@ def test_invalid_inputs_rejected(mhs):
     assert ei.value.status == mhs.MHS_EINVAL
 
 
+def test_invalid_large_instance_rejected(mhs):
+    """Above 128k incidences the host checks run on several threads while the
+    inputs are copied to the device; an error anywhere is still found, with
+    the single-threaded check's message, and a valid load afterwards works."""
+    base = I.config_powerlaw(0)  # 160k incidences
+    assert base.nnz >= 1 << 17
+
+    def variant(edit):
+        ptr, vtx, dem = base.edge_ptr.copy(), base.edge_vtx.copy(), base.demand.copy()
+        edit(ptr, vtx, dem)
+        return I.Instance(n=base.n, m=base.m, edge_ptr=ptr, edge_vtx=vtx, demand=dem, k=base.k)
+
+    last = int(base.m) - 1
+    wide = next(e for e in range(last, 0, -1) if base.edge_ptr[e + 1] - base.edge_ptr[e] >= 2)
+
+    def dup(ptr, vtx, dem):
+        vtx[ptr[wide] + 1] = vtx[ptr[wide]]
+
+    def decrease(ptr, vtx, dem):  # hyperedge m/2 ends before it starts (the first error)
+        ptr[base.m // 2 + 1] = ptr[base.m // 2] - 1
+
+    cases = [(lambda p, v, d: v.__setitem__(-1, base.n), "outside"),
+             (dup, "twice"),
+             (lambda p, v, d: d.__setitem__(last, 0), "demand"),
+             (decrease, "decreases")]
+    for edit, frag in cases:
+        with pytest.raises(mhs.MhsError) as ei:
+            mhs.Instance.load(variant(edit), contraction="fp8")
+        assert ei.value.status == mhs.MHS_EINVAL and frag in str(ei.value), str(ei.value)
+    with mhs.Instance.load(base, contraction="fp8") as h:
+        st = h.kernelize()
+    assert st["rounds"] >= 2 and st["m_alive"] < base.m
+
+
 def test_deterministic_repeats(mhs):
     inst = I.config_powerlaw(1, n=4000, m=8000)
     first = mhs.kernelize(inst)
