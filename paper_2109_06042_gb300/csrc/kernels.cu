@@ -570,24 +570,37 @@ __global__ void __launch_bounds__(256) k_scatter(InstState *st, const Plan *plan
 constexpr int kSecWarps = 4;          // warps per block
 constexpr int kSecTab = 512;          // table entries per warp (a power of two)
 constexpr int kSecTabLog = 9;
-constexpr uint32_t kSecEmpty = 0xffffffffu;
 
+// One entry per sector: key << 32 | byte mask (bit b: byte b is 1.0).
 struct SecTable {
-    uint32_t key[kSecTab];
-    uint32_t mask[kSecTab];  // bit b: byte b of the sector is 1.0
-    int32_t aux[kSecTab];    // A^T: maximum demand over the sector's hyperedges
+    unsigned long long e[kSecTab];
 };
+constexpr unsigned long long kSecFree = ~0ull;
 
-// Slot of `key` in the table, inserting it if absent; kSecTab if the table
-// is full (callers insert at most kSecTab keys, so it never is).
-__device__ __forceinline__ int sec_slot(SecTable &t, uint32_t key) {
+// Sets `bit` in the entry of `key`, inserting the key if absent: one shared
+// atomic in the common cases (the key present: an OR; its slot free: a
+// compare-and-swap).  False if the table is full (callers insert at most
+// kSecTab keys, so it never is).
+__device__ __forceinline__ bool sec_set(SecTable &t, uint32_t key, uint32_t bit) {
     uint32_t h = (key * 2654435761u) >> (32 - kSecTabLog);
+    const unsigned long long mine = (unsigned long long)key << 32;
     for (int p = 0; p < kSecTab; ++p) {
-        const uint32_t old = atomicCAS(&t.key[h], kSecEmpty, key);
-        if (old == kSecEmpty || old == key) return (int)h;
+        const unsigned long long cur = *reinterpret_cast<volatile unsigned long long *>(&t.e[h]);
+        if (cur != kSecFree && (cur >> 32) == key) {
+            atomicOr(&t.e[h], (unsigned long long)bit);
+            return true;
+        }
+        if (cur == kSecFree) {
+            const unsigned long long old = atomicCAS(&t.e[h], kSecFree, mine | bit);
+            if (old == kSecFree) return true;
+            if ((old >> 32) == key) {
+                atomicOr(&t.e[h], (unsigned long long)bit);
+                return true;
+            }
+        }
         h = (h + 1) & (kSecTab - 1);
     }
-    return kSecTab;
+    return false;
 }
 
 // Four mask bits -> four bytes of 0 or 1.0 (bit i -> byte i).
@@ -681,25 +694,21 @@ __device__ __forceinline__ void walk_live(const InstState &s, int lane, int32_t 
     }
 }
 
-// Empties the table entries the warp has written: fn(key, mask, aux) writes
-// an entry's sector and returns, through *ow / *ob, the occupancy word and
-// bit it sets.  The lanes of one pass over 32 slots set each distinct word
-// with one atomic.
+// Empties the table entries the warp has written: fn(key, mask) writes an
+// entry's sector and returns, through *ow / *ob, the occupancy word and bit
+// it sets.  The lanes of one pass over 32 slots set each distinct word with
+// one atomic.
 template <typename F>
 __device__ __forceinline__ void drain_table(SecTable &t, int lane, F &&fn) {
     __syncwarp();
     for (int base = 0; base < kSecTab; base += 32) {
         const int i = base + lane;
-        const uint32_t key = t.key[i];
+        const unsigned long long ent = t.e[i];
         uint32_t *ow = nullptr;
         uint32_t ob = 0;
-        if (key != kSecEmpty) {
-            const uint32_t m = t.mask[i];
-            const int32_t aux = t.aux[i];
-            t.key[i] = kSecEmpty;
-            t.mask[i] = 0;
-            t.aux[i] = 0;
-            fn(key, m, aux, &ow, &ob);
+        if (ent != kSecFree) {
+            t.e[i] = kSecFree;
+            fn((uint32_t)(ent >> 32), (uint32_t)ent, &ow, &ob);
         }
         const unsigned grp = __match_any_sync(0xffffffffu, (unsigned long long)(uintptr_t)ow);
         const uint32_t bits = __reduce_or_sync(grp, ob);
@@ -709,11 +718,7 @@ __device__ __forceinline__ void drain_table(SecTable &t, int lane, F &&fn) {
 }
 
 __device__ __forceinline__ void init_table(SecTable &t, int lane) {
-    for (int i = lane; i < kSecTab; i += 32) {
-        t.key[i] = kSecEmpty;
-        t.mask[i] = 0;
-        t.aux[i] = 0;
-    }
+    for (int i = lane; i < kSecTab; i += 32) t.e[i] = kSecFree;
     __syncwarp();
 }
 
@@ -759,9 +764,8 @@ __global__ void __launch_bounds__(32 * kSecWarps) k_set_a_tc(InstState *st, cons
         walk_live(s, lane, p0, start, tot, 0, [&](int r, int32_t cv, int32_t) {
             if (cv >= K) { atomicOr(&s.status, kErrCapacity); return; }
             if (table) {
-                const int slot = sec_slot(t, ((uint32_t)r << 26) | (uint32_t)(cv >> 5));
-                if (slot < kSecTab) atomicOr(&t.mask[slot], 1u << (cv & 31));
-                else atomicOr(&s.status, kErrCapacity);
+                if (!sec_set(t, ((uint32_t)r << 26) | (uint32_t)(cv >> 5), 1u << (cv & 31)))
+                    atomicOr(&s.status, kErrCapacity);
             } else {
                 const int32_t rr = ce0 + r;
                 if (set_byte(A + (int64_t)rr * pitch, cv)) atomicAdd(&wfresh[wib][r], 1);
@@ -769,8 +773,7 @@ __global__ void __launch_bounds__(32 * kSecWarps) k_set_a_tc(InstState *st, cons
             }
         });
         if (table) {
-            drain_table(t, lane, [&](uint32_t key, uint32_t m, int32_t, uint32_t **ow,
-                                     uint32_t *ob) {
+            drain_table(t, lane, [&](uint32_t key, uint32_t m, uint32_t **ow, uint32_t *ob) {
                 const int r = (int)(key >> 26);
                 const int32_t c0 = (int32_t)(key & 0x3ffffffu) * 32;
                 const int32_t rr = ce0 + r;
@@ -806,6 +809,7 @@ __global__ void __launch_bounds__(32 * kSecWarps) k_set_a_tc(InstState *st, cons
 //      and the occupancy bits of A^T.
 __global__ void __launch_bounds__(32 * kSecWarps) k_set_md_tc(InstState *st, const Plan *plan) {
     __shared__ SecTable tab[kSecWarps];
+    __shared__ int32_t wdem[kSecWarps][32];  // demands of the group's hyperedges
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     SecTable &t = tab[wib];
     init_table(t, lane);
@@ -851,6 +855,8 @@ __global__ void __launch_bounds__(32 * kSecWarps) k_set_md_tc(InstState *st, con
             int32_t start;
             const int32_t tot = rows_prefix(lane, len, &start);
             const bool table = tot <= kSecTab;
+            wdem[wib][lane] = fe;
+            __syncwarp();
             uint8_t *const At = s.At;
             const int64_t pitch = s.At_pitch;
             int32_t *const deg = s.v_deg;
@@ -858,13 +864,7 @@ __global__ void __launch_bounds__(32 * kSecWarps) k_set_md_tc(InstState *st, con
             walk_live(s, lane, p0, start, tot, fe, [&](int r, int32_t cv, int32_t rfe) {
                 if (cv >= n) { atomicOr(&s.status, kErrCapacity); return; }
                 if (table) {
-                    const int slot = sec_slot(t, (uint32_t)cv);
-                    if (slot < kSecTab) {
-                        atomicOr(&t.mask[slot], 1u << r);
-                        atomicMax(&t.aux[slot], rfe);
-                    } else {
-                        atomicOr(&s.status, kErrCapacity);
-                    }
+                    if (!sec_set(t, (uint32_t)cv, 1u << r)) atomicOr(&s.status, kErrCapacity);
                 } else {
                     if (set_byte(At + (int64_t)cv * pitch, c0 + r)) {
                         atomicAdd(&deg[cv], 1);
@@ -874,8 +874,10 @@ __global__ void __launch_bounds__(32 * kSecWarps) k_set_md_tc(InstState *st, con
                 }
             });
             if (table) {
-                drain_table(t, lane, [&](uint32_t cv, uint32_t m, int32_t mf, uint32_t **ow,
-                                         uint32_t *ob) {
+                drain_table(t, lane, [&](uint32_t cv, uint32_t m, uint32_t **ow, uint32_t *ob) {
+                    int32_t mf = 0;  // the largest demand among the sector's hyperedges
+                    for (uint32_t bits = m; bits; bits &= bits - 1)
+                        mf = max(mf, wdem[wib][__ffs(bits) - 1]);
                     store_sector(At + (int64_t)cv * pitch + c0, m);
                     atomicAdd(&deg[cv], __popc(m));
                     atomicMax(&maxf[cv], mf);
@@ -1398,11 +1400,11 @@ cudaError_t launch_build(InstState *st, int count, int32_t max_rounds, int64_t m
 template <int kPhase>
 static void launch_scatter(InstState *st, const Plan *plan, bool set, bool dense, int sms,
                            cudaStream_t s) {
-    if (dense) {
-        const int grid = grid_for(sms, 8);
+    if (dense) {  // 12 blocks of 4 warps per SM (17 KB of tables each), 16 for the clear
+        const int grid = grid_for(sms, 12);
         if (kPhase == 0) k_set_a_tc<<<grid, 32 * kSecWarps, 0, s>>>(st, plan);
         else if (set) k_set_md_tc<<<grid, 32 * kSecWarps, 0, s>>>(st, plan);
-        else k_clear_at_tc<<<2 * grid, 32 * kSecWarps, 0, s>>>(st, plan);
+        else k_clear_at_tc<<<grid_for(sms, 16), 32 * kSecWarps, 0, s>>>(st, plan);
         return;
     }
     const int grid = grid_for(sms, 8);
