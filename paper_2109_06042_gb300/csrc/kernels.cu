@@ -1400,10 +1400,11 @@ cudaError_t launch_build(InstState *st, int count, int32_t max_rounds, int64_t m
 template <int kPhase>
 static void launch_scatter(InstState *st, const Plan *plan, bool set, bool dense, int sms,
                            cudaStream_t s) {
-    if (dense) {  // 12 blocks of 4 warps per SM (17 KB of tables each), 16 for the clear
-        const int grid = grid_for(sms, 12);
-        if (kPhase == 0) k_set_a_tc<<<grid, 32 * kSecWarps, 0, s>>>(st, plan);
-        else if (set) k_set_md_tc<<<grid, 32 * kSecWarps, 0, s>>>(st, plan);
+    if (dense) {  // blocks of 4 warps (17 KB of tables each): per SM 8 for the A set
+                  // pass (its row-local sector writes lose with more), 12 for the MD
+                  // set pass, 16 for the clear (measured)
+        if (kPhase == 0) k_set_a_tc<<<grid_for(sms, 8), 32 * kSecWarps, 0, s>>>(st, plan);
+        else if (set) k_set_md_tc<<<grid_for(sms, 12), 32 * kSecWarps, 0, s>>>(st, plan);
         else k_clear_at_tc<<<grid_for(sms, 16), 32 * kSecWarps, 0, s>>>(st, plan);
         return;
     }
