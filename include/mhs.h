@@ -391,12 +391,15 @@ mhs_status mhs_kernelize_noalloc(int32_t n, int32_t m, const int32_t *edge_ptr,
 /* Serving: continuous batching of independent requests on one GPU.          */
 /*                                                                          */
 /* The paper reduces one instance at a time; the server keeps many in      */
-/* flight.  A worker thread admits queued requests into free slots while   */
-/* their device footprint fits the HBM budget, runs one round of           */
-/* Algorithm 3 for all admitted instances at once (one captured CUDA graph */
-/* over the slot table), retires the instances that reached their          */
-/* fixpoint and admits new ones at every round boundary.  Each result is   */
-/* exactly what mhs_kernelize gives for the instance alone.                */
+/* flight.  The request loop runs on the device: one CUDA graph per lane   */
+/* whose conditional WHILE node repeats admission of the slots the host    */
+/* has loaded, one round of Algorithm 3 for all live slots at once, and    */
+/* retirement of the instances that reached their fixpoint (published in   */
+/* host-mapped memory), with no host step between rounds.  A host thread   */
+/* per lane admits queued requests by HBM footprint, loads them into free  */
+/* slots beside the running loop, copies finished results out and starts   */
+/* the loop again when it has gone idle.  Each result is exactly what      */
+/* mhs_kernelize gives for the instance alone.                             */
 /* ------------------------------------------------------------------------ */
 
 typedef struct mhs_server mhs_server;

@@ -1319,6 +1319,96 @@ __global__ void k_alive_masks(const InstState *st, int count, bool batch, uint8_
     }
 }
 
+// ---- serving loop (device-resident; see server.cpp) ----
+
+// One block per slot at a time.  The ready flag is read once per slot (by
+// thread 0): the host may set it while this kernel runs.
+__global__ void k_server_admit(InstState *live, const InstState *staged, volatile int32_t *ready,
+                               int count) {
+    __shared__ int32_t go;
+    constexpr int kWords = (int)(sizeof(InstState) / 4);
+    static_assert(sizeof(InstState) % 4 == 0, "state copied in words");
+    for (int si = blockIdx.x; si < count; si += gridDim.x) {
+        if (threadIdx.x == 0) go = ready[si];
+        __syncthreads();
+        if (go) {
+            const int32_t *src = reinterpret_cast<const int32_t *>(staged + si);
+            int32_t *dst = reinterpret_cast<int32_t *>(live + si);
+            for (int w = threadIdx.x; w < kWords; w += blockDim.x) dst[w] = src[w];
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                __threadfence();
+                ready[si] = 0;
+                __threadfence_system();
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// One block.  A slot is retired once: a finished instance is inactive (and
+// its live slot zeroed here), a failed one is taken while still active.
+__global__ void __launch_bounds__(256) k_server_retire(InstState *live, InstState *out,
+                                                       const int32_t *done,
+                                                       const BatchCounters *ctr,
+                                                       volatile int32_t *ring,
+                                                       volatile ServerFlags *flags,
+                                                       ServerDev *dev, int count) {
+    __shared__ int32_t fin[4096];  // max_slots <= 4096
+    __shared__ int32_t nfin;
+    constexpr int kWords = (int)(sizeof(InstState) / 4);
+    if (threadIdx.x == 0) nfin = 0;
+    __syncthreads();
+    const int nd = min(ctr->n_done, count);
+    for (int i = threadIdx.x; i < nd; i += blockDim.x) {
+        const int si = done[i];
+        if (si >= 0 && si < count) fin[atomicAdd(&nfin, 1) & 4095] = si;
+    }
+    for (int si = threadIdx.x; si < count; si += blockDim.x)
+        if (live[si].active && live[si].status) fin[atomicAdd(&nfin, 1) & 4095] = si;
+    __syncthreads();
+    const int nf = min(nfin, count);  // each slot at most once
+    for (int i = 0; i < nf; ++i) {
+        const int si = fin[i];
+        int32_t *src = reinterpret_cast<int32_t *>(live + si);
+        int32_t *dst = reinterpret_cast<int32_t *>(out + si);
+        for (int w = threadIdx.x; w < kWords; w += blockDim.x) dst[w] = src[w];
+        __syncthreads();
+        for (int w = threadIdx.x; w < kWords; w += blockDim.x) src[w] = 0;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && nf > 0) {
+        __threadfence_system();  // the states in `out` before the ring entries
+        const int32_t head = dev->head;
+        for (int i = 0; i < nf; ++i) ring[(head + i) % count] = fin[i];
+        __threadfence_system();  // the entries before the head
+        dev->head = head + nf;
+        flags->head = head + nf;
+        __threadfence_system();
+    }
+}
+
+__global__ void k_server_cond(cudaGraphConditionalHandle h, const BatchCounters *ctr,
+                              const int32_t *kerr, const Plan *plan, ServerDev *dev,
+                              volatile ServerFlags *flags, volatile const int32_t *ready,
+                              int count, int32_t cap) {
+    __shared__ int32_t pending;
+    if (threadIdx.x == 0) pending = 0;
+    __syncthreads();
+    for (int si = threadIdx.x; si < count; si += blockDim.x)
+        if (ready[si]) pending = 1;
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    if (plan->any_active) dev->rounds += 1;
+    const int32_t it = ++dev->iters;
+    const int32_t err = *kerr;
+    flags->rounds = dev->rounds;
+    flags->kerr = err;
+    __threadfence_system();
+    const bool go = !flags->stop && err == 0 && it < cap && (ctr->active > 0 || pending);
+    cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
 __global__ void k_loop_cond(cudaGraphConditionalHandle h, BatchCounters *ctr, int32_t *kerr,
                             int32_t round_cap) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -1338,6 +1428,28 @@ __global__ void k_loop_cond(cudaGraphConditionalHandle h, BatchCounters *ctr, in
 cudaError_t launch_loop_cond(cudaGraphConditionalHandle h, BatchCounters *ctr, int32_t *kerr,
                              int32_t round_cap, cudaStream_t s) {
     k_loop_cond<<<1, 32, 0, s>>>(h, ctr, kerr, round_cap);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_server_admit(InstState *live, const InstState *staged, int32_t *ready,
+                                int count, cudaStream_t s) {
+    k_server_admit<<<count < 152 ? count : 152, 128, 0, s>>>(live, staged, ready, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_server_retire(InstState *live, InstState *out, const int32_t *done,
+                                 const BatchCounters *ctr, int32_t *ring, ServerFlags *flags,
+                                 ServerDev *dev, int count, cudaStream_t s) {
+    if (count > 4096) return cudaErrorInvalidValue;  // one block lists the retirements
+    k_server_retire<<<1, 256, 0, s>>>(live, out, done, ctr, ring, flags, dev, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_server_cond(cudaGraphConditionalHandle h, const BatchCounters *ctr,
+                               const int32_t *kerr, const Plan *plan, ServerDev *dev,
+                               ServerFlags *flags, const int32_t *ready, int count, int32_t cap,
+                               cudaStream_t s) {
+    k_server_cond<<<1, 256, 0, s>>>(h, ctr, kerr, plan, dev, flags, ready, count, cap);
     return cudaGetLastError();
 }
 

@@ -73,6 +73,41 @@ cudaError_t launch_full_edges(InstState *st, int count, BatchCounters *ctr, int3
                               int sms, cudaStream_t s);
 cudaError_t launch_alive_masks(const InstState *st, uint8_t *alive_v, uint8_t *alive_e,
                                cudaStream_t s);
+
+// ---- serving: the device-resident request loop (server.cpp) ----
+// Host-mapped page-locked words shared by a lane's loop and its host thread.
+struct ServerFlags {
+    int32_t stop;      // host -> device: end the loop at its next round boundary
+    int32_t kerr;      // device -> host: the loop's error bits
+    int32_t head;      // device -> host: slot indices published in `ring` so far
+    int32_t pad_;
+    long long rounds;  // device -> host: rounds run over the lane's slot table
+};
+// Device-side bookkeeping of a lane's loop.
+struct ServerDev {
+    int32_t head;      // slot indices published so far
+    int32_t iters;     // iterations of the current launch
+    long long rounds;
+};
+// Start of an iteration: every slot whose host-mapped ready flag is set
+// enters the live table (its staged state, which the host has loaded and
+// built, is copied in whole) and the flag is cleared.
+cudaError_t launch_server_admit(InstState *live, const InstState *staged, int32_t *ready,
+                                int count, cudaStream_t s);
+// End of a round: the slots whose instance finished (done list) or failed
+// (status bits) leave the live table: the state goes to `out` for the host,
+// the live slot is zeroed, and the slot index is published in the
+// host-mapped ring (capacity `count`) before `flags->head` advances.
+cudaError_t launch_server_retire(InstState *live, InstState *out, const int32_t *done,
+                                 const BatchCounters *ctr, int32_t *ring, ServerFlags *flags,
+                                 ServerDev *dev, int count, cudaStream_t s);
+// Loop condition: go on while the host has not asked to stop, no error was
+// raised, fewer than `cap` iterations ran in this launch, and some slot is
+// active or ready to enter.
+cudaError_t launch_server_cond(cudaGraphConditionalHandle h, const BatchCounters *ctr,
+                               const int32_t *kerr, const Plan *plan, ServerDev *dev,
+                               ServerFlags *flags, const int32_t *ready, int count, int32_t cap,
+                               cudaStream_t s);
 cudaError_t launch_alive_masks_batch(const InstState *st, int count, uint8_t *alive_v,
                                      uint8_t *alive_e, cudaStream_t s);
 

@@ -1,17 +1,22 @@
 // server.cpp -- continuous-batching server: mhs_server_create / mhs_submit /
 // mhs_poll / mhs_server_destroy.
 //
-// A worker thread owns the GPU side.  Each iteration of its loop:
-//   1. admits pending requests into free slots while their device
-//      footprint fits the HBM budget (each admitted request gets its own
-//      arena from the library's memory pool, its inputs uploaded and its
-//      state written into the slot table);
-//   2. runs ONE round of Algorithm 3 (DP then MD) for every busy slot at
-//      once, by replaying a CUDA graph captured over the whole slot table;
-//   3. retires the slots whose instance reached its fixpoint in that round
-//      (the round kernels append them to a device-side done list): copies
-//      their results to the host, returns their arenas to the pool and
-//      wakes the pollers.
+// The request loop runs on the device.  Each lane's loop is one CUDA graph
+// whose conditional WHILE node repeats, with no host step in between:
+//   1. admission: every slot whose (host-mapped) ready flag is set enters
+//      the live slot table;
+//   2. ONE round of Algorithm 3 (DP then MD) for every live slot at once;
+//   3. retirement: the slots whose instance reached its fixpoint (or
+//      failed) leave the live table, their state is kept for the host and
+//      their index is published in a host-mapped ring;
+// until the host asks it to stop or no slot is live or ready, when the
+// graph ends and the host launches it again once there is work.
+// The lane's host thread only moves data: it loads each admitted request
+// into a free slot's arena on a stream of its own (inputs, tensor maps, the
+// build kernels, the staged state), waits for that to finish and then sets
+// the slot's ready flag; it takes the slots published in the ring, copies
+// their results out, returns their arenas to the pool and wakes the pollers.
+// Admission is by HBM footprint, at the host, before a request is loaded.
 // Requests that arrive while others are on the GPU join at the next round
 // boundary, so work of different sizes overlaps in the same launches.
 // Requests are split by size into two lanes, each with its own slot table,
@@ -26,6 +31,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -50,6 +56,9 @@ inline int64_t kbytes(int64_t K) { return up(K > 0 ? K : 1, kTcK); }
 inline int64_t kwords(int64_t K) { return up(((K + 31) / 32) > 0 ? (K + 31) / 32 : 1, 4); }
 inline int64_t occ_words(int64_t K) { return (kbytes(K) / kOccK + 31) / 32; }
 constexpr int64_t kServerListCap = 16 << 20;  // tile-list entries shared by the slots
+// Iterations of one launch of a lane's loop at most (it also ends when idle);
+// the host launches it again while there is work.
+constexpr int32_t kLoopIters = 1 << 16;
 inline int64_t now_ns() {
     return std::chrono::duration_cast<std::chrono::nanoseconds>(
                std::chrono::steady_clock::now().time_since_epoch())
@@ -138,19 +147,28 @@ struct Slot {
 struct Lane {
     int id = 0;
     mhs_server *S = nullptr;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;  // the loop
     bool own_stream = false;
+    cudaStream_t load = nullptr;    // uploads and result copies, beside the loop
     int32_t slots_n = 0;
-    // device slot table and round bookkeeping (one allocation)
+    // device slot table and loop bookkeeping (one allocation)
     uint8_t *ctl = nullptr;
-    InstState *dstate = nullptr;
+    InstState *dstate = nullptr;    // the live slot table (written by the loop only)
+    InstState *dstage = nullptr;    // states the host has loaded, before they enter
+    InstState *dout = nullptr;      // states of retired slots, for the host
     Plan *dplan = nullptr;
     BatchCounters *dctr = nullptr;
+    ServerDev *ddev = nullptr;
     int32_t *dkerr = nullptr, *ddone = nullptr;
-    BatchCounters *hctr = nullptr;  // pinned
-    int32_t *hkerr = nullptr, *hdone = nullptr;
+    // host-mapped page-locked block: flags, ready[slots], ring[slots]
+    uint8_t *mapped = nullptr;
+    ServerFlags *hflags = nullptr, *dflags = nullptr;
+    int32_t *hready = nullptr, *dready = nullptr;
+    int32_t *hring = nullptr, *dring = nullptr;
+    int32_t consumed = 0;           // ring entries taken by the host
+    bool running = false;           // a launch of the loop may still run
     uint8_t *hmaps = nullptr;       // pinned: 2 tensor maps per slot, staged for upload
-    InstState *hstates = nullptr;   // pinned: states of the slots retired in a round
+    InstState *hstates = nullptr;   // pinned: states of the slots retired at once
     cudaGraphExec_t graph = nullptr;
     int64_t list_cap = 0;
     std::vector<Slot> slots;                         // owned by the lane's worker
@@ -160,7 +178,6 @@ struct Lane {
     int64_t in_use_release = 0, tiles_release = 0;   // worker-local
     std::condition_variable cv_work;
     std::thread worker;
-    int64_t rounds = 0;
 };
 
 struct mhs_server {
@@ -192,7 +209,7 @@ mhs_status admit(Lane &Ln, int si, std::shared_ptr<Request> req) {
     Layout L = plan_layout(req->n, req->m, nnz, dense, fe);
     uint8_t *a = nullptr;
     cudaError_t e = cudaMallocFromPoolAsync(reinterpret_cast<void **>(&a), (size_t)L.bytes, S->pool,
-                                            Ln.stream);
+                                            Ln.load);
     if (e != cudaSuccess) return set_error(MHS_ENOMEM, "server: arena allocation failed");
     InstState s;
     std::memset(&s, 0, sizeof(s));
@@ -242,7 +259,7 @@ mhs_status admit(Lane &Ln, int si, std::shared_ptr<Request> req) {
         s.tmap_At = a + L.tmaps + tmap_bytes();
         if (!make_operand_tmap(maps, s.A, s.A_pitch, s.A_rows) ||
             !make_operand_tmap(maps + tmap_bytes(), s.At, s.At_pitch, s.At_rows)) {
-            cudaFreeAsync(a, Ln.stream);
+            cudaFreeAsync(a, Ln.load);
             return set_error(MHS_ECUDA, "server: tensor map encoding failed");
         }
     } else {
@@ -251,24 +268,25 @@ mhs_status admit(Lane &Ln, int si, std::shared_ptr<Request> req) {
         s.Ab_pitch = (int32_t)kwords(req->n);
         s.Atb_pitch = (int32_t)kwords(req->m);
     }
-    // pageable sources: each copy has staged its source when it returns
+    // On the load stream, into the slot's staged state (the loop takes it
+    // once the ready flag is set, after this work has finished).  Pageable
+    // sources: each copy has staged its source when it returns.
     e = cudaMemcpyAsync(a + L.eptr, req->ptr.data(), 4 * req->ptr.size(), cudaMemcpyHostToDevice,
-                        Ln.stream);
+                        Ln.load);
     if (e == cudaSuccess && nnz > 0)
         e = cudaMemcpyAsync(a + L.evtx, req->vtx.data(), 4 * (size_t)nnz, cudaMemcpyHostToDevice,
-                            Ln.stream);
+                            Ln.load);
     if (e == cudaSuccess && req->m > 0)
         e = cudaMemcpyAsync(a + L.f, req->dem.data(), 4 * (size_t)req->m, cudaMemcpyHostToDevice,
-                            Ln.stream);
+                            Ln.load);
     if (e == cudaSuccess && dense)
-        e = cudaMemcpyAsync(a + L.tmaps, maps, 2 * tmap_bytes(), cudaMemcpyHostToDevice,
-                            Ln.stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(a + L.dense, 0, (size_t)L.dense_bytes, Ln.stream);
+        e = cudaMemcpyAsync(a + L.tmaps, maps, 2 * tmap_bytes(), cudaMemcpyHostToDevice, Ln.load);
+    if (e == cudaSuccess) e = cudaMemsetAsync(a + L.dense, 0, (size_t)L.dense_bytes, Ln.load);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(Ln.dstate + si, &s, sizeof(s), cudaMemcpyHostToDevice, Ln.stream);
-    if (e == cudaSuccess) e = launch_build(Ln.dstate + si, 1, 0, nnz, req->m, req->n, Ln.stream);
+        e = cudaMemcpyAsync(Ln.dstage + si, &s, sizeof(s), cudaMemcpyHostToDevice, Ln.load);
+    if (e == cudaSuccess) e = launch_build(Ln.dstage + si, 1, 0, nnz, req->m, req->n, Ln.load);
     if (e != cudaSuccess) {
-        cudaFreeAsync(a, Ln.stream);
+        cudaFreeAsync(a, Ln.load);
         return set_error(MHS_ECUDA, "server: admission failed: %s", cudaGetErrorString(e));
     }
     Slot &sl = Ln.slots[si];
@@ -299,16 +317,18 @@ void fail_all_locked(mhs_server *S, mhs_status st) {
     }
 }
 
-// Copy the results of the slots that finished in the last round to their
-// requests and release the slots: two synchronisations for the whole set.
+// Copy the results of the slots the loop retired (their states are in
+// dout, the live slots already empty) to their requests and release the
+// slots: two synchronisations of the load stream for the whole set, while
+// the loop goes on.
 void retire(Lane &Ln, const std::vector<int> &fin) {
     if (fin.empty()) return;
     mhs_server *S = Ln.S;
     cudaError_t e = cudaSuccess;
     for (size_t i = 0; i < fin.size() && e == cudaSuccess; ++i)
-        e = cudaMemcpyAsync(Ln.hstates + i, Ln.dstate + fin[i], sizeof(InstState),
-                            cudaMemcpyDeviceToHost, Ln.stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(Ln.stream);
+        e = cudaMemcpyAsync(Ln.hstates + i, Ln.dout + fin[i], sizeof(InstState),
+                            cudaMemcpyDeviceToHost, Ln.load);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(Ln.load);
     std::vector<std::vector<uint8_t>> taken(S->opt.full_edges ? fin.size() : 0);
     for (size_t i = 0; i < fin.size() && e == cudaSuccess; ++i) {
         const InstState &s = Ln.hstates[i];
@@ -317,23 +337,21 @@ void retire(Lane &Ln, const std::vector<int> &fin) {
         r.eout.resize(s.m);
         if (s.n > 0)
             e = cudaMemcpyAsync(r.vout.data(), s.v_c2o, 4 * (size_t)s.n, cudaMemcpyDeviceToHost,
-                                Ln.stream);
+                                Ln.load);
         if (e == cudaSuccess && s.m > 0)
             e = cudaMemcpyAsync(r.eout.data(), s.e_c2o, 4 * (size_t)s.m, cudaMemcpyDeviceToHost,
-                                Ln.stream);
+                                Ln.load);
         if (S->opt.full_edges) {  // FE lowered demands and took vertices
             if (e == cudaSuccess && s.m0 > 0)
                 e = cudaMemcpyAsync(r.dem.data(), s.f, 4 * (size_t)s.m0, cudaMemcpyDeviceToHost,
-                                    Ln.stream);
+                                    Ln.load);
             taken[i].resize(s.n0);
             if (e == cudaSuccess && s.n0 > 0 && s.forced)
                 e = cudaMemcpyAsync(taken[i].data(), s.forced, (size_t)s.n0,
-                                    cudaMemcpyDeviceToHost, Ln.stream);
+                                    cudaMemcpyDeviceToHost, Ln.load);
         }
     }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(Ln.stream);
-    InstState z;
-    std::memset(&z, 0, sizeof(z));
+    if (e == cudaSuccess) e = cudaStreamSynchronize(Ln.load);
     const int64_t t = now_ns();
     std::vector<std::shared_ptr<Request>> done;
     for (size_t i = 0; i < fin.size(); ++i) {
@@ -354,8 +372,7 @@ void retire(Lane &Ln, const std::vector<int> &fin) {
         } else {
             r.status = MHS_ECUDA;
         }
-        cudaMemcpyAsync(Ln.dstate + fin[i], &z, sizeof(z), cudaMemcpyHostToDevice, Ln.stream);
-        cudaFreeAsync(sl.arena, Ln.stream);
+        cudaFreeAsync(sl.arena, Ln.load);
         done.push_back(sl.req);
         Ln.in_use_release += sl.bytes;
         Ln.tiles_release += sl.tiles;
@@ -382,16 +399,29 @@ void retire(Lane &Ln, const std::vector<int> &fin) {
     for (auto &ln : S->lanes) ln.cv_work.notify_one();
 }
 
+// Fail everything and stop (the loop's launch has ended or faulted).
+void fatal_stop(mhs_server *S, mhs_status st) {
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (S->fatal == MHS_OK) S->fatal = st;
+    fail_all_locked(S, S->fatal);
+    S->stop = true;
+    S->cv_done.notify_all();
+    for (auto &ln : S->lanes) ln.cv_work.notify_all();
+}
+
 void worker_loop(Lane *L) {
     Lane &Ln = *L;
     mhs_server *S = Ln.S;
     cudaSetDevice(S->device);
     for (;;) {
-        // ---- admission at the round boundary ----
+        bool progress = false;
+        // ---- admission: load into free slots, then mark them ready ----
         std::vector<std::pair<int, std::shared_ptr<Request>>> to_admit;
         {
             std::unique_lock<std::mutex> lk(S->mu);
-            if (Ln.active_count == 0)
+            bool any_busy = false;
+            for (auto &sl : Ln.slots) any_busy |= sl.busy;
+            if (!any_busy && !Ln.running)
                 Ln.cv_work.wait_for(lk, std::chrono::milliseconds(50), [&] {
                     return S->stop || (!S->paused && !Ln.pending.empty());
                 });
@@ -418,6 +448,7 @@ void worker_loop(Lane *L) {
                 }
             }
         }
+        std::vector<int> loaded;
         for (auto &p : to_admit) {
             mhs_status st = admit(Ln, p.first, p.second);
             if (st != MHS_OK) {
@@ -428,60 +459,138 @@ void worker_loop(Lane *L) {
                 p.second->done = true;
                 p.second->t_done = now_ns();
                 S->cv_done.notify_all();
+            } else {
+                loaded.push_back(p.first);
             }
         }
-        bool any_busy = false;
-        for (auto &sl : Ln.slots) any_busy |= sl.busy;
-        if (!any_busy) continue;
-        // ---- one round for every busy slot of this lane ----
-        cudaError_t e = cudaGraphLaunch(Ln.graph, Ln.stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(Ln.stream);
-        if (e != cudaSuccess || *Ln.hkerr) {
-            std::lock_guard<std::mutex> lk(S->mu);
-            S->fatal = e != cudaSuccess ? MHS_ECUDA : MHS_EDEVICE;
-            fail_all_locked(S, S->fatal);
-            S->stop = true;
-            S->cv_done.notify_all();
-            for (auto &ln : S->lanes) ln.cv_work.notify_all();
-            break;
+        if (!loaded.empty()) {
+            // the staged states, arenas and build kernels are complete before
+            // the loop can see a ready flag
+            if (cudaStreamSynchronize(Ln.load) != cudaSuccess) {
+                fatal_stop(S, MHS_ECUDA);
+                break;
+            }
+            std::atomic_thread_fence(std::memory_order_seq_cst);
+            for (int si : loaded) reinterpret_cast<volatile int32_t *>(Ln.hready)[si] = 1;
+            std::atomic_thread_fence(std::memory_order_seq_cst);
+            progress = true;
         }
-        ++Ln.rounds;
-        const int nd = Ln.hctr->n_done;
-        std::vector<int> fin;
-        for (int i = 0; i < nd && i < Ln.slots_n; ++i) {
-            const int si = Ln.hdone[i];
-            if (si >= 0 && si < Ln.slots_n && Ln.slots[si].busy) fin.push_back(si);
+        // ---- retirement: the slots the loop published ----
+        const int32_t head = reinterpret_cast<volatile ServerFlags *>(Ln.hflags)->head;
+        std::atomic_thread_fence(std::memory_order_seq_cst);
+        if (head != Ln.consumed) {
+            std::vector<int> fin;
+            for (int32_t q = Ln.consumed; q != head; ++q) {
+                const int si = reinterpret_cast<volatile int32_t *>(Ln.hring)[q % Ln.slots_n];
+                if (si >= 0 && si < Ln.slots_n && Ln.slots[si].busy) fin.push_back(si);
+            }
+            Ln.consumed = head;
+            retire(Ln, fin);
+            progress = true;
         }
-        retire(Ln, fin);
+        // ---- the loop's launch: ended, faulted, or to be started ----
+        if (Ln.running) {
+            const cudaError_t q = cudaStreamQuery(Ln.stream);
+            if (q == cudaSuccess) {
+                Ln.running = false;
+                if (reinterpret_cast<volatile ServerFlags *>(Ln.hflags)->kerr) {
+                    fatal_stop(S, MHS_EDEVICE);
+                    break;
+                }
+                continue;  // take what it published last before deciding to start it again
+            }
+            if (q != cudaErrorNotReady) {
+                fatal_stop(S, MHS_ECUDA);
+                break;
+            }
+        }
+        if (!Ln.running) {
+            bool any_busy = false;
+            for (auto &sl : Ln.slots) any_busy |= sl.busy;
+            if (any_busy) {
+                cudaError_t e = cudaGraphLaunch(Ln.graph, Ln.stream);
+                if (e != cudaSuccess) {
+                    fatal_stop(S, MHS_ECUDA);
+                    break;
+                }
+                Ln.running = true;
+                progress = true;
+            }
+        }
+        if (!progress && Ln.running) {  // rounds are running: look again shortly
+            std::unique_lock<std::mutex> lk(S->mu);
+            Ln.cv_work.wait_for(lk, std::chrono::microseconds(20), [&] {
+                return S->stop || (!S->paused && !Ln.pending.empty());
+            });
+        }
     }
+    // stop: end the loop at its next round boundary and wait for it
+    reinterpret_cast<volatile ServerFlags *>(Ln.hflags)->stop = 1;
+    std::atomic_thread_fence(std::memory_order_seq_cst);
+    if (Ln.running) cudaStreamSynchronize(Ln.stream);
+    Ln.running = false;
+    cudaStreamSynchronize(Ln.load);
 }
 
+// The lane's loop: a memset node resets the iteration count, then a WHILE
+// node whose body admits ready slots, runs one round (DP, then MD, then FE
+// if enabled) over the slot table, retires finished slots and sets the
+// condition.
 mhs_status capture_graph(Lane &Ln) {
     mhs_server *S = Ln.S;
-    cudaGraph_t g;
-    cudaError_t e = cudaStreamBeginCapture(Ln.stream, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) return set_error(MHS_ECUDA, "server capture: %s", cudaGetErrorString(e));
-    cudaError_t e1 = launch_round_phase(Ln.dstate, Ln.dplan, Ln.dctr, Ln.slots_n, 0, S->contraction,
-                                        S->sms, Ln.dkerr, Ln.stream, nullptr, nullptr, nullptr);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaGraphCreate(&g, 0);
+    auto bail = [&](cudaError_t err, const char *what) {
+        if (g) cudaGraphDestroy(g);
+        return set_error(MHS_ECUDA, "server loop graph (%s): %s", what, cudaGetErrorString(err));
+    };
+    if (e != cudaSuccess) return bail(e, "create");
+    cudaGraphConditionalHandle cond;
+    e = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) return bail(e, "handle");
+    cudaGraphNode_t reset;
+    cudaMemsetParams mp;
+    std::memset(&mp, 0, sizeof(mp));
+    mp.dst = &Ln.ddev->iters;
+    mp.value = 0;
+    mp.elementSize = 4;
+    mp.width = 1;
+    mp.height = 1;
+    e = cudaGraphAddMemsetNode(&reset, g, nullptr, 0, &mp);
+    if (e != cudaSuccess) return bail(e, "reset");
+    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t loop;
+    e = cudaGraphAddNode(&loop, g, &reset, nullptr, 1, &cp);
+    if (e != cudaSuccess) return bail(e, "conditional node");
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(Ln.stream, body, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return bail(e, "capture");
+    cudaError_t e1 = launch_server_admit(Ln.dstate, Ln.dstage, Ln.dready, Ln.slots_n, Ln.stream);
+    if (e1 == cudaSuccess)
+        e1 = launch_round_phase(Ln.dstate, Ln.dplan, Ln.dctr, Ln.slots_n, 0, S->contraction,
+                                S->sms, Ln.dkerr, Ln.stream, nullptr, nullptr, nullptr);
     if (e1 == cudaSuccess)
         e1 = launch_round_phase(Ln.dstate, Ln.dplan, Ln.dctr, Ln.slots_n, 1, S->contraction,
                                 S->sms, Ln.dkerr, Ln.stream, nullptr, nullptr, Ln.ddone);
     if (e1 == cudaSuccess && S->opt.full_edges)
         e1 = launch_full_edges(Ln.dstate, Ln.slots_n, Ln.dctr, Ln.ddone, S->sms, Ln.stream);
     if (e1 == cudaSuccess)
-        e1 = cudaMemcpyAsync(Ln.hctr, Ln.dctr, sizeof(BatchCounters), cudaMemcpyDeviceToHost,
-                             Ln.stream);
+        e1 = launch_server_retire(Ln.dstate, Ln.dout, Ln.ddone, Ln.dctr, Ln.dring, Ln.dflags,
+                                  Ln.ddev, Ln.slots_n, Ln.stream);
     if (e1 == cudaSuccess)
-        e1 = cudaMemcpyAsync(Ln.hdone, Ln.ddone, 4 * (size_t)Ln.slots_n, cudaMemcpyDeviceToHost,
-                             Ln.stream);
-    if (e1 == cudaSuccess)
-        e1 = cudaMemcpyAsync(Ln.hkerr, Ln.dkerr, 4, cudaMemcpyDeviceToHost, Ln.stream);
-    cudaError_t e2 = cudaStreamEndCapture(Ln.stream, &g);
-    if (e1 != cudaSuccess || e2 != cudaSuccess)
-        return set_error(MHS_ECUDA, "server capture failed: %s",
-                         cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
+        e1 = launch_server_cond(cond, Ln.dctr, Ln.dkerr, Ln.dplan, Ln.ddev, Ln.dflags, Ln.dready,
+                                Ln.slots_n, kLoopIters, Ln.stream);
+    cudaGraph_t captured = nullptr;
+    e = cudaStreamEndCapture(Ln.stream, &captured);
+    if (e1 != cudaSuccess) return bail(e1, "round");
+    if (e != cudaSuccess) return bail(e, "end capture");
     e = cudaGraphInstantiate(&Ln.graph, g, 0);
     cudaGraphDestroy(g);
+    g = nullptr;
     if (e != cudaSuccess) return set_error(MHS_ECUDA, "server graph: %s", cudaGetErrorString(e));
     return MHS_OK;
 }
@@ -501,13 +610,18 @@ mhs_status setup_lane(mhs_server *S, Lane &Ln, int id, int32_t slots, int64_t li
             return set_error(MHS_ECUDA, "stream creation failed");
         Ln.own_stream = true;
     }
+    if (cudaStreamCreateWithFlags(&Ln.load, cudaStreamNonBlocking) != cudaSuccess)
+        return set_error(MHS_ECUDA, "stream creation failed");
     const int64_t ns = slots;
     const int64_t o_state = 0;
-    const int64_t o_plan = up(sizeof(InstState) * ns, 256);
+    const int64_t o_stage = o_state + up(sizeof(InstState) * ns, 256);
+    const int64_t o_out = o_stage + up(sizeof(InstState) * ns, 256);
+    const int64_t o_plan = o_out + up(sizeof(InstState) * ns, 256);
     const int64_t o_row = o_plan + up(sizeof(Plan), 256);
     const int64_t o_tile = o_row + up(4 * (ns + 1), 256);
     const int64_t o_ctr = o_tile + up(8 * (ns + 1), 256);
-    const int64_t o_kerr = o_ctr + up(sizeof(BatchCounters), 256);
+    const int64_t o_dev = o_ctr + up(sizeof(BatchCounters), 256);
+    const int64_t o_kerr = o_dev + up(sizeof(ServerDev), 256);
     const int64_t o_done = o_kerr + 256;
     const int64_t o_list = o_done + up(4 * ns, 256);
     const int64_t total = o_list + up(8 * std::max<int64_t>(list_cap, 1), 256);
@@ -515,17 +629,34 @@ mhs_status setup_lane(mhs_server *S, Lane &Ln, int id, int32_t slots, int64_t li
                                 Ln.stream) != cudaSuccess)
         return set_error(MHS_ENOMEM, "server control allocation failed");
     Ln.dstate = reinterpret_cast<InstState *>(Ln.ctl + o_state);
+    Ln.dstage = reinterpret_cast<InstState *>(Ln.ctl + o_stage);
+    Ln.dout = reinterpret_cast<InstState *>(Ln.ctl + o_out);
     Ln.dplan = reinterpret_cast<Plan *>(Ln.ctl + o_plan);
     Ln.dctr = reinterpret_cast<BatchCounters *>(Ln.ctl + o_ctr);
+    Ln.ddev = reinterpret_cast<ServerDev *>(Ln.ctl + o_dev);
     Ln.dkerr = reinterpret_cast<int32_t *>(Ln.ctl + o_kerr);
     Ln.ddone = reinterpret_cast<int32_t *>(Ln.ctl + o_done);
-    if (cudaMallocHost(&Ln.hctr, sizeof(BatchCounters)) != cudaSuccess ||
-        cudaMallocHost(&Ln.hkerr, 4) != cudaSuccess ||
-        cudaMallocHost(&Ln.hdone, 4 * (size_t)ns) != cudaSuccess ||
-        cudaMallocHost(&Ln.hmaps, 2 * tmap_bytes() * (size_t)ns) != cudaSuccess ||
+    // host-mapped: the flags, then ready[ns], then ring[ns]
+    const size_t o_ready = up(sizeof(ServerFlags), 64);
+    const size_t o_ring = o_ready + up(4 * ns, 64);
+    const size_t mapped_bytes = o_ring + up(4 * ns, 64);
+    if (cudaHostAlloc(reinterpret_cast<void **>(&Ln.mapped), mapped_bytes,
+                      cudaHostAllocMapped) != cudaSuccess)
+        return set_error(MHS_ENOMEM, "mapped host allocation failed");
+    std::memset(Ln.mapped, 0, mapped_bytes);
+    uint8_t *dmapped = nullptr;
+    if (cudaHostGetDevicePointer(reinterpret_cast<void **>(&dmapped), Ln.mapped, 0) !=
+        cudaSuccess)
+        return set_error(MHS_ECUDA, "mapped host memory unavailable on the device");
+    Ln.hflags = reinterpret_cast<ServerFlags *>(Ln.mapped);
+    Ln.dflags = reinterpret_cast<ServerFlags *>(dmapped);
+    Ln.hready = reinterpret_cast<int32_t *>(Ln.mapped + o_ready);
+    Ln.dready = reinterpret_cast<int32_t *>(dmapped + o_ready);
+    Ln.hring = reinterpret_cast<int32_t *>(Ln.mapped + o_ring);
+    Ln.dring = reinterpret_cast<int32_t *>(dmapped + o_ring);
+    if (cudaMallocHost(&Ln.hmaps, 2 * tmap_bytes() * (size_t)ns) != cudaSuccess ||
         cudaMallocHost(&Ln.hstates, sizeof(InstState) * (size_t)ns) != cudaSuccess)
         return set_error(MHS_ENOMEM, "pinned allocation failed");
-    *Ln.hkerr = 0;
     Plan p;
     std::memset(&p, 0, sizeof(p));
     p.count = slots;
@@ -562,14 +693,14 @@ void destroy_server(mhs_server *S) {
         if (ln.stream) cudaStreamSynchronize(ln.stream);
         for (auto &sl : ln.slots)
             if (sl.arena) cudaFreeAsync(sl.arena, ln.stream);
+        if (ln.load) cudaStreamSynchronize(ln.load);
         if (ln.graph) cudaGraphExecDestroy(ln.graph);
         if (ln.ctl) cudaFreeAsync(ln.ctl, ln.stream);
         if (ln.stream) cudaStreamSynchronize(ln.stream);
-        if (ln.hctr) cudaFreeHost(ln.hctr);
-        if (ln.hkerr) cudaFreeHost(ln.hkerr);
-        if (ln.hdone) cudaFreeHost(ln.hdone);
+        if (ln.mapped) cudaFreeHost(ln.mapped);
         if (ln.hmaps) cudaFreeHost(ln.hmaps);
         if (ln.hstates) cudaFreeHost(ln.hstates);
+        if (ln.load) cudaStreamDestroy(ln.load);
         if (ln.own_stream && ln.stream) cudaStreamDestroy(ln.stream);
     }
     delete S;
@@ -783,7 +914,8 @@ mhs_status mhs_server_get_stats(mhs_server *S, mhs_server_stats *out) {
     out->submitted = S->submitted;
     out->admitted = S->admitted;
     out->completed = S->completed;
-    out->rounds = S->lanes[0].rounds + S->lanes[1].rounds;
+    for (auto &ln : S->lanes)
+        if (ln.hflags) out->rounds += reinterpret_cast<volatile ServerFlags *>(ln.hflags)->rounds;
     out->pending = (int32_t)(S->lanes[0].pending.size() + S->lanes[1].pending.size());
     out->active = S->lanes[0].active_count + S->lanes[1].active_count;
     out->bytes_in_use = S->in_use;
