@@ -318,6 +318,28 @@ __device__ __forceinline__ int32_t kit_next(KIter &k) {
     return (k.w * 32 + bit) >> 1;
 }
 
+// Shared K-block halves of a tile (its MMA work in half stages): the set
+// bits of the ANDed occupancy words over its K range.
+__device__ __forceinline__ int32_t kit_weight(const KIter &k) {
+    if (k.all) return 2 * k.nk;
+    int32_t w = 0;
+    for (int32_t i = 0; i < k.nkw; ++i) {
+        uint32_t bm = __ldg(k.b0 + i);
+        if (k.b1) bm |= __ldg(k.b1 + i);
+        w += __popc(__ldg(k.a + i) & bm);
+    }
+    return w;
+}
+
+// A tile whose MMA work exceeds about what the epilogue spends on a tile
+// (~5,000 cycles: 18 half stages of 128 x 256 x 64 at the FP8 rate) is
+// heavy; the scheduler alternates heavy and light tiles so that the MMA
+// thread and the epilogue warps stay busy together.  Measured on one GB300:
+// power-law 20,000 x 40,000 +2.8 % per kernelization, the batch of 4,096
+// -1.1 % (its two frontiers of the tile order share L2 less well), so a load
+// of one instance uses two queues and a batch one (Plan::two_queues).
+constexpr int32_t kHeavyHalves = 18;
+
 // Build this phase's tile list: every tile of the upper triangle (in the
 // grouped order of tc_tile_coords, tiles 128 x plan->tile_n) that holds a
 // candidate row or column (incremental rounds) and shares a nonzero K block
@@ -338,6 +360,7 @@ __global__ void k_tile_list(InstState *st, Plan *plan, int phase, int shard, int
         const int64_t t = base + lane;
         bool keep = false;
         int64_t packed = 0;
+        int32_t weight = kHeavyHalves;  // (the dense formulation: every tile heavy)
         if (t < total) {
             int lo = 0, hi = plan->count;
             while (hi - lo > 1) {
@@ -365,17 +388,26 @@ __global__ void k_tile_list(InstState *st, Plan *plan, int phase, int shard, int
                 if (keep) {
                     KIter k;
                     kit_init(k, s, phase, ti, r);
-                    has_k = kit_next(k) >= 0;
+                    weight = kit_weight(k);
+                    has_k = weight > 0;
                     keep = has_k || (phase == 0 && s.has_loose);
                 }
             }
             packed = pack_tile(lo, ti.bi, ti.bj) | (has_k ? 0 : kTileNoK);
         }
-        const uint32_t ballot = __ballot_sync(0xffffffffu, keep);
-        int32_t start = 0;
-        if (lane == 0 && ballot) start = atomicAdd(&plan->list_count, __popc(ballot));
-        start = __shfl_sync(0xffffffffu, start, 0);
-        if (keep) plan->tile_list[start + __popc(ballot & ((1u << lane) - 1))] = packed;
+        // heavy tiles from the front of the list, light ones from the back
+        // (a 128 x 128 tile halves both sides, so the threshold holds for both widths)
+        const bool heavy = !plan->two_queues || weight >= kHeavyHalves;
+        const uint32_t bh = __ballot_sync(0xffffffffu, keep && heavy);
+        const uint32_t bl = __ballot_sync(0xffffffffu, keep && !heavy);
+        int32_t sh = 0, sl = 0;
+        if (lane == 0 && bh) sh = atomicAdd(&plan->list_count, __popc(bh));
+        if (lane == 0 && bl) sl = atomicAdd(&plan->list_light, __popc(bl));
+        sh = __shfl_sync(0xffffffffu, sh, 0);
+        sl = __shfl_sync(0xffffffffu, sl, 0);
+        const uint32_t below = (1u << lane) - 1u;
+        if (keep && heavy) plan->tile_list[sh + __popc(bh & below)] = packed;
+        if (keep && !heavy) plan->tile_list[plan->list_cap - 1 - (sl + __popc(bl & below))] = packed;
     }
 }
 
@@ -1059,6 +1091,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // slot and publishes it; every lane arrives on the slot's barrier
         // after its own writes.  Runs at most kRing slots ahead of the
         // slowest reader.
+        bool heavy_left = true, light_left = true;  // (lane 0: a queue once empty stays so)
         for (int k = 0;; ++k) {
             const int sl = k % kRing;
             bool ok = true;
@@ -1068,8 +1101,24 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (!__shfl_sync(0xffffffffu, ok ? 1 : 0, 0)) break;
             int64_t e = -1;
             if (lane == 0) {
-                const int32_t t = atomicAdd(const_cast<int32_t *>(&plan->list_next), 1);
-                e = t < plan->list_count ? plan->tile_list[t] : -1;
+                // alternate the heavy (front) and light (back) queues; when one
+                // is empty, take from the other (a list of one queue: only it)
+                const int first = plan->list_light == 0 ? 0 : (int)((k + blockIdx.x) & 1);
+                for (int q = 0; q < 2 && e < 0; ++q) {
+                    if (((first + q) & 1) == 0) {
+                        if (heavy_left) {
+                            const int32_t t =
+                                atomicAdd(const_cast<int32_t *>(&plan->list_next), 1);
+                            if (t < plan->list_count) e = plan->tile_list[t];
+                            else heavy_left = false;
+                        }
+                    } else if (light_left) {
+                        const int32_t t =
+                            atomicAdd(const_cast<int32_t *>(&plan->list_next_light), 1);
+                        if (t < plan->list_light) e = plan->tile_list[plan->list_cap - 1 - t];
+                        else light_left = false;
+                    }
+                }
             }
             e = __shfl_sync(0xffffffffu, e, 0);
             TileSlot &ts = ctl->slot[sl];

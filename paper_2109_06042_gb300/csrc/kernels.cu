@@ -412,6 +412,8 @@ __global__ void k_plan(InstState *st, Plan *plan, int phase, int tc, BatchCounte
         plan->total_rows = rcarry;
         plan->list_count = 0;
         plan->list_next = 0;
+        plan->list_light = 0;
+        plan->list_next_light = 0;
         plan->total_tiles = tcarry;
         plan->any_active = act_any;
         if (phase == 0 && ctr) {
@@ -1542,6 +1544,7 @@ cudaError_t launch_phase_contract(InstState *st, Plan *plan, BatchCounters *ctr,
         // each share builds its own list and hands it out from its start
         cudaError_t e = cudaMemsetAsync(&plan->list_count, 0, sizeof(int32_t), s);
         if (e == cudaSuccess) e = cudaMemsetAsync(&plan->list_next, 0, sizeof(int32_t), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(&plan->list_light, 0, 2 * sizeof(int32_t), s);
         if (e == cudaSuccess) e = launch_tc_tile_list(st, plan, phase, sms, s, shard, nshards);
         if (e != cudaSuccess) return e;
         return launch_tc_contract(st, plan, ctr, phase, sms, tile_n, kerr, s);

@@ -151,7 +151,12 @@ struct Plan {
     int32_t list_next;      // tcgen05: next tile_list entry to hand out (dynamic schedule)
     int32_t tile_n;         // tcgen05: columns per tile, 128 or 256 (rows: kTcM)
     int32_t half_stages;    // tcgen05: 1 = load a K block shared in one half as that half
-    int32_t pad_;
+    // tcgen05: the tile list holds two queues, tiles whose MMA work exceeds
+    // the epilogue's from the front (list_count entries), the others from
+    // the back (list_light entries, the j-th at list_cap - 1 - j)
+    int32_t list_light;
+    int32_t list_next_light;  // next light entry to hand out
+    int32_t two_queues;       // 0: every tile in the front queue (one queue)
 };
 
 // Number of pair tiles of an R x R upper triangle.
