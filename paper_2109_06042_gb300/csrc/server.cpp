@@ -20,7 +20,7 @@
 // Requests that arrive while others are on the GPU join at the next round
 // boundary, so work of different sizes overlaps in the same launches.
 // Requests are split by size into two lanes, each with its own slot table,
-// captured round graph, worker thread and stream: small instances are
+// device loop, host thread and streams: small instances are
 // batched by the hundreds on a high-priority stream, large ones (which fill
 // the GPU on their own) run a few at a time on the other, so a small
 // request never waits for the rounds of a large one.  The HBM budget, the
