@@ -646,7 +646,54 @@ def sub_records(torch, mhs, stream, args, peaks, kind):
         torch.cuda.empty_cache()
     out["stream"] = serve_sweep(mhs, torch, args, args.sub_requests, min(args.pool, 150),
                                 args.sub_rates, rank=0)
+    if args.contraction == "fp8":
+        out["precision"] = precision_record(torch, mhs, stream, args, peaks)
     return out
+
+
+def precision_record(torch, mhs, stream, args, peaks):
+    """The headline instance through the bit-packed AND + popcount form and
+    through the FP8 tensor-core form on the same GPU: time per kernelization
+    of each, the popcount contraction's ALU and HBM fractions, and whether
+    the two forms give the same result masks byte for byte."""
+    import copy
+    insts, desc = make_instances(args, 0, "powerlaw")
+    pa = copy.copy(args)
+    pa.contraction = "popcount"
+    P = Runner(torch, mhs, stream, insts, pa, reps=1)
+    traces, rounds = P.traces()
+    flops, _, bits_bytes = algorithmic_work(traces)
+    steps = 3
+    ms, cms, _ = P.timed(steps, 1)
+    P.one()
+    av_p, ae_p = P.D.av.clone(), P.D.ae.clone()
+    F = Runner(torch, mhs, stream, insts, args, reps=1)
+    ms_f, _, _ = F.timed(steps, 1)
+    F.one()
+    nv, ne = int(F.D.n.sum()), int(F.D.m.sum())  # (the masks' last byte is padding)
+    same = bool(torch.equal(av_p[:nv], F.D.av[:nv]) and torch.equal(ae_p[:ne], F.D.ae[:ne]))
+    s_contract = cms / steps / 1e3
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    popc_peak = 152 * 16 * 32 * 2 * sm_mhz * 1e6 / 1e12  # 16 POPC/clk/SM x 32 bit-MACs
+    alu = flops / s_contract / 1e12 if s_contract > 0 else 0.0
+    hbm = bits_bytes / s_contract / 1e9 if s_contract > 0 else 0.0
+    rec = {"workload": desc, "rounds": rounds,
+           "popcount": {"kernel": "k_pop_contract",
+                        "ms_per_kernelization": round(ms / steps, 3),
+                        "value": round(steps / (ms / 1e3), 3), "unit": UNIT,
+                        "alu": {"achieved": round(alu, 2), "peak": round(popc_peak, 1),
+                                "unit": "TOP/s", "frac": round(alu / popc_peak, 4),
+                                "basis": "bit-MACs of the dense formulation x 2"},
+                        "hbm": {"achieved": round(hbm, 2), "peak": peaks["hbm_gbs"],
+                                "unit": "GB/s", "frac": round(hbm / peaks["hbm_gbs"], 4),
+                                "basis": "bit-packed operand bytes per pass"}},
+           "fp8": {"kernel": "k_tc_contract", "ms_per_kernelization": round(ms_f / steps, 3),
+                   "value": round(steps / (ms_f / 1e3), 3), "unit": UNIT},
+           "identical_output": same,
+           "speedup_fp8_over_popcount": round(ms / ms_f, 2) if ms_f > 0 else None}
+    del P, F
+    torch.cuda.empty_cache()
+    return rec
 
 
 def serve_sweep(mhs, torch, args, requests, pool_size, rates, rank=0):
