@@ -1381,11 +1381,11 @@ __global__ void __launch_bounds__(256) k_server_retire(InstState *live, InstStat
     }
     if (threadIdx.x == 0 && nf > 0) {
         __threadfence_system();  // the states in `out` before the ring entries
-        const int32_t head = dev->head;
-        for (int i = 0; i < nf; ++i) ring[(head + i) % count] = fin[i];
+        const uint32_t head = dev->head;
+        for (int i = 0; i < nf; ++i) ring[(head + (uint32_t)i) % (uint32_t)count] = fin[i];
         __threadfence_system();  // the entries before the head
-        dev->head = head + nf;
-        flags->head = head + nf;
+        dev->head = head + (uint32_t)nf;
+        flags->head = head + (uint32_t)nf;
         __threadfence_system();
     }
 }

@@ -79,13 +79,13 @@ cudaError_t launch_alive_masks(const InstState *st, uint8_t *alive_v, uint8_t *a
 struct ServerFlags {
     int32_t stop;      // host -> device: end the loop at its next round boundary
     int32_t kerr;      // device -> host: the loop's error bits
-    int32_t head;      // device -> host: slot indices published in `ring` so far
+    uint32_t head;     // device -> host: slot indices published in `ring` so far (wraps)
     int32_t pad_;
     long long rounds;  // device -> host: rounds run over the lane's slot table
 };
 // Device-side bookkeeping of a lane's loop.
 struct ServerDev {
-    int32_t head;      // slot indices published so far
+    uint32_t head;     // slot indices published so far (wraps; the ring index is head % count)
     int32_t iters;     // iterations of the current launch
     long long rounds;
 };

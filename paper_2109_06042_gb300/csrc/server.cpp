@@ -165,7 +165,7 @@ struct Lane {
     ServerFlags *hflags = nullptr, *dflags = nullptr;
     int32_t *hready = nullptr, *dready = nullptr;
     int32_t *hring = nullptr, *dring = nullptr;
-    int32_t consumed = 0;           // ring entries taken by the host
+    uint32_t consumed = 0;          // ring entries taken by the host (wraps with the head)
     bool running = false;           // a launch of the loop may still run
     uint8_t *hmaps = nullptr;       // pinned: 2 tensor maps per slot, staged for upload
     InstState *hstates = nullptr;   // pinned: states of the slots retired at once
@@ -476,12 +476,13 @@ void worker_loop(Lane *L) {
             progress = true;
         }
         // ---- retirement: the slots the loop published ----
-        const int32_t head = reinterpret_cast<volatile ServerFlags *>(Ln.hflags)->head;
+        const uint32_t head = reinterpret_cast<volatile ServerFlags *>(Ln.hflags)->head;
         std::atomic_thread_fence(std::memory_order_seq_cst);
         if (head != Ln.consumed) {
             std::vector<int> fin;
-            for (int32_t q = Ln.consumed; q != head; ++q) {
-                const int si = reinterpret_cast<volatile int32_t *>(Ln.hring)[q % Ln.slots_n];
+            for (uint32_t q = Ln.consumed; q != head; ++q) {
+                const int si =
+                    reinterpret_cast<volatile int32_t *>(Ln.hring)[q % (uint32_t)Ln.slots_n];
                 if (si >= 0 && si < Ln.slots_n && Ln.slots[si].busy) fin.push_back(si);
             }
             Ln.consumed = head;
