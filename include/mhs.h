@@ -151,8 +151,12 @@ mhs_status mhs_default_options(mhs_options *opt);
  *   opt           options (NULL: defaults)
  *   cuda_stream   cudaStream_t for all work of this instance, or NULL
  *   out           receives the new instance handle
- * Errors: MHS_EINVAL for malformed input (nothing allocated), MHS_ENOMEM,
- * MHS_ECUDA.  The call returns after the input is on the device.
+ * Errors: MHS_EINVAL for malformed input, MHS_ENOMEM, MHS_ECUDA; on any
+ * error no handle is returned and nothing stays allocated.  The pointer
+ * array is checked before anything is read from edge_vtx; the incidences
+ * are checked on the host (on several threads for a large instance) while
+ * the inputs are copied, and no kernel reads them before the checks pass.
+ * The call returns after the input is on the device.
  */
 mhs_status mhs_load(int32_t n, int32_t m, const int32_t *edge_ptr, const int32_t *edge_vtx,
                     const int32_t *demand, int64_t k, const mhs_options *opt,
@@ -179,6 +183,8 @@ mhs_status mhs_load_device(int32_t n, int32_t m, const int32_t *edge_ptr,
  *   edge_vtx              vertex ids local to each instance, in [0, n[b])
  *   demand                int32[sum m]
  *   k                     int64[count]
+ * Checks as mhs_load, on several host threads for a large batch while the
+ * inputs are copied; MHS_EINVAL names the lowest malformed instance.
  * Results are read per instance with mhs_result_at().
  */
 mhs_status mhs_load_batch(int32_t count, const int32_t *n, const int32_t *m,
