@@ -371,21 +371,40 @@ mhs_status validate_host(int32_t n, int32_t m, const int64_t *eptr64, const int3
 
 // validate_host over hyperedge ranges on several threads for a large
 // instance; a failure is validated again on this thread for its message.
+// With `stage` (page-locked, the layout of the device copies: edge_ptr,
+// edge_vtx, demand), each part also copies its range there once it has
+// checked it, while the range is still in cache.  The pointer array must
+// already be known monotone with edge_ptr[0] = 0.
 mhs_status validate_host_parallel(int32_t n, int32_t m, const int32_t *eptr32,
                                   const int32_t *evtx, const int32_t *demand, int64_t nnz,
-                                  const char *what) {
+                                  const char *what, uint8_t *stage = nullptr) {
     std::vector<int32_t> mark;
-    const int nt = nnz >= (1 << 17) ? (int)std::min<int64_t>(8, nnz >> 16) : 1;
-    if (nt <= 1) return validate_host(n, m, nullptr, eptr32, evtx, demand, mark, 0, what);
+    const int nt = nnz >= (1 << 16) ? (int)std::min<int64_t>(8, nnz >> 15) : 1;
+    int32_t *s_ptr = reinterpret_cast<int32_t *>(stage);
+    int32_t *s_vtx = stage ? s_ptr + (m + 1) : nullptr;
+    int32_t *s_f = stage ? s_vtx + nnz : nullptr;
     std::atomic<bool> bad{false};
     auto part = [&](int t) {
         const int32_t e0 = (int32_t)((int64_t)m * t / nt);
         const int32_t e1 = (int32_t)((int64_t)m * (t + 1) / nt);
         std::vector<int32_t> mk;
         if (validate_host(n, e1 - e0, nullptr, eptr32 + e0, evtx, demand + e0, mk, 0, what,
-                          /*quiet=*/true))
+                          /*quiet=*/true)) {
             bad = true;
+            return;
+        }
+        if (stage) {
+            const int32_t p0 = eptr32[e0], p1 = eptr32[e1];
+            std::memcpy(s_ptr + e0, eptr32 + e0, 4 * (size_t)(e1 - e0 + (t == nt - 1 ? 1 : 0)));
+            if (p1 > p0) std::memcpy(s_vtx + p0, evtx + p0, 4 * (size_t)(p1 - p0));
+            if (e1 > e0) std::memcpy(s_f + e0, demand + e0, 4 * (size_t)(e1 - e0));
+        }
     };
+    if (nt <= 1) {
+        part(0);
+        if (!bad) return MHS_OK;
+        return validate_host(n, m, nullptr, eptr32, evtx, demand, mark, 0, what);
+    }
     std::vector<std::thread> threads;
     int started = 1;
     try {
@@ -983,18 +1002,22 @@ mhs_status mhs_load(int32_t n, int32_t m, const int32_t *edge_ptr, const int32_t
     mhs_instance *h = nullptr;
     mhs_status st = create(1, &n, &m, &nnz, &k, opt, cuda_stream, &h, lay, tmoff);
     if (st) return st;
-    // The inputs go to the device (through pinned staging when it is
-    // available) while the host validates them; no kernel reads them before
-    // the validation has passed.
+    // The host checks the incidences, several threads each taking a range
+    // of hyperedges and, once it has checked it, copying the range into
+    // page-locked staging (a buffer of its own, nothing else writes it while
+    // the copies run); the copies to the device follow.  Without staging the
+    // inputs are copied from the caller's arrays while the host checks them.
+    // No kernel reads them before the checks have passed.
     const InstState &s = h->hstate[0];
     const size_t b_ptr = 4 * ((size_t)m + 1), b_vtx = 4 * (size_t)nnz, b_f = 4 * (size_t)m;
-    // (a buffer of its own: nothing else writes it while the copies run)
     h->in_stage = static_cast<uint8_t *>(pinned_take(b_ptr + b_vtx + b_f, &h->in_stage_cls));
     const void *src_ptr = edge_ptr, *src_vtx = edge_vtx, *src_f = demand;
     if (uint8_t *in = h->in_stage) {
-        std::memcpy(in, edge_ptr, b_ptr);
-        if (b_vtx) std::memcpy(in + b_ptr, edge_vtx, b_vtx);
-        if (b_f) std::memcpy(in + b_ptr + b_vtx, demand, b_f);
+        st = validate_host_parallel(n, m, edge_ptr, edge_vtx, demand, nnz, "instance", in);
+        if (st) {
+            destroy(h);
+            return st;
+        }
         src_ptr = in;
         src_vtx = in + b_ptr;
         src_f = in + b_ptr + b_vtx;
@@ -1011,10 +1034,12 @@ mhs_status mhs_load(int32_t n, int32_t m, const int32_t *edge_ptr, const int32_t
         destroy(h);
         return fail(MHS_ECUDA, "input copy failed: %s", cudaGetErrorString(e));
     }
-    st = validate_host_parallel(n, m, edge_ptr, edge_vtx, demand, nnz, "instance");
-    if (st) {
-        destroy(h);  // (waits for the copies)
-        return st;
+    if (!h->in_stage) {
+        st = validate_host_parallel(n, m, edge_ptr, edge_vtx, demand, nnz, "instance");
+        if (st) {
+            destroy(h);  // (waits for the copies)
+            return st;
+        }
     }
     st = finish_load(h, tmoff);
     if (st == MHS_OK && cudaStreamSynchronize(h->stream) != cudaSuccess)
