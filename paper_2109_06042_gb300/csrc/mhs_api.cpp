@@ -1146,16 +1146,44 @@ mhs_status mhs_load_batch(int32_t count, const int32_t *n, const int32_t *m,
         return validate_host(n[b], m[b], edge_ptr + eoff[b], nullptr, edge_vtx, demand + eoff[b],
                              mark, 0, what, /*quiet=*/true);
     };
-    const int nt = count >= 64 ? 8 : 1;
+    // Page-locked staging in the layout of the arena's input arrays (local
+    // int32 offsets, vertex ids, demands, each over the whole batch): every
+    // checked instance is converted and copied there by the thread that
+    // checked it, and three copies take the batch to the device.  Without it
+    // (inputs above 1 GB, or no page-locked memory) this thread converts the
+    // offsets and copies from the caller's arrays.
+    const int64_t sum_m = eoff[count], sum_m1 = sum_m + count, sum_z = edge_ptr[sum_m];
+    const int64_t stage_bytes = 4 * (sum_m1 + sum_z + sum_m);
+    size_t stage_cls = 0;
+    uint8_t *stage = stage_bytes <= (1ll << 30)
+                         ? static_cast<uint8_t *>(pinned_take((size_t)stage_bytes, &stage_cls))
+                         : nullptr;
+    int32_t *s_ptr = reinterpret_cast<int32_t *>(stage);
+    int32_t *s_vtx = stage ? s_ptr + sum_m1 : nullptr;
+    int32_t *s_f = stage ? s_vtx + sum_z : nullptr;
+    auto to_stage = [&](int b) {
+        const int64_t e0 = eoff[b], p0 = edge_ptr[e0];
+        int32_t *dp = s_ptr + e0 + b;  // instance b's m[b] + 1 offsets
+        for (int32_t i = 0; i <= m[b]; ++i) dp[i] = (int32_t)(edge_ptr[e0 + i] - p0);
+        if (nnz[b] > 0) std::memcpy(s_vtx + p0, edge_vtx + p0, 4 * (size_t)nnz[b]);
+        if (m[b] > 0) std::memcpy(s_f + e0, demand + e0, 4 * (size_t)m[b]);
+    };
+    // threads: one per core, up to 16 (none for a small batch)
+    const int nt = count >= 64
+                       ? (int)std::min<unsigned>(16, std::max(1u, std::thread::hardware_concurrency()))
+                       : 1;
     std::atomic<int> first_bad{count};
     auto share = [&](int t) {
         std::vector<int32_t> mark;
-        for (int b = t; b < count && b < first_bad.load(); b += nt)
+        for (int b = t; b < count && b < first_bad.load(); b += nt) {
             if (check(b, mark)) {
                 int cur = first_bad.load();
                 while (b < cur && !first_bad.compare_exchange_weak(cur, b)) {
                 }
+            } else if (stage) {
+                to_stage(b);
             }
+        }
     };
     std::vector<std::thread> threads;
     int started = 1;
@@ -1185,8 +1213,36 @@ mhs_status mhs_load_batch(int32_t count, const int32_t *n, const int32_t *m,
     if (st) {  // a malformed input is reported first, as a check before the allocation would
         const std::string msg = g_err;
         const mhs_status vst = finish_checks();
+        pinned_give(stage, stage_cls);
         if (vst) return vst;
         return fail(st, "%s", msg.c_str());
+    }
+    if (stage) {  // checked and staged: three copies; the buffer lives as long as the handle
+        h->in_stage = stage;
+        h->in_stage_cls = stage_cls;
+        st = finish_checks();
+        if (st) {
+            destroy(h);
+            return st;
+        }
+        cudaError_t e = cudaMemcpyAsync(h->arena + h->in_eptr, s_ptr, 4 * (size_t)sum_m1,
+                                        cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess && sum_z > 0)
+            e = cudaMemcpyAsync(h->arena + h->in_evtx, s_vtx, 4 * (size_t)sum_z,
+                                cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess && sum_m > 0)
+            e = cudaMemcpyAsync(h->arena + h->in_f, s_f, 4 * (size_t)sum_m,
+                                cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) st = finish_load(h, tmoff);
+        else st = fail(MHS_ECUDA, "input copy failed: %s", cudaGetErrorString(e));
+        if (st == MHS_OK && cudaStreamSynchronize(h->stream) != cudaSuccess)
+            st = fail(MHS_ECUDA, "load failed");
+        if (st) {
+            destroy(h);
+            return st;
+        }
+        *out = h;
+        return MHS_OK;
     }
     // one copy per input array: local int32 offsets, vertex ids, demands
     std::vector<int32_t> local_ptr((size_t)h->sum_m1);
