@@ -117,3 +117,32 @@ def test_destroy_with_pending_work(mhs):
     for s in range(5):
         srv.submit(I.config_uniform(s))
     srv.close()  # must not hang
+
+
+def test_loop_restarts_and_admits_while_running(mhs):
+    """The device-resident loop ends when no slot holds work and is started
+    again by the next submission; requests submitted while rounds run are
+    admitted at a round boundary of the running loop.  Every result equals
+    the oracle's."""
+    waves = [[I.config_batch_one(9100 + 10 * w + i) for i in range(6)] for w in range(3)]
+    with mhs.Server(max_slots=8) as srv:
+        done = []
+        for w, wave in enumerate(waves):  # each wave finishes: the loop goes idle
+            tickets = [srv.submit(i) for i in wave]
+            done.append((wave, _poll_all(srv, tickets)))
+            time.sleep(0.05)
+        rounds_idle = srv.stats()["rounds"]
+        # staggered submissions into a loop that is running
+        stag = [I.config_batch_one(9200 + i) for i in range(12)] + \
+               [I.config_powerlaw(7, n=2500, m=5000)]
+        tickets = []
+        for inst in stag:
+            tickets.append(srv.submit(inst))
+            time.sleep(0.002)
+        done.append((stag, _poll_all(srv, tickets)))
+        st = srv.stats()
+    assert rounds_idle > 0 and st["rounds"] > rounds_idle
+    assert st["completed"] == sum(len(w) for w, _ in done) and st["active"] == 0
+    for wave, results in done:
+        for idx, (inst, res) in enumerate(zip(wave, results)):
+            _same(res, O.reduce(inst), f"oracle {idx}")
