@@ -138,6 +138,22 @@ def test_fp8_and_popcount_agree_on_medium(mhs):
             assert np.array_equal(a[key], b[key])
 
 
+def test_groups_beyond_the_sector_table(mhs):
+    """Hyperedges of 30-60 vertices: a group of 32 rows holds more incidences
+    than the operand passes' shared-memory table (512), so those groups set
+    their bytes with atomics instead; mixed with groups that use the table
+    (sizes 2-6), and with a few dominated hyperedges so that rounds go on."""
+    big = I.uniform_random(1500, 900, 30, 60, 3, 150, seed=31)
+    mixed = I.uniform_random(1200, 1600, 2, 6, 2, 120, seed=32)
+    edges = big.edges() + [e[:3] for e in big.edges()[:64]] + mixed.edges()
+    dem = np.concatenate([big.demand, np.ones(64, np.int32), mixed.demand]).tolist()
+    inst = I.from_edges(1500, edges, dem, k=150)
+    assert max(len(e) for e in edges) >= 30 and inst.nnz > 40_000
+    ref = O.reduce(inst)
+    _same(mhs.kernelize(inst, contraction="fp8"), ref, "fp8 sector table overflow")
+    _same(mhs.kernelize(inst, contraction="fp8", layout="input"), ref, "input layout")
+
+
 def test_large_counts_exact(mhs):
     """Counts up to 2^20 stay exact with E4M3 0/1 operands and FP32 accumulation.
 
